@@ -1,0 +1,261 @@
+"""Python access to the FP64 CPU oracle (``nbody_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the package smoke check
+in ``__graft_entry__.py`` and by the CPU-baseline leg of ``bench.py``.  The
+product path never imports it.  It shares nothing with the CUDA library but
+the seeded input generators that produce its inputs.
+
+``build()`` compiles the C file with gcc (``-O3 -fopenmp -ffp-contract=off``,
+no machine-specific flags) into ``oracle/_build/liboracle.so``; ``lib()``
+builds on first use when the shared object is missing or older than the
+source.  ``compile_to(src, out)`` builds any copy of the source the same way.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "nbody_oracle.c")
+BUILD = os.path.join(HERE, "_build")
+SO = os.path.join(BUILD, "liboracle.so")
+# A test that checks that the pins catch planted mistakes points this at a
+# deliberately broken copy of the oracle built in a temporary directory.
+_SO_OVERRIDE = os.environ.get("NBODY_ORACLE_SO")
+TICKS_LOG2 = 20
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    if _SO_OVERRIDE:
+        return _SO_OVERRIDE
+    os.makedirs(BUILD, exist_ok=True)
+    if force or not os.path.exists(SO) or os.path.getmtime(SO) < os.path.getmtime(SRC):
+        tmp = SO + f".tmp{os.getpid()}"
+        compile_to(SRC, tmp)
+        os.replace(tmp, SO)
+    return SO
+
+
+def compile_to(src: str, out: str) -> str:
+    cmd = ["gcc", "-O3", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-std=c11", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            d, i64, i32, vp = C.c_double, C.c_int64, C.c_int32, C.c_void_p
+            L.orc_max_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_force_jerk.argtypes = [i64, vp, vp, vp, d, d, i64, vp, vp, vp]
+            L.orc_energy.argtypes = [i64, vp, vp, vp, d, d, vp, vp]
+            L.orc_predict.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_aarseth_dt.argtypes = [vp, vp, vp, vp, d]
+            L.orc_aarseth_dt.restype = d
+            L.orc_level_from_dt.argtypes = [d, C.c_int, C.c_int, vp]
+            L.orc_level_from_dt.restype = C.c_int
+            L.orc_next_level.argtypes = [C.c_int, C.c_int, i64, C.c_int]
+            L.orc_next_level.restype = C.c_int
+            L.orc_hermite_init.argtypes = [i64, vp, vp, vp, d, d, d, C.c_int, C.c_int,
+                                           vp, vp, vp, vp]
+            L.orc_block_step.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, d, d, d,
+                                         C.c_int, C.c_int, C.c_int, i64, i64, vp,
+                                         vp, vp, vp]
+            L.orc_block_step.restype = i64
+            L.orc_hermite_shared.argtypes = [i64, vp, vp, vp, vp, vp, d, d, C.c_int, i64]
+            L.orc_acc.argtypes = [i64, vp, vp, d, d, vp]
+            L.orc_leapfrog.argtypes = [i64, vp, vp, vp, d, d, d, i64]
+            L.orc_acc_vjp.argtypes = [i64, vp, vp, d, d, vp, vp, vp]
+            L.orc_leapfrog_loss_grad.argtypes = [i64, vp, vp, vp, vp, d, d, d, i64,
+                                                 vp, vp, vp]
+            L.orc_leapfrog_loss_grad.restype = d
+            _lib = L
+    return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def force_jerk(m, x, v, eps, G=1.0, idx=None):
+    """Acceleration and jerk on particles ``idx`` (all when None) from all
+    others.  Returns (acc, jerk) of shape (n_i, 3)."""
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    if idx is None:
+        n_i, ip = n, None
+    else:
+        ip = np.ascontiguousarray(idx, dtype=np.int64)
+        n_i = ip.shape[0]
+    acc = np.zeros((n_i, 3))
+    jerk = np.zeros((n_i, 3))
+    lib().orc_force_jerk(n, _p(m), _p(x), _p(v), float(G), float(eps), n_i, _p(ip),
+                         _p(acc), _p(jerk))
+    return acc, jerk
+
+
+def acc(m, x, eps, G=1.0):
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    out = np.zeros((n, 3))
+    lib().orc_acc(n, _p(m), _p(x), float(G), float(eps), _p(out))
+    return out
+
+
+def energy(m, x, v, eps, G=1.0):
+    """Returns (K, W, E) with the softened pair potential."""
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    k = np.zeros(1)
+    w = np.zeros(1)
+    lib().orc_energy(n, _p(m), _p(x), _p(v), float(G), float(eps), _p(k), _p(w))
+    return float(k[0]), float(w[0]), float(k[0] + w[0])
+
+
+def predict(x, v, a, jk, dt):
+    x, v, a, jk = (_f64(q).reshape(-1, 3) for q in (x, v, a, jk))
+    n = x.shape[0]
+    dt = np.broadcast_to(np.asarray(dt, np.float64), (n,)).copy()
+    xp = np.zeros_like(x)
+    vp = np.zeros_like(v)
+    lib().orc_predict(n, _p(x), _p(v), _p(a), _p(jk), _p(dt), _p(xp), _p(vp))
+    return xp, vp
+
+
+def aarseth_dt(a, jk, a2, a3, eta):
+    a, jk, a2, a3 = (_f64(q) for q in (a, jk, a2, a3))
+    return lib().orc_aarseth_dt(_p(a), _p(jk), _p(a2), _p(a3), float(eta))
+
+
+def level_from_dt(dt, lev_min=3, lev_max=20):
+    cl = np.zeros(1, dtype=np.int32)
+    lev = lib().orc_level_from_dt(float(dt), int(lev_min), int(lev_max), _p(cl))
+    return lev, bool(cl[0])
+
+
+def next_level(lev_old, lev_want, t_new, lev_min=3):
+    return lib().orc_next_level(int(lev_old), int(lev_want), int(t_new), int(lev_min))
+
+
+class HermiteState:
+    """FP64 state of a Hermite-4 integration in the oracle (arrays owned by
+    Python).  ``block_levels`` selects the Aarseth block-step scheme; with it
+    off every particle keeps its level (shared fixed dt = 2^-lev)."""
+
+    def __init__(self, m, x, v, eps, G=1.0, eta=0.01, eta_start=0.01, lev_min=3,
+                 lev_max=20, block_levels=True, shared_lev=None):
+        self.m = _f64(m).copy()
+        n = self.n = self.m.shape[0]
+        self.x = _f64(x, (n, 3)).copy()
+        self.v = _f64(v, (n, 3)).copy()
+        self.a = np.zeros((n, 3))
+        self.jk = np.zeros((n, 3))
+        self.lev = np.zeros(n, dtype=np.int32)
+        self.t = np.zeros(n, dtype=np.int64)
+        self.G, self.eps, self.eta = float(G), float(eps), float(eta)
+        self.lev_min, self.lev_max = int(lev_min), int(lev_max)
+        self.block_levels = bool(block_levels)
+        self.n_clamped = np.zeros(1, dtype=np.int64)
+        lib().orc_hermite_init(n, _p(self.m), _p(self.x), _p(self.v), self.G, self.eps,
+                               float(eta_start), self.lev_min, self.lev_max, _p(self.a),
+                               _p(self.jk), _p(self.lev), _p(self.t))
+        if shared_lev is not None:
+            self.lev[:] = int(shared_lev)
+        self._act = np.zeros(n, dtype=np.int64)
+
+    def step(self, replay=None):
+        """One block step; ``replay`` = (t_next_tick, active indices) follows a
+        given schedule.  Returns (t_next_tick, active indices)."""
+        tn = np.zeros(1, dtype=np.int64)
+        if replay is None:
+            rt, rn, ra = 0, -1, None
+        else:
+            rt = int(replay[0])
+            ra = np.ascontiguousarray(replay[1], dtype=np.int64)
+            rn = ra.shape[0]
+        n_act = lib().orc_block_step(
+            self.n, _p(self.m), _p(self.x), _p(self.v), _p(self.a), _p(self.jk),
+            _p(self.t), _p(self.lev), self.G, self.eps, self.eta, self.lev_min,
+            self.lev_max, int(self.block_levels), rt, rn, _p(ra), _p(tn), _p(self._act),
+            _p(self.n_clamped))
+        return int(tn[0]), self._act[:n_act].copy()
+
+    def time(self) -> float:
+        return float(self.t.max()) * 2.0 ** (-TICKS_LOG2)
+
+    def energy(self):
+        return energy(self.m, self.x, self.v, self.eps, self.G)
+
+
+def hermite_shared(m, x, v, eps, lev, nsteps, G=1.0):
+    """Shared fixed dt = 2^-lev; returns (x, v, a, jerk) after nsteps."""
+    st = HermiteState(m, x, v, eps, G=G, block_levels=False, shared_lev=lev)
+    for _ in range(nsteps):
+        st.step()
+    return st.x, st.v, st.a, st.jk
+
+
+def leapfrog(m, x, v, eps, dt, nsteps, G=1.0):
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3)).copy()
+    v = _f64(v, (n, 3)).copy()
+    lib().orc_leapfrog(n, _p(m), _p(x), _p(v), float(G), float(eps), float(dt), int(nsteps))
+    return x, v
+
+
+def acc_vjp(m, x, g, eps, G=1.0):
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    g = _f64(g, (n, 3))
+    gx = np.zeros((n, 3))
+    gm = np.zeros(n)
+    lib().orc_acc_vjp(n, _p(m), _p(x), float(G), float(eps), _p(g), _p(gx), _p(gm))
+    return gx, gm
+
+
+def leapfrog_loss_grad(m, x0, v0, y, eps, dt, nsteps, G=1.0):
+    """Returns (L, dL/dx0, dL/dv0, dL/dm) for L = sum |x(T) - y|^2."""
+    m = _f64(m)
+    n = m.shape[0]
+    x0 = _f64(x0, (n, 3))
+    v0 = _f64(v0, (n, 3))
+    y = _f64(y, (n, 3))
+    gx = np.zeros((n, 3))
+    gv = np.zeros((n, 3))
+    gm = np.zeros(n)
+    L = lib().orc_leapfrog_loss_grad(n, _p(m), _p(x0), _p(v0), _p(y), float(G), float(eps),
+                                     float(dt), int(nsteps), _p(gx), _p(gv), _p(gm))
+    return L, gx, gv, gm
