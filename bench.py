@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: G pair-interactions/s of the direct-summation
+force + jerk hot path at N = 1,048,576.
+
+Workload: a King W0 = 7 cluster (seeded, equal masses, Henon units),
+eps = 1e-4, advanced by 4th-order Hermite steps with a shared step
+dt = 2^-10 so that every particle is active in every step.  One timed step
+is one pass of the whole path: block scheduling, FP64 predictor (writing
+the split-precision j-records), force + jerk of all N active particles
+against all N, FP64 corrector.  An interaction is one (i, j) pair
+evaluation; a step evaluates N^2 of them.
+
+Output: one JSON line (rank 0).  `value` is whole-job interactions/s from
+CUDA events on the library's stream with inputs resident in HBM; `e2e` is
+the same through the C ABI with host buffers (state uploaded and downloaded
+every step); `roofline` puts the force kernel's FP32 arithmetic against the
+FP32 peak; `cpu_baseline` times the FP64 oracle on the host cores on a
+bounded sample.  With `--impl reference` the oracle alone is timed.
+
+Multi-GPU (torchrun): every rank integrates its own independent cluster
+(seed 1003 + rank); no collective is on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0909_0879_gb300 import ics, metrics  # noqa: E402
+
+N_DEFAULT = 1 << 20
+EPS = 1e-4
+W0 = 7.0
+LEV_SHARED = 10
+METRIC = "G pair-interactions/s (acc+jerk, N=1M)"
+UNIT = "Ginteractions/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=6)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="ds", choices=["ds", "fp32"])
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--no-energy", action="store_true", help="skip the FP64 energy check")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--variant", type=int, default=-1)
+    p.add_argument("--grid", type=int, default=0)
+    p.add_argument("--sweep", action="store_true",
+                   help="also time single evaluations at active fractions 2^-10..1")
+    return p.parse_args()
+
+
+def workload_name(n):
+    return f"king_w0_7_n{n}_eps1e-4_hermite_shared_dt2^-{LEV_SHARED}_all_active"
+
+
+# ------------------------------------------------------------------ clocks
+
+REASON_BITS = {
+    0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+    0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+    0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+    0x100: "display_clock_setting",
+}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.gpu),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [q.strip() for q in ln.split(",")]
+            if len(parts) < 4:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[3], 16) if parts[3].startswith("0x") else int(parts[3])
+            except ValueError:
+                continue
+            for b, name in REASON_BITS.items():
+                if bits & b and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- roofline
+
+
+def force_traffic_from_profile(n):
+    """DRAM bytes per force launch from the committed ncu summary, if it was
+    taken on the current force-kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "force_jerk_ds_traffic.md")
+    src = os.path.join(ROOT, "paper_0909_0879_gb300", "csrc", "nb_force.cu")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    b = re.search(r"dram_bytes_per_launch_at_n1048576:\s*([0-9.eE+]+)", txt)
+    if not h or not b:
+        return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if cur != h.group(1) or n != N_DEFAULT:
+        return None
+    return float(b.group(1))
+
+
+def peak_info(num_sms):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = 2070.0
+    src = "fallback max SM clock 2070 MHz"
+    if os.path.exists(path):
+        try:
+            mp = json.load(open(path))
+            if mp.get("sm_max_mhz"):
+                sm_max = float(mp["sm_max_mhz"])
+                src = "sm_max_mhz from MEASURED_PEAKS.json"
+        except Exception:
+            pass
+    return metrics.fp32_peak_tflops(num_sms, sm_max), sm_max, src
+
+
+# ------------------------------------------------------------- CPU leg
+
+
+def cpu_baseline(m, x, v, n, seconds):
+    """Time the FP64 oracle's force + jerk for a bounded sample of
+    i-particles against all n j-particles on every host core."""
+    from oracle import oracle as O
+
+    O.build()
+    cores = O.max_threads()
+    rng = np.random.default_rng(7)
+    probe = np.sort(rng.choice(n, 32, replace=False))
+    t0 = time.perf_counter()
+    O.force_jerk(m, x, v, EPS, idx=probe)
+    dt = time.perf_counter() - t0
+    rate = 32 * n / max(dt, 1e-6)
+    ns = int(min(n, max(64, rate * seconds / n)))
+    ns = max(cores, ns - ns % cores)
+    sample = np.sort(rng.choice(n, ns, replace=False))
+    t0 = time.perf_counter()
+    O.force_jerk(m, x, v, EPS, idx=sample)
+    dt = time.perf_counter() - t0
+    return {"value": ns * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{ns} random i-particles x {n} j-particles, FP64 acc+jerk, "
+                      f"{dt:.1f} s on {cores} OpenMP threads",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n = args.n
+    m, x, v = ics.king(n, W0, 1003)
+    steps = []
+    cb = None
+    per = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(m, x, v, n, per)
+        if s >= args.warmup:
+            steps.append(r)
+        cb = r
+    vals = [r["value"] for r in steps]
+    val = float(np.mean(vals))
+    tot_s = sum(r["seconds"] for r in steps)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * tot_s / len(steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(n), "n": n, "eps": EPS,
+                      "note": "FP64 CPU oracle; each step a bounded i-sample of one "
+                              "force+jerk evaluation against all N"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU leg
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_0909_0879_gb300 import _lib
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    m, x, v = ics.king(n, W0, 1003 + rank)
+    stream = torch.cuda.current_stream(dev)
+    s = _lib.NBody(m, x, v, eps=EPS, precision=args.precision, block_steps=False,
+                   lev_shared=LEV_SHARED, stream=stream)
+    if args.variant >= 0 or args.grid > 0:
+        s.set_force_variant(args.variant, args.grid)
+    props = torch.cuda.get_device_properties(dev)
+    num_sms = props.multi_processor_count
+
+    E0 = None
+    if not args.no_energy:
+        E0 = s.energy()[2]
+    # L2 flush buffer: larger than the 129 MB L2
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step(record):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        flush.zero_()
+        ev[0].record(stream)
+        t, na = s.next_block()
+        s.predict(t)
+        ev[1].record(stream)
+        s.force_jerk_dev(None, na, None, None)
+        ev[2].record(stream)
+        s.correct(t)
+        ev[3].record(stream)
+        return ev, na
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    l0 = s.launch_count()
+    evs = []
+    inter = 0
+    for _ in range(args.steps):
+        ev, na = one_step(True)
+        evs.append(ev)
+        inter += na * n
+    torch.cuda.synchronize(dev)
+    launches = s.launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    force_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+        it = torch.tensor([inter], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(it, op=torch.distributed.ReduceOp.SUM)
+        inter_all = float(it.item())
+    else:
+        inter_all = float(inter)
+    value = inter_all / t_total / 1e9
+
+    dE = None
+    if E0 is not None:
+        E1 = s.energy()[2]
+        dE = abs(E1 - E0) / abs(E0)
+
+    # end to end through the C ABI with host buffers: upload state, step,
+    # download state, every step
+    st = s.get_state()
+    e2e_steps = max(1, args.e2e_steps)
+    h2d = sum(a.nbytes for a in st.values())
+    d2h = h2d
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(st)
+        s.step()
+        st = s.get_state()
+    torch.cuda.synchronize(dev)
+    e2e_t = time.perf_counter() - t0
+    e2e_val = e2e_steps * n * n / e2e_t / 1e9
+    if world > 1:
+        et = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(et, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = world * e2e_steps * n * n / float(et.item()) / 1e9
+
+    sweep = None
+    if args.sweep:
+        sweep = []
+        for k in range(10, -1, -1):
+            na = max(1, n >> k)
+            idx = torch.from_numpy(ics.random_active_subset(n, na, 3000 + k)).to(dev)
+            acc = torch.empty((na, 3), dtype=torch.float64, device=dev)
+            jrk = torch.empty_like(acc)
+            s.force_jerk_dev(idx, na, acc, jrk)
+            ts = []
+            for _ in range(3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.force_jerk_dev(idx, na, acc, jrk)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1))
+            ms = float(np.median(ts))
+            sweep.append({"active_fraction": f"2^-{k}", "n_act": na, "ms": ms,
+                          "ginter_s": na * n / ms / 1e6})
+
+    if rank != 0:
+        s.close()
+        return 0
+
+    force_s = float(np.mean(force_ms)) / 1e3
+    achieved = metrics.FLOPS_PER_INTERACTION * n * n / force_s / 1e12
+    peak, sm_max, peak_src = peak_info(num_sms)
+    traffic = force_traffic_from_profile(n) if args.precision == "ds" else None
+    clk_mhz = clocks.get("sm_mhz") if clocks else None
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(m, x, v, n, args.cpu_seconds)
+        cpu.pop("seconds", None)
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32-ds" if args.precision == "ds" else "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": workload_name(n), "n": n, "eps": EPS, "W0": W0,
+            "integrator": "hermite4 shared dt, all active", "precision": args.precision,
+            "parallelism": f"replicas x{world} (independent clusters per GPU)",
+            "l2": "flushed between timed steps (256 MB write outside the events)",
+            "seed": "1003 + rank",
+        },
+        "dE_over_E": dE,
+        "dE_note": f"FP64 GPU energy before warm-up and after {args.warmup + args.steps} steps "
+                   f"of dt 2^-{LEV_SHARED}" if dE is not None else None,
+        "roofline": {
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": traffic,
+            "kernel": "force_jerk_kernel (+ fix-up) per force evaluation, CUDA events on the "
+                      "library stream",
+            "flops_per_interaction": metrics.FLOPS_PER_INTERACTION,
+            "peak_def": f"{num_sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src})",
+            "frac_at_measured_clock": (achieved / metrics.fp32_peak_tflops(num_sms, clk_mhz)
+                                       if clk_mhz else None),
+            "frac_60flop_convention": achieved / metrics.FLOPS_PER_INTERACTION
+            * metrics.FLOPS_PER_INTERACTION_CONVENTION / peak,
+        },
+        "force_ms": float(np.mean(force_ms)),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "note": "nb_set_state + nb_step + nb_get_state with host arrays, wall clock"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if sweep is not None:
+        out["sweep"] = sweep
+    print(json.dumps(out), flush=True)
+    s.close()
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * nbody.h -- C ABI of the GB300 direct-summation N-body library (libnbody.so).
+ *
+ * The library evaluates the Plummer-softened Newtonian acceleration
+ *   a_i = G sum_{j != i} m_j d_ij / (|d_ij|^2 + eps^2)^(3/2),  d_ij = x_j - x_i
+ * (paper eq. 1, Sec. 2, with the softening of Sec. 3) and its time
+ * derivative, the jerk
+ *   j_i = G sum_{j != i} m_j [ w_ij / s^3 - 3 (d_ij . w_ij) d_ij / s^5 ],
+ *   w_ij = v_j - v_i, s^2 = |d_ij|^2 + eps^2
+ * for a list of active i-particles against all j-particles, on one GPU, and
+ * advances the system with the 4th-order Hermite predictor-corrector and
+ * power-of-two block time steps (the paper's "individual time steps",
+ * Sec. 2, strategy (ii); the Hermite scheme itself is Makino & Aarseth 1992
+ * and is not printed in the paper).
+ *
+ * Conventions (every entry point):
+ *  - Every call returns nb_status; NB_OK is 0.  On error a message is kept
+ *    per host thread and returned by nb_last_error().  No C++ exception
+ *    crosses this interface.
+ *  - Host pointers are owned by the caller and are only read or written
+ *    during the call.  Device pointers (the *_dev entry points) are owned by
+ *    the caller; the library never frees memory it did not allocate.
+ *  - Vectors are (n, 3) row-major float64 arrays: x[3*i + c].
+ *  - Time is kept as integer ticks of 2^-20; time arguments given as double
+ *    must be exact multiples of 2^-20.
+ *  - Work is queued on the stream given in nb_config.stream (NULL = the
+ *    legacy default stream).  Calls that return host data synchronise that
+ *    stream (with a host watchdog, see nb_config.sync_timeout_ms).
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef NBODY_GB300_H
+#define NBODY_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx; /* opaque, library-owned */
+
+typedef enum {
+  NB_OK = 0,
+  NB_ERR_INVALID_ARG = 1, /* bad size, NULL pointer, non-finite input, bad time */
+  NB_ERR_STATE = 2,       /* call out of order (e.g. correct before force) */
+  NB_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  NB_ERR_OOM = 4,         /* device allocation failed (or the test cap hit) */
+  NB_ERR_NUMERIC = 5,     /* a result was not finite */
+  NB_ERR_TIMEOUT = 6,     /* the host watchdog gave up waiting for the GPU */
+  NB_ERR_DEVICE = 7       /* a kernel's bounded wait ran out; see message */
+} nb_status;
+
+typedef enum { NB_FP32 = 0, NB_DS = 1 } nb_precision;
+
+/* Integration and arithmetic settings.  Fill with nb_default_config(). */
+typedef struct {
+  double G;          /* gravitational constant (paper: G = 1, Sec. 3) */
+  double eps;        /* Plummer softening length, >= 0 (paper Sec. 3).  With
+                        eps == 0 the kernels mask the i == j term. */
+  double eta;        /* Aarseth accuracy parameter for block steps */
+  double eta_start;  /* initial step: dt0 = eta_start |a| / |j| */
+  int32_t lev_min;   /* largest step 2^-lev_min; 0 <= lev_min <= lev_max */
+  int32_t lev_max;   /* smallest step 2^-lev_max; lev_max <= 20 */
+  int32_t precision; /* nb_precision: pair arithmetic and accumulation */
+  int32_t block_steps; /* 1: Aarseth block steps; 0: shared dt = 2^-lev_shared */
+  int32_t lev_shared;  /* shared step level when block_steps == 0 */
+  int32_t sync_timeout_ms; /* host watchdog per synchronisation; <= 0: 600 s */
+  void *stream;      /* cudaStream_t to queue work on; NULL = default stream */
+} nb_config;
+
+/* Defaults: G = 1, eps = 1e-3, eta = 0.01, eta_start = 0.01, lev 3..20,
+ * NB_DS, block steps on, lev_shared = 8, watchdog 600 s, default stream. */
+void nb_default_config(nb_config *cfg);
+
+/* Create a context holding n particles (1 <= n <= 2^30).  m (n), x and v
+ * ((n,3)) are host arrays copied to the device.  Evaluates a and j at t = 0
+ * for every particle and sets the initial step levels (block steps:
+ * dt0 = eta_start |a|/|j| quantised down to a power of two; shared: lev_shared).
+ * Errors: NB_ERR_INVALID_ARG (n out of range, NULL, non-finite, bad config),
+ * NB_ERR_OOM, NB_ERR_CUDA.  On error *out is set to NULL. */
+nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
+                  const double *v, const nb_config *cfg);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+void nb_destroy(nb_ctx *ctx);
+
+/* Block scheduling (paper Sec. 2, individual time steps): t_next =
+ * min_i (t_i + dt_i); the active list becomes every i with t_i + dt_i ==
+ * t_next, in ascending index order (deterministic).  Returns t_next (time
+ * units) and the number of active particles; synchronises the stream. */
+nb_status nb_next_block(nb_ctx *ctx, double *t_next, int64_t *n_active);
+
+/* Predict every particle to time t (Hermite predictor, FP64):
+ *   x_p = x + v dt + a dt^2/2 + j dt^3/6, v_p = v + a dt + j dt^2/2,
+ *   dt = t - t_i, and write the j-records the force kernels read (FP32 or
+ * double-single split positions).  Asynchronous.  t must be a tick multiple
+ * and not earlier than any t_i (NB_ERR_INVALID_ARG). */
+nb_status nb_predict(nb_ctx *ctx, double t);
+
+/* Acceleration and jerk (eq. 1 and its time derivative) on the particles
+ * idx[0..n_idx) from all n particles at the last predicted state.
+ * idx == NULL: the current active list (n_idx must equal its length, or be
+ * negative to take it); the result is then also kept for nb_correct.
+ * acc/jerk: host (n_idx,3) outputs, either may be NULL.  Synchronises.
+ * Errors: NB_ERR_INVALID_ARG (index out of range, n_idx mismatch),
+ * NB_ERR_STATE (no prediction yet), NB_ERR_NUMERIC (non-finite result). */
+nb_status nb_force_jerk(nb_ctx *ctx, const int32_t *idx, int64_t n_idx,
+                        double *acc, double *jerk);
+
+/* Same on device pointers, asynchronous on the context stream: d_idx
+ * (int32, n_idx entries, each in [0, n); NULL = the active list as above),
+ * d_acc / d_jerk (float64, (n_idx,3); may be NULL when idx == NULL, in
+ * which case the result is kept only for nb_correct).  Indices are not
+ * range-checked on the device: an out-of-range index is undefined behaviour. */
+nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *d_idx, int64_t n_idx,
+                            double *d_acc, double *d_jerk);
+
+/* Hermite corrector (Makino & Aarseth 1992) for the active list at time t
+ * (must equal the t_next of the current block and follow a force
+ * evaluation of the active list at that time), then the Aarseth step
+ * criterion and its power-of-two quantisation (block steps: shrink freely,
+ * grow by one level only on a multiple of the doubled step).  Asynchronous. */
+nb_status nb_correct(nb_ctx *ctx, double t);
+
+/* One full block step: nb_next_block, nb_predict, nb_force_jerk_dev on the
+ * active list, nb_correct.  Returns t_next and the active count. */
+nb_status nb_step(nb_ctx *ctx, double *t_next, int64_t *n_active);
+
+/* Energy of the current (synchronised) state in FP64 on the GPU:
+ * K = 1/2 sum m v^2, W = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)
+ * (the softened pair potential consistent with the force).  Uses the
+ * particles' own stored x, v (not predicted).  Synchronises. */
+nb_status nb_energy(nb_ctx *ctx, double *kin, double *pot, double *tot);
+
+/* Copy the integrator state to host arrays (any may be NULL):
+ * x, v, a, jerk (n,3); t_tick (n) int64 ticks of 2^-20; lev (n) int32.
+ * Synchronises.  Together with nb_set_state this is checkpoint/resume:
+ * a run continued from a copied state is bitwise identical. */
+nb_status nb_get_state(nb_ctx *ctx, double *x, double *v, double *a,
+                       double *jerk, int64_t *t_tick, int32_t *lev);
+
+/* Overwrite the state (all six arrays required; masses are kept).
+ * Validates finiteness, 0 <= lev <= 20 and t_tick a multiple of 2^(20-lev).
+ * The next call must be nb_next_block or nb_predict. */
+nb_status nb_set_state(nb_ctx *ctx, const double *x, const double *v,
+                       const double *a, const double *jerk,
+                       const int64_t *t_tick, const int32_t *lev);
+
+/* Copy the current active list (ascending int32 indices) into idx, which
+ * holds cap entries; *n_active receives its length.  Synchronises. */
+nb_status nb_get_active(nb_ctx *ctx, int32_t *idx, int64_t cap,
+                        int64_t *n_active);
+
+/* Counters: block steps taken, interactions evaluated (n_act * n summed
+ * over force evaluations), and particles whose step criterion fell below
+ * 2^-lev_max and were clamped.  Synchronises. */
+nb_status nb_get_counters(nb_ctx *ctx, int64_t *n_blocks,
+                          int64_t *n_interactions, int64_t *n_clamped);
+
+/* Wait for all queued work (host watchdog) and report device-side errors. */
+nb_status nb_sync(nb_ctx *ctx);
+
+/* Number of kernel launches the library has queued on this context. */
+int64_t nb_launch_count(const nb_ctx *ctx);
+
+/* Force-kernel shape for the next force evaluations (autotuning):
+ * variant indexes the compiled shape table (see nb_variant_info); -1
+ * restores the built-in choice by active-list length.  grid_ctas > 0 caps
+ * the persistent grid.  Errors: NB_ERR_INVALID_ARG for an unknown variant or
+ * one whose precision differs from the context's. */
+nb_status nb_set_force_variant(nb_ctx *ctx, int32_t variant, int32_t grid_ctas);
+
+/* Describe compiled force-kernel variant v: precision, i-particles per
+ * thread, threads per i-particle, threads per CTA.  NB_ERR_INVALID_ARG past
+ * the end of the table. */
+nb_status nb_variant_info(int32_t v, int32_t *precision, int32_t *ipt,
+                          int32_t *tpi, int32_t *threads);
+
+/* Host-side fault injection for tests: kind 1 makes the next device
+ * allocation of nb_init fail with NB_ERR_OOM (process-wide, one shot);
+ * kind 2 makes the next synchronisation of ctx report NB_ERR_TIMEOUT
+ * (ctx required).  No GPU fault is ever caused. */
+nb_status nb_debug_inject(nb_ctx *ctx, int32_t kind);
+
+const char *nb_status_string(nb_status s);
+const char *nb_last_error(void); /* message of the last error on this thread */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_GB300_H */

@@ -1,0 +1,306 @@
+"""ctypes binding of libnbody.so (the C ABI in include/nbody.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  The binding fails loudly when the library has not
+been built; there is no CPU fallback.  Device-pointer calls accept any
+object with ``data_ptr()`` (torch tensors) or a raw integer address.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NB_OK, NB_ERR_INVALID_ARG, NB_ERR_STATE, NB_ERR_CUDA = 0, 1, 2, 3
+NB_ERR_OOM, NB_ERR_NUMERIC, NB_ERR_TIMEOUT, NB_ERR_DEVICE = 4, 5, 6, 7
+NB_FP32, NB_DS = 0, 1
+TICKS_LOG2 = 20
+
+
+class NBodyError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("G", C.c_double),
+        ("eps", C.c_double),
+        ("eta", C.c_double),
+        ("eta_start", C.c_double),
+        ("lev_min", C.c_int32),
+        ("lev_max", C.c_int32),
+        ("precision", C.c_int32),
+        ("block_steps", C.c_int32),
+        ("lev_shared", C.c_int32),
+        ("sync_timeout_ms", C.c_int32),
+        ("stream", C.c_void_p),
+    ]
+
+
+# (name, restype, argtypes) for every entry point in include/nbody.h
+_vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+_P = C.POINTER
+SIGNATURES = [
+    ("nb_default_config", None, [_P(Config)]),
+    ("nb_init", C.c_int, [_P(_vp), _i64, _vp, _vp, _vp, _P(Config)]),
+    ("nb_destroy", None, [_vp]),
+    ("nb_next_block", C.c_int, [_vp, _P(_d), _P(_i64)]),
+    ("nb_predict", C.c_int, [_vp, _d]),
+    ("nb_force_jerk", C.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    ("nb_force_jerk_dev", C.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    ("nb_correct", C.c_int, [_vp, _d]),
+    ("nb_step", C.c_int, [_vp, _P(_d), _P(_i64)]),
+    ("nb_energy", C.c_int, [_vp, _P(_d), _P(_d), _P(_d)]),
+    ("nb_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_set_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("nb_get_active", C.c_int, [_vp, _vp, _i64, _P(_i64)]),
+    ("nb_get_counters", C.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)]),
+    ("nb_sync", C.c_int, [_vp]),
+    ("nb_launch_count", _i64, [_vp]),
+    ("nb_set_force_variant", C.c_int, [_vp, _i32, _i32]),
+    ("nb_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
+    ("nb_debug_inject", C.c_int, [_vp, _i32]),
+    ("nb_status_string", C.c_char_p, [C.c_int]),
+    ("nb_last_error", C.c_char_p, []),
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libnbody.so (building it first only when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(
+                f"libnbody.so is not built ({path}); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        _build.build()
+    L = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != NB_OK:
+        L = load()
+        raise NBodyError(status, L.nb_last_error().decode(errors="replace"))
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(a)}")
+
+
+def _f64(a, shape):
+    return np.ascontiguousarray(a, dtype=np.float64).reshape(shape)
+
+
+def variant_info(v: int):
+    L = load()
+    p, i, t, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(L.nb_variant_info(v, C.byref(p), C.byref(i), C.byref(t), C.byref(n)))
+    return {"precision": p.value, "ipt": i.value, "tpi": t.value, "threads": n.value}
+
+
+def num_variants() -> int:
+    v = 0
+    L = load()
+    while L.nb_variant_info(v, None, None, None, None) == NB_OK:
+        v += 1
+    return v
+
+
+def default_config() -> Config:
+    cfg = Config()
+    load().nb_default_config(C.byref(cfg))
+    return cfg
+
+
+class NBody:
+    """A direct-summation N-body system on the GPU (one libnbody context).
+
+    Host arrays are float64 numpy arrays: m (n,), x and v (n, 3).
+    """
+
+    def __init__(self, m, x, v, *, G=1.0, eps=1e-3, eta=0.01, eta_start=0.01,
+                 lev_min=3, lev_max=20, precision="ds", block_steps=True,
+                 lev_shared=8, stream=None, sync_timeout_ms=0):
+        L = load()
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        n = m.shape[0]
+        x = _f64(x, (n, 3))
+        v = _f64(v, (n, 3))
+        cfg = default_config()
+        cfg.G, cfg.eps, cfg.eta, cfg.eta_start = float(G), float(eps), float(eta), float(eta_start)
+        cfg.lev_min, cfg.lev_max = int(lev_min), int(lev_max)
+        cfg.precision = NB_DS if precision in ("ds", NB_DS) else NB_FP32
+        cfg.block_steps = 1 if block_steps else 0
+        cfg.lev_shared = int(lev_shared)
+        cfg.sync_timeout_ms = int(sync_timeout_ms)
+        cfg.stream = _ptr(stream) if stream is not None and not isinstance(stream, int) else stream
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            cfg.stream = stream.cuda_stream
+        self.cfg = cfg
+        self.n = n
+        h = C.c_void_p()
+        _check(L.nb_init(C.byref(h), n, m.ctypes.data, x.ctypes.data, v.ctypes.data,
+                         C.byref(cfg)))
+        self._h = h
+        self._L = L
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.nb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- integrator
+    def next_block(self):
+        t, na = C.c_double(), C.c_int64()
+        _check(self._L.nb_next_block(self._h, C.byref(t), C.byref(na)))
+        return t.value, na.value
+
+    def predict(self, t: float):
+        _check(self._L.nb_predict(self._h, float(t)))
+
+    def force_jerk(self, idx=None, n_idx: int = -1):
+        """Host path: returns (acc, jerk) numpy arrays of shape (n_idx, 3)."""
+        if idx is None:
+            if n_idx < 0:
+                _, cnt = self.active_count()
+            else:
+                cnt = n_idx
+            acc = np.zeros((cnt, 3))
+            jerk = np.zeros((cnt, 3))
+            _check(self._L.nb_force_jerk(self._h, None, cnt, acc.ctypes.data, jerk.ctypes.data))
+            return acc, jerk
+        ii = np.ascontiguousarray(idx, dtype=np.int32)
+        acc = np.zeros((ii.shape[0], 3))
+        jerk = np.zeros((ii.shape[0], 3))
+        _check(self._L.nb_force_jerk(self._h, ii.ctypes.data if ii.size else None, ii.shape[0],
+                                     acc.ctypes.data, jerk.ctypes.data))
+        return acc, jerk
+
+    def force_jerk_dev(self, d_idx, n_idx: int, d_acc, d_jerk):
+        """Device path, asynchronous on the context stream."""
+        _check(self._L.nb_force_jerk_dev(self._h, _ptr(d_idx), int(n_idx), _ptr(d_acc),
+                                         _ptr(d_jerk)))
+
+    def correct(self, t: float):
+        _check(self._L.nb_correct(self._h, float(t)))
+
+    def step(self):
+        t, na = C.c_double(), C.c_int64()
+        _check(self._L.nb_step(self._h, C.byref(t), C.byref(na)))
+        return t.value, na.value
+
+    def run_until(self, t_end: float):
+        """Block steps until every particle has reached t_end (a tick multiple
+        reachable by the largest step).  Returns the number of block steps."""
+        steps = 0
+        tick_end = int(round(t_end * 2**TICKS_LOG2))
+        while True:
+            st = self.get_state(want=("t_tick", "lev"))
+            due = st["t_tick"] + (1 << (TICKS_LOG2 - st["lev"].astype(np.int64)))
+            if due.min() > tick_end:
+                return steps
+            self.step()
+            steps += 1
+
+    def energy(self):
+        k, w, e = C.c_double(), C.c_double(), C.c_double()
+        _check(self._L.nb_energy(self._h, C.byref(k), C.byref(w), C.byref(e)))
+        return k.value, w.value, e.value
+
+    def get_state(self, want=("x", "v", "a", "jerk", "t_tick", "lev")):
+        n = self.n
+        out = {}
+        bufs = {}
+        for key in ("x", "v", "a", "jerk"):
+            if key in want:
+                bufs[key] = out[key] = np.zeros((n, 3))
+        if "t_tick" in want:
+            bufs["t_tick"] = out["t_tick"] = np.zeros(n, dtype=np.int64)
+        if "lev" in want:
+            bufs["lev"] = out["lev"] = np.zeros(n, dtype=np.int32)
+        p = {k: (bufs[k].ctypes.data if k in bufs else None)
+             for k in ("x", "v", "a", "jerk", "t_tick", "lev")}
+        _check(self._L.nb_get_state(self._h, p["x"], p["v"], p["a"], p["jerk"], p["t_tick"],
+                                    p["lev"]))
+        return out
+
+    def set_state(self, st):
+        n = self.n
+        x = _f64(st["x"], (n, 3))
+        v = _f64(st["v"], (n, 3))
+        a = _f64(st["a"], (n, 3))
+        jk = _f64(st["jerk"], (n, 3))
+        t = np.ascontiguousarray(st["t_tick"], dtype=np.int64)
+        lev = np.ascontiguousarray(st["lev"], dtype=np.int32)
+        _check(self._L.nb_set_state(self._h, x.ctypes.data, v.ctypes.data, a.ctypes.data,
+                                    jk.ctypes.data, t.ctypes.data, lev.ctypes.data))
+
+    def active_count(self):
+        na = C.c_int64()
+        _check(self._L.nb_get_active(self._h, None, 0, C.byref(na)))
+        return None, na.value
+
+    def active(self):
+        _, cnt = self.active_count()
+        idx = np.zeros(max(cnt, 1), dtype=np.int32)
+        na = C.c_int64()
+        _check(self._L.nb_get_active(self._h, idx.ctypes.data, idx.shape[0], C.byref(na)))
+        return idx[: na.value].copy()
+
+    def counters(self):
+        b, i, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(self._L.nb_get_counters(self._h, C.byref(b), C.byref(i), C.byref(c)))
+        return {"blocks": b.value, "interactions": i.value, "clamped": c.value}
+
+    def sync(self):
+        _check(self._L.nb_sync(self._h))
+
+    def launch_count(self) -> int:
+        return int(self._L.nb_launch_count(self._h))
+
+    def set_force_variant(self, variant: int = -1, grid_ctas: int = 0):
+        _check(self._L.nb_set_force_variant(self._h, int(variant), int(grid_ctas)))
+
+    def inject(self, kind: int):
+        _check(self._L.nb_debug_inject(self._h, int(kind)))

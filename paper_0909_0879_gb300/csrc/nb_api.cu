@@ -1,0 +1,700 @@
+// C ABI of libnbody (declared in include/nbody.h): context, validation,
+// device memory, stream ordering, the host watchdog and error reporting.
+// Every step of the computation runs in the kernels of nb_force.cu and
+// nb_hermite.cu; this file only marshals.
+#include "../../include/nbody.h"
+#include "nb_internal.cuh"
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+using namespace nbi;
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<int> g_inject_oom{0};
+
+nb_status fail(nb_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define NB_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                  __LINE__);                                                 \
+  } while (0)
+
+bool finite_all(const double *p, int64_t cnt) {
+  for (int64_t i = 0; i < cnt; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+int64_t tick_of(double t, bool *ok) {
+  const double s = std::ldexp(t, kTicksLog2);
+  *ok = std::isfinite(t) && s >= 0.0 && s < 9.0e18 && std::floor(s) == s;
+  return *ok ? static_cast<int64_t>(s) : 0;
+}
+
+}  // namespace
+
+struct nb_ctx {
+  int64_t n = 0, n_pad = 0, n_jt = 0;
+  nb_config cfg{};
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  // device state, (n,3) row-major vectors
+  double *m = nullptr, *x = nullptr, *v = nullptr, *a = nullptr, *jk = nullptr;
+  double *a1 = nullptr, *j1 = nullptr;  // force output of the active list
+  int64_t *t_tick = nullptr;
+  int32_t *lev = nullptr;
+  float4 *jhi = nullptr, *jlo = nullptr, *jvel = nullptr;  // j-records
+  int32_t *act = nullptr;       // active list
+  int32_t *blk = nullptr;       // scheduling scratch
+  int64_t *scal = nullptr;      // [0] t_next ticks, [1] n_act
+  double *part = nullptr;       // force partial sums
+  size_t part_cap = 0;
+  double *red = nullptr;        // energy scratch
+  int *err = nullptr;           // device error word
+  unsigned long long *clamped = nullptr;
+  int32_t *qidx = nullptr;      // staged host index lists
+  int64_t qidx_cap = 0;
+  double *qout = nullptr;       // staged outputs for host queries
+  int64_t qout_cap = 0;
+  // pinned host mirror of small values
+  int64_t *h_scal = nullptr;    // [0] t_next [1] n_act [2] err [3] clamped
+  double *h_energy = nullptr;
+  cudaEvent_t ev = nullptr;
+  // host-side protocol state
+  int64_t t_pred = -1;          // tick of the last prediction
+  int64_t t_block = -1;         // t_next of the current block
+  int64_t n_act = 0;
+  bool have_block = false;
+  bool force_done = false;
+  int variant_override = -1;
+  int grid_cap = 0;
+  int64_t launches = 0, n_blocks = 0, interactions = 0;
+  bool inject_timeout = false;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+nb_status dev_alloc(nb_ctx *c, void **p, size_t bytes) {
+  if (g_inject_oom.exchange(0)) return fail(NB_ERR_OOM, "injected allocation failure");
+  const char *cap = std::getenv("NB_TEST_MAX_BYTES");
+  if (cap) {
+    if (bytes > static_cast<size_t>(std::strtoull(cap, nullptr, 10)))
+      return fail(NB_ERR_OOM, "allocation of %zu bytes exceeds NB_TEST_MAX_BYTES", bytes);
+  }
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA,
+                "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return NB_OK;
+}
+
+template <class T>
+nb_status dev_alloc_t(nb_ctx *c, T **p, size_t count) {
+  return dev_alloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+// Wait for the stream with a host watchdog, then read the device error word
+// and the small scalars into pinned memory.
+nb_status sync_ctx(nb_ctx *c) {
+  NB_CUDA(cudaMemcpyAsync(c->h_scal, c->scal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          c->stream));
+  NB_CUDA(cudaMemcpyAsync(&c->h_scal[2], c->err, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->stream));
+  NB_CUDA(cudaMemcpyAsync(&c->h_scal[3], c->clamped, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, c->stream));
+  NB_CUDA(cudaEventRecord(c->ev, c->stream));
+  if (c->inject_timeout) {
+    c->inject_timeout = false;
+    cudaEventSynchronize(c->ev);
+    return fail(NB_ERR_TIMEOUT, "injected watchdog timeout");
+  }
+  const int ms = c->cfg.sync_timeout_ms > 0 ? c->cfg.sync_timeout_ms : 600000;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(c->ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady)
+      return fail(NB_ERR_CUDA, "stream execution failed: %s", cudaGetErrorString(e));
+    const auto el = std::chrono::steady_clock::now() - t0;
+    if (std::chrono::duration_cast<std::chrono::milliseconds>(el).count() > ms)
+      return fail(NB_ERR_TIMEOUT, "GPU work did not finish within %d ms", ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  const int err = static_cast<int>(c->h_scal[2] & 0xffffffff);
+  if (err != 0)
+    return fail(NB_ERR_DEVICE, "a force kernel's bounded wait for a shared-memory tile ran out "
+                               "(device error word 0x%x)", err);
+  return NB_OK;
+}
+
+nb_status check_ctx(nb_ctx *c) {
+  if (!c) return fail(NB_ERR_INVALID_ARG, "null context");
+  return NB_OK;
+}
+
+int pick_variant(nb_ctx *c, int64_t n_i) {
+  if (c->variant_override >= 0) return c->variant_override;
+  return choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, n_i);
+}
+
+nb_status ensure_part(nb_ctx *c, size_t bytes) {
+  if (bytes <= c->part_cap) return NB_OK;
+  // Grows only when a tuning override asks for a larger grid than the one
+  // sized at init; never on the default path.
+  if (c->part) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->part);
+    for (auto &p : c->allocs)
+      if (p == c->part) p = nullptr;
+    c->part = nullptr;
+  }
+  nb_status s = dev_alloc(c, reinterpret_cast<void **>(&c->part), bytes);
+  if (s != NB_OK) return s;
+  c->part_cap = bytes;
+  return NB_OK;
+}
+
+// Queue one force evaluation of n_i i-particles (d_idx may be null for the
+// identity list) into d_acc / d_jerk.
+nb_status queue_force(nb_ctx *c, const int32_t *d_idx, int64_t n_i, double *d_acc,
+                      double *d_jerk) {
+  if (n_i == 0) return NB_OK;
+  const int v = pick_variant(c, n_i);
+  const int grid = force_grid(v, n_i, c->n_jt, c->num_sms, c->grid_cap);
+  nb_status s = ensure_part(c, part_bytes(v, grid));
+  if (s != NB_OK) return s;
+  ForceArgs A;
+  A.jhi = c->jhi;
+  A.jlo = c->jlo;
+  A.jvel = c->jvel;
+  A.n_jt = c->n_jt;
+  A.idx = d_idx;
+  A.n_i = n_i;
+  A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
+  A.G = c->cfg.G;
+  A.acc = d_acc;
+  A.jerk = d_jerk;
+  A.part = c->part;
+  A.err = c->err;
+  int nl = 0;
+  NB_CUDA(launch_force(v, A, grid, c->stream, &nl));
+  c->launches += nl;
+  c->interactions += n_i * c->n;
+  return NB_OK;
+}
+
+nb_status queue_predict(nb_ctx *c, int64_t tick) {
+  NB_CUDA(launch_predict(c->n, tick, c->x, c->v, c->a, c->jk, c->m, c->t_tick,
+                         c->cfg.precision, c->jhi, c->jlo, c->jvel, c->stream));
+  c->launches += 1;
+  c->t_pred = tick;
+  return NB_OK;
+}
+
+nb_status validate_config(const nb_config *cfg) {
+  if (!cfg) return fail(NB_ERR_INVALID_ARG, "null config");
+  if (!(std::isfinite(cfg->G) && cfg->G > 0))
+    return fail(NB_ERR_INVALID_ARG, "G must be finite and > 0");
+  if (!(std::isfinite(cfg->eps) && cfg->eps >= 0))
+    return fail(NB_ERR_INVALID_ARG, "eps must be finite and >= 0");
+  if (cfg->precision != NB_FP32 && cfg->precision != NB_DS)
+    return fail(NB_ERR_INVALID_ARG, "precision must be NB_FP32 or NB_DS");
+  if (cfg->lev_min < 0 || cfg->lev_max > kTicksLog2 || cfg->lev_min > cfg->lev_max)
+    return fail(NB_ERR_INVALID_ARG, "need 0 <= lev_min <= lev_max <= 20");
+  if (cfg->block_steps) {
+    if (!(std::isfinite(cfg->eta) && cfg->eta > 0) ||
+        !(std::isfinite(cfg->eta_start) && cfg->eta_start > 0))
+      return fail(NB_ERR_INVALID_ARG, "eta and eta_start must be finite and > 0");
+  } else if (cfg->lev_shared < 0 || cfg->lev_shared > kTicksLog2) {
+    return fail(NB_ERR_INVALID_ARG, "need 0 <= lev_shared <= 20");
+  }
+  return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nb_default_config(nb_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->G = 1.0;
+  cfg->eps = 1e-3;
+  cfg->eta = 0.01;
+  cfg->eta_start = 0.01;
+  cfg->lev_min = 3;
+  cfg->lev_max = 20;
+  cfg->precision = NB_DS;
+  cfg->block_steps = 1;
+  cfg->lev_shared = 8;
+  cfg->sync_timeout_ms = 600000;
+  cfg->stream = nullptr;
+}
+
+const char *nb_status_string(nb_status s) {
+  switch (s) {
+    case NB_OK: return "ok";
+    case NB_ERR_INVALID_ARG: return "invalid argument";
+    case NB_ERR_STATE: return "call out of order";
+    case NB_ERR_CUDA: return "CUDA error";
+    case NB_ERR_OOM: return "out of device memory";
+    case NB_ERR_NUMERIC: return "non-finite result";
+    case NB_ERR_TIMEOUT: return "watchdog timeout";
+    case NB_ERR_DEVICE: return "device-side error";
+  }
+  return "unknown status";
+}
+
+const char *nb_last_error(void) { return g_err; }
+
+void nb_destroy(nb_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs)
+    if (p) cudaFree(p);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_energy) cudaFreeHost(c->h_energy);
+  if (c->ev) cudaEventDestroy(c->ev);
+  delete c;
+}
+
+nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
+                  const double *v, const nb_config *cfg) {
+  if (!out) return fail(NB_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (n < 1 || n > (int64_t(1) << 30))
+    return fail(NB_ERR_INVALID_ARG, "n = %lld out of range [1, 2^30]", (long long)n);
+  if (!m || !x || !v) return fail(NB_ERR_INVALID_ARG, "null input array");
+  nb_status s = validate_config(cfg);
+  if (s != NB_OK) return s;
+  if (!finite_all(m, n) || !finite_all(x, 3 * n) || !finite_all(v, 3 * n))
+    return fail(NB_ERR_INVALID_ARG, "non-finite mass, position or velocity");
+  for (int64_t i = 0; i < n; ++i)
+    if (m[i] < 0) return fail(NB_ERR_INVALID_ARG, "negative mass at %lld", (long long)i);
+
+  nb_ctx *c = new nb_ctx();
+  c->cfg = *cfg;
+  c->n = n;
+  c->n_jt = (n + kJT - 1) / kJT;
+  c->n_pad = c->n_jt * kJT;
+  c->stream = static_cast<cudaStream_t>(cfg->stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    nb_destroy(c);
+    return fail(NB_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+#define TRY(expr)          \
+  do {                     \
+    nb_status s_ = (expr); \
+    if (s_ != NB_OK) {     \
+      nb_destroy(c);       \
+      return s_;           \
+    }                      \
+  } while (0)
+  const size_t n3 = 3 * static_cast<size_t>(n);
+  TRY(dev_alloc_t(c, &c->m, n));
+  TRY(dev_alloc_t(c, &c->x, n3));
+  TRY(dev_alloc_t(c, &c->v, n3));
+  TRY(dev_alloc_t(c, &c->a, n3));
+  TRY(dev_alloc_t(c, &c->jk, n3));
+  TRY(dev_alloc_t(c, &c->a1, n3));
+  TRY(dev_alloc_t(c, &c->j1, n3));
+  TRY(dev_alloc_t(c, &c->t_tick, n));
+  TRY(dev_alloc_t(c, &c->lev, n));
+  TRY(dev_alloc_t(c, &c->jhi, c->n_pad));
+  if (cfg->precision == NB_DS) TRY(dev_alloc_t(c, &c->jlo, c->n_pad));
+  TRY(dev_alloc_t(c, &c->jvel, c->n_pad));
+  TRY(dev_alloc_t(c, &c->act, n));
+  TRY(dev_alloc_t(c, &c->blk, next_block_scratch_ints(n) + 1));
+  TRY(dev_alloc_t(c, &c->scal, 4));
+  TRY(dev_alloc_t(c, &c->red, energy_scratch_doubles(n)));
+  TRY(dev_alloc_t(c, &c->err, 4));
+  TRY(dev_alloc_t(c, &c->clamped, 1));
+  // Partial-sum scratch for the largest built-in grid of every variant of
+  // this precision, so the default path never allocates after init.
+  size_t pb = 0;
+  for (int vv = 0; vv < num_variants(); ++vv) {
+    const Variant &V = variant_at(vv);
+    if (V.prec != cfg->precision) continue;
+    const size_t b = part_bytes(vv, c->num_sms * ctas_per_sm(vv));
+    pb = b > pb ? b : pb;
+  }
+  TRY(dev_alloc(c, reinterpret_cast<void **>(&c->part), pb));
+  c->part_cap = pb;
+  if (cudaMallocHost(reinterpret_cast<void **>(&c->h_scal), 8 * sizeof(int64_t)) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void **>(&c->h_energy), 4 * sizeof(double)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
+    nb_destroy(c);
+    return fail(NB_ERR_CUDA, "pinned host buffers / event creation failed");
+  }
+  std::memset(c->h_scal, 0, 8 * sizeof(int64_t));
+#define TRYC(call)                                                                  \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      nb_destroy(c);                                                                \
+      return fail(NB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));            \
+    }                                                                               \
+  } while (0)
+  cudaStream_t st = c->stream;
+  TRYC(cudaMemcpyAsync(c->m, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  TRYC(cudaMemcpyAsync(c->x, x, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  TRYC(cudaMemcpyAsync(c->v, v, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  TRYC(cudaMemsetAsync(c->a, 0, n3 * sizeof(double), st));
+  TRYC(cudaMemsetAsync(c->jk, 0, n3 * sizeof(double), st));
+  TRYC(cudaMemsetAsync(c->t_tick, 0, n * sizeof(int64_t), st));
+  TRYC(cudaMemsetAsync(c->scal, 0, 4 * sizeof(int64_t), st));
+  TRYC(cudaMemsetAsync(c->err, 0, 4 * sizeof(int), st));
+  TRYC(cudaMemsetAsync(c->clamped, 0, sizeof(unsigned long long), st));
+  TRYC(launch_pad_records(n, c->n_pad, c->jhi, c->jlo, c->jvel, st));
+  c->launches += 1;
+  TRY(queue_predict(c, 0));
+  TRY(queue_force(c, nullptr, n, c->a, c->jk));
+  TRYC(launch_init_levels(n, c->a, c->jk, cfg->eta_start, cfg->lev_min, cfg->lev_max,
+                          cfg->block_steps, cfg->lev_shared, c->lev, c->t_tick, st));
+  c->launches += 1;
+  TRY(sync_ctx(c));
+  // initial force must be finite
+  {
+    std::vector<double> probe(n3);
+    TRYC(cudaMemcpy(probe.data(), c->a, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+    if (!finite_all(probe.data(), static_cast<int64_t>(n3))) {
+      nb_destroy(c);
+      return fail(NB_ERR_NUMERIC, "initial acceleration is not finite (coincident particles with eps = 0?)");
+    }
+  }
+  c->have_block = false;
+  c->force_done = false;
+  *out = c;
+  return NB_OK;
+#undef TRY
+#undef TRYC
+}
+
+nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  int nl = 0;
+  NB_CUDA(launch_next_block(c->n, c->t_tick, c->lev, c->act, c->blk, c->scal, c->stream, &nl));
+  c->launches += nl;
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  c->t_block = c->h_scal[0];
+  c->n_act = c->h_scal[1];
+  c->have_block = true;
+  c->force_done = false;
+  c->n_blocks += 1;
+  if (t_next) *t_next = std::ldexp(static_cast<double>(c->t_block), -kTicksLog2);
+  if (n_active) *n_active = c->n_act;
+  return NB_OK;
+}
+
+nb_status nb_predict(nb_ctx *c, double t) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  bool ok;
+  const int64_t tick = tick_of(t, &ok);
+  if (!ok) return fail(NB_ERR_INVALID_ARG, "time %.17g is not a non-negative multiple of 2^-20", t);
+  s = queue_predict(c, tick);
+  if (s != NB_OK) return s;
+  c->force_done = false;
+  return NB_OK;
+}
+
+nb_status nb_force_jerk_dev(nb_ctx *c, const int32_t *d_idx, int64_t n_idx, double *d_acc,
+                            double *d_jerk) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (c->t_pred < 0) return fail(NB_ERR_STATE, "nb_predict must come first");
+  if (d_idx == nullptr) {
+    if (!c->have_block) return fail(NB_ERR_STATE, "no active list: call nb_next_block first");
+    if (n_idx >= 0 && n_idx != c->n_act)
+      return fail(NB_ERR_INVALID_ARG, "n_idx %lld != active count %lld", (long long)n_idx,
+                  (long long)c->n_act);
+    if (c->t_pred != c->t_block)
+      return fail(NB_ERR_STATE, "prediction time differs from the block time");
+    s = queue_force(c, c->act, c->n_act, c->a1, c->j1);
+    if (s != NB_OK) return s;
+    if (d_acc)
+      NB_CUDA(cudaMemcpyAsync(d_acc, c->a1, 3 * c->n_act * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c->stream));
+    if (d_jerk)
+      NB_CUDA(cudaMemcpyAsync(d_jerk, c->j1, 3 * c->n_act * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c->stream));
+    c->force_done = true;
+    return NB_OK;
+  }
+  if (n_idx < 0) return fail(NB_ERR_INVALID_ARG, "negative n_idx");
+  if (n_idx > 0 && (!d_acc || !d_jerk))
+    return fail(NB_ERR_INVALID_ARG, "d_acc and d_jerk are required with an explicit index list");
+  return queue_force(c, d_idx, n_idx, d_acc, d_jerk);
+}
+
+nb_status nb_force_jerk(nb_ctx *c, const int32_t *idx, int64_t n_idx, double *acc, double *jerk) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (c->t_pred < 0) return fail(NB_ERR_STATE, "nb_predict must come first");
+  const double *src_a = nullptr, *src_j = nullptr;
+  int64_t cnt = 0;
+  if (idx == nullptr) {
+    s = nb_force_jerk_dev(c, nullptr, n_idx, nullptr, nullptr);
+    if (s != NB_OK) return s;
+    src_a = c->a1;
+    src_j = c->j1;
+    cnt = c->n_act;
+  } else {
+    if (n_idx < 0) return fail(NB_ERR_INVALID_ARG, "negative n_idx");
+    for (int64_t k = 0; k < n_idx; ++k)
+      if (idx[k] < 0 || idx[k] >= c->n)
+        return fail(NB_ERR_INVALID_ARG, "index %lld at position %lld out of range [0, %lld)",
+                    (long long)idx[k], (long long)k, (long long)c->n);
+    if (n_idx > c->qidx_cap) {
+      if (c->qidx) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->qidx);
+        for (auto &p : c->allocs)
+          if (p == c->qidx) p = nullptr;
+        c->qidx = nullptr;
+      }
+      s = dev_alloc_t(c, &c->qidx, n_idx);
+      if (s != NB_OK) return s;
+      c->qidx_cap = n_idx;
+    }
+    if (6 * n_idx > c->qout_cap) {
+      if (c->qout) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->qout);
+        for (auto &p : c->allocs)
+          if (p == c->qout) p = nullptr;
+        c->qout = nullptr;
+      }
+      s = dev_alloc_t(c, &c->qout, 6 * n_idx);
+      if (s != NB_OK) return s;
+      c->qout_cap = 6 * n_idx;
+    }
+    if (n_idx > 0)
+      NB_CUDA(cudaMemcpyAsync(c->qidx, idx, n_idx * sizeof(int32_t), cudaMemcpyHostToDevice,
+                              c->stream));
+    s = queue_force(c, c->qidx, n_idx, c->qout, c->qout + 3 * n_idx);
+    if (s != NB_OK) return s;
+    src_a = c->qout;
+    src_j = c->qout + 3 * n_idx;
+    cnt = n_idx;
+  }
+  if (acc && cnt)
+    NB_CUDA(cudaMemcpyAsync(acc, src_a, 3 * cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+  if (jerk && cnt)
+    NB_CUDA(cudaMemcpyAsync(jerk, src_j, 3 * cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  if ((acc && !finite_all(acc, 3 * cnt)) || (jerk && !finite_all(jerk, 3 * cnt)))
+    return fail(NB_ERR_NUMERIC, "non-finite acceleration or jerk");
+  return NB_OK;
+}
+
+nb_status nb_correct(nb_ctx *c, double t) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  bool ok;
+  const int64_t tick = tick_of(t, &ok);
+  if (!ok) return fail(NB_ERR_INVALID_ARG, "time %.17g is not a non-negative multiple of 2^-20", t);
+  if (!c->have_block || !c->force_done || tick != c->t_block)
+    return fail(NB_ERR_STATE, "nb_correct needs nb_next_block, nb_predict and nb_force_jerk "
+                              "of the active list at the same time first");
+  NB_CUDA(launch_correct(c->n_act, c->act, c->t_block, c->x, c->v, c->a, c->jk, c->t_tick,
+                         c->lev, c->a1, c->j1, c->cfg.eta, c->cfg.lev_min, c->cfg.lev_max,
+                         c->cfg.block_steps, c->clamped, c->stream));
+  c->launches += 1;
+  c->force_done = false;
+  c->have_block = false;
+  return NB_OK;
+}
+
+nb_status nb_step(nb_ctx *c, double *t_next, int64_t *n_active) {
+  double tn;
+  int64_t na;
+  nb_status s = nb_next_block(c, &tn, &na);
+  if (s != NB_OK) return s;
+  s = nb_predict(c, tn);
+  if (s != NB_OK) return s;
+  s = nb_force_jerk_dev(c, nullptr, na, nullptr, nullptr);
+  if (s != NB_OK) return s;
+  s = nb_correct(c, tn);
+  if (s != NB_OK) return s;
+  if (t_next) *t_next = tn;
+  if (n_active) *n_active = na;
+  return NB_OK;
+}
+
+nb_status nb_energy(nb_ctx *c, double *kin, double *pot, double *tot) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  int nl = 0;
+  double *d_out = c->red + energy_scratch_doubles(c->n) - 2;
+  NB_CUDA(launch_energy(c->n, c->m, c->x, c->v, c->cfg.G, c->cfg.eps, c->red, d_out, c->stream,
+                        &nl));
+  c->launches += nl;
+  NB_CUDA(cudaMemcpyAsync(c->h_energy, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  if (kin) *kin = c->h_energy[0];
+  if (pot) *pot = c->h_energy[1];
+  if (tot) *tot = c->h_energy[0] + c->h_energy[1];
+  if (!std::isfinite(c->h_energy[0]) || !std::isfinite(c->h_energy[1]))
+    return fail(NB_ERR_NUMERIC, "non-finite energy");
+  return NB_OK;
+}
+
+nb_status nb_get_state(nb_ctx *c, double *x, double *v, double *a, double *jerk,
+                       int64_t *t_tick, int32_t *lev) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  const size_t n3 = 3 * static_cast<size_t>(c->n) * sizeof(double);
+  if (x) NB_CUDA(cudaMemcpyAsync(x, c->x, n3, cudaMemcpyDeviceToHost, c->stream));
+  if (v) NB_CUDA(cudaMemcpyAsync(v, c->v, n3, cudaMemcpyDeviceToHost, c->stream));
+  if (a) NB_CUDA(cudaMemcpyAsync(a, c->a, n3, cudaMemcpyDeviceToHost, c->stream));
+  if (jerk) NB_CUDA(cudaMemcpyAsync(jerk, c->jk, n3, cudaMemcpyDeviceToHost, c->stream));
+  if (t_tick)
+    NB_CUDA(cudaMemcpyAsync(t_tick, c->t_tick, c->n * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            c->stream));
+  if (lev)
+    NB_CUDA(cudaMemcpyAsync(lev, c->lev, c->n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c->stream));
+  return sync_ctx(c);
+}
+
+nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double *a,
+                       const double *jerk, const int64_t *t_tick, const int32_t *lev) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (!x || !v || !a || !jerk || !t_tick || !lev)
+    return fail(NB_ERR_INVALID_ARG, "nb_set_state needs all six arrays");
+  const int64_t n = c->n;
+  if (!finite_all(x, 3 * n) || !finite_all(v, 3 * n) || !finite_all(a, 3 * n) ||
+      !finite_all(jerk, 3 * n))
+    return fail(NB_ERR_INVALID_ARG, "non-finite state");
+  for (int64_t i = 0; i < n; ++i) {
+    if (lev[i] < 0 || lev[i] > kTicksLog2 || t_tick[i] < 0 ||
+        t_tick[i] % (int64_t(1) << (kTicksLog2 - lev[i])) != 0)
+      return fail(NB_ERR_INVALID_ARG, "particle %lld: level or tick invalid", (long long)i);
+  }
+  const size_t n3 = 3 * static_cast<size_t>(n) * sizeof(double);
+  NB_CUDA(cudaMemcpyAsync(c->x, x, n3, cudaMemcpyHostToDevice, c->stream));
+  NB_CUDA(cudaMemcpyAsync(c->v, v, n3, cudaMemcpyHostToDevice, c->stream));
+  NB_CUDA(cudaMemcpyAsync(c->a, a, n3, cudaMemcpyHostToDevice, c->stream));
+  NB_CUDA(cudaMemcpyAsync(c->jk, jerk, n3, cudaMemcpyHostToDevice, c->stream));
+  NB_CUDA(cudaMemcpyAsync(c->t_tick, t_tick, n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                          c->stream));
+  NB_CUDA(cudaMemcpyAsync(c->lev, lev, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  c->have_block = false;
+  c->force_done = false;
+  c->t_pred = -1;
+  return sync_ctx(c);
+}
+
+nb_status nb_get_active(nb_ctx *c, int32_t *idx, int64_t cap, int64_t *n_active) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (!c->have_block) return fail(NB_ERR_STATE, "no active list: call nb_next_block first");
+  if (n_active) *n_active = c->n_act;
+  if (idx) {
+    if (cap < c->n_act) return fail(NB_ERR_INVALID_ARG, "capacity %lld < active count %lld",
+                                    (long long)cap, (long long)c->n_act);
+    if (c->n_act)
+      NB_CUDA(cudaMemcpyAsync(idx, c->act, c->n_act * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              c->stream));
+  }
+  return sync_ctx(c);
+}
+
+nb_status nb_get_counters(nb_ctx *c, int64_t *n_blocks, int64_t *n_interactions,
+                          int64_t *n_clamped) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  if (n_blocks) *n_blocks = c->n_blocks;
+  if (n_interactions) *n_interactions = c->interactions;
+  if (n_clamped) *n_clamped = c->h_scal[3];
+  return NB_OK;
+}
+
+nb_status nb_sync(nb_ctx *c) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  return sync_ctx(c);
+}
+
+int64_t nb_launch_count(const nb_ctx *c) { return c ? c->launches : -1; }
+
+nb_status nb_set_force_variant(nb_ctx *c, int32_t variant, int32_t grid_ctas) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (variant >= num_variants() || variant < -1)
+    return fail(NB_ERR_INVALID_ARG, "unknown force variant %d", variant);
+  if (variant >= 0) {
+    const Variant &V = variant_at(variant);
+    if (V.prec != c->cfg.precision)
+      return fail(NB_ERR_INVALID_ARG, "variant %d has the other precision", variant);
+    if (V.mask != (c->cfg.eps == 0.0 ? 1 : 0))
+      return fail(NB_ERR_INVALID_ARG, "variant %d does not match the eps == 0 masking", variant);
+  }
+  c->variant_override = variant;
+  c->grid_cap = grid_ctas > 0 ? grid_ctas : 0;
+  return NB_OK;
+}
+
+nb_status nb_variant_info(int32_t v, int32_t *precision, int32_t *ipt, int32_t *tpi,
+                          int32_t *threads) {
+  if (v < 0 || v >= num_variants()) return fail(NB_ERR_INVALID_ARG, "unknown variant %d", v);
+  const Variant &V = variant_at(v);
+  if (precision) *precision = V.prec;
+  if (ipt) *ipt = V.ipt;
+  if (tpi) *tpi = V.tpi;
+  if (threads) *threads = V.threads;
+  return NB_OK;
+}
+
+nb_status nb_debug_inject(nb_ctx *c, int32_t kind) {
+  if (kind == 1) {
+    g_inject_oom.store(1);
+    return NB_OK;
+  }
+  if (kind == 2) {
+    if (!c) return fail(NB_ERR_INVALID_ARG, "timeout injection needs a context");
+    c->inject_timeout = true;
+    return NB_OK;
+  }
+  return fail(NB_ERR_INVALID_ARG, "unknown injection kind %d", kind);
+}
+
+}  // extern "C"

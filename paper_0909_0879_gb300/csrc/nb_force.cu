@@ -1,0 +1,436 @@
+// Force + jerk kernels for sm_103a.
+//
+// What is computed (paper eq. 1, Sec. 2, with the Plummer softening of
+// Sec. 3, and its time derivative):
+//   a_i = G sum_j m_j d / s^3,  j_i = G sum_j m_j (w / s^3 - 3 (d.w) d / s^5)
+//   d = x_j - x_i, w = v_j - v_i, s^2 = |d|^2 + eps^2
+// for an active list of i against every j-record.  The i == j term is
+// evaluated and is exactly zero when eps > 0 (d = w = 0); the eps == 0
+// variants zero it explicitly.
+//
+// Design (GB300, not the paper's GT200 kernel):
+//  * Pair arithmetic on the FP32 pipe with one MUFU reciprocal square root
+//    per pair; no tensor cores (the pair sum is not a dense contraction).
+//  * Each thread keeps IPT i-particles in registers; every j-record read from
+//    shared memory (a broadcast) is reused IPT times.
+//  * j-tiles of 256 records are staged in shared memory by the bulk-copy
+//    (TMA) engine, cp.async.bulk + mbarrier, three stages deep, one thread
+//    issuing.  No cluster multicast.
+//  * Split precision ("double-single", after Gaburov, Harfst & Portegies
+//    Zwart 2009, cited in the paper's Sec. 4): positions are hi + lo FP32
+//    pairs and d = (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo); the per-tile FP32
+//    partial sums are folded into hi + lo accumulators with an error-free
+//    two-sum once per tile, so the split-precision overhead is per tile, not
+//    per pair, except for the three extra subtractions per coordinate.
+//  * Work decomposition: the (i-block, j-tile) space is cut into equal
+//    contiguous ranges, one per persistent CTA (a "stream-K" split), so every
+//    active-list length fills the GPU evenly.  An i-block whose j-range spans
+//    several CTAs gets FP64 partial sums that a fix-up kernel adds in
+//    ascending CTA order: results are deterministic.
+//  * Several threads per i-particle (TPI > 1) split a tile's j-range inside
+//    the CTA for short active lists; their sums meet by a warp-shuffle
+//    butterfly (commutative pairwise adds, identical on every lane).
+#include "nb_internal.cuh"
+
+#include <algorithm>
+#include <mutex>
+
+namespace nbi {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// 1-D bulk copy global -> shared through the TMA engine; completion is
+// signalled on the mbarrier as transaction bytes.  dst, src 16-byte aligned
+// and bytes a multiple of 16 (always kJT * 16 here).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src,
+                                         uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after kWaitLimit unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+// Error-free addition of x into the unevaluated sum hi + lo (two-sum).
+__device__ __forceinline__ void ds_add(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
+// CTA owning unit u of U units split over P CTAs (ranges [U p / P, U (p+1) / P)).
+__host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) {
+  return static_cast<int>(((u + 1) * static_cast<uint64_t>(P) - 1) / U);
+}
+
+template <int PREC, int IPT, int TPI, int NT, int MASK>
+__global__ void __launch_bounds__(NT, 1)
+    force_jerk_kernel(const ForceArgs A, const uint64_t U, const int P) {
+  constexpr int NG = NT / TPI;    // i-slots per CTA (per q)
+  constexpr int BI = NG * IPT;    // i-particles per i-block
+  constexpr int NARR = PREC ? 3 : 2;
+  constexpr uint32_t kTileBytes = kJT * 16;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4 *sbase = reinterpret_cast<float4 *>(smem_raw);
+  __shared__ __align__(8) uint64_t bars[kStages];
+
+  const int tid = threadIdx.x;
+  const int g = tid / TPI;
+  const int r = tid % TPI;
+  const int p = blockIdx.x;
+  const uint64_t u0 = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
+  const uint64_t u1 = U * static_cast<uint64_t>(p + 1) / static_cast<uint64_t>(P);
+  if (u0 >= u1) return;  // uniform over the CTA
+  const uint64_t nunits = u1 - u0;
+  const uint64_t n_jt = static_cast<uint64_t>(A.n_jt);
+  const int64_t n_i = A.n_i;
+  const float eps2 = A.eps2;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](uint64_t s_idx) {
+    const int st = static_cast<int>(s_idx % kStages);
+    const uint64_t jt = (u0 + s_idx) % n_jt;
+    float4 *dst = sbase + static_cast<size_t>(st) * NARR * kJT;
+    mbar_expect_tx(&bars[st], kTileBytes * NARR);
+    bulk_g2s(dst, A.jhi + jt * kJT, kTileBytes, &bars[st]);
+    if (PREC) bulk_g2s(dst + kJT, A.jlo + jt * kJT, kTileBytes, &bars[st]);
+    bulk_g2s(dst + (NARR - 1) * kJT, A.jvel + jt * kJT, kTileBytes, &bars[st]);
+  };
+  if (tid == 0) {
+    const uint64_t pre = nunits < kStages ? nunits : kStages;
+    for (uint64_t s = 0; s < pre; ++s) issue(s);
+  }
+
+  const uint64_t ib_first = u0 / n_jt;
+  uint64_t s_idx = 0;
+  uint64_t u = u0;
+  while (u < u1) {
+    const uint64_t ib = u / n_jt;
+    const uint64_t jt0 = u % n_jt;
+    const uint64_t seg = (n_jt - jt0) < (u1 - u) ? (n_jt - jt0) : (u1 - u);
+    const bool full = (jt0 == 0) && (seg == n_jt);
+
+    float xh[IPT][3], xl[IPT][3], vi[IPT][3];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      const int64_t k = static_cast<int64_t>(ib) * BI + g + q * NG;
+      int64_t i = 0;
+      if (k < n_i) i = A.idx ? A.idx[k] : k;
+      const float4 h = A.jhi[i];
+      const float4 w = A.jvel[i];
+      xh[q][0] = h.x; xh[q][1] = h.y; xh[q][2] = h.z;
+      vi[q][0] = w.x; vi[q][1] = w.y; vi[q][2] = w.z;
+      if (PREC) {
+        const float4 l = A.jlo[i];
+        xl[q][0] = l.x; xl[q][1] = l.y; xl[q][2] = l.z;
+      } else {
+        xl[q][0] = xl[q][1] = xl[q][2] = 0.f;
+      }
+    }
+    float ah[IPT][3], al[IPT][3], jh[IPT][3], jl[IPT][3];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ah[q][c] = al[q][c] = jh[q][c] = jl[q][c] = 0.f;
+
+    for (uint64_t t = 0; t < seg; ++t, ++s_idx) {
+      const int st = static_cast<int>(s_idx % kStages);
+      const uint32_t ph = static_cast<uint32_t>((s_idx / kStages) & 1);
+      const bool ok = mbar_wait(&bars[st], ph);
+      const float4 *sh = sbase + static_cast<size_t>(st) * NARR * kJT;
+      const float4 *sl = sh + kJT;
+      const float4 *sv = sh + (NARR - 1) * kJT;
+
+      float pa[IPT][3], p1[IPT][3], p2[IPT][3];
+#pragma unroll
+      for (int q = 0; q < IPT; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pa[q][c] = p1[q][c] = p2[q][c] = 0.f;
+
+#pragma unroll 4
+      for (int jj = r; jj < kJT; jj += TPI) {
+        const float4 hj = sh[jj];
+        const float4 wj = sv[jj];
+        float4 lj;
+        if (PREC) lj = sl[jj];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+          float dx, dy, dz;
+          if (PREC) {
+            dx = (hj.x - xh[q][0]) + (lj.x - xl[q][0]);
+            dy = (hj.y - xh[q][1]) + (lj.y - xl[q][1]);
+            dz = (hj.z - xh[q][2]) + (lj.z - xl[q][2]);
+          } else {
+            dx = hj.x - xh[q][0];
+            dy = hj.y - xh[q][1];
+            dz = hj.z - xh[q][2];
+          }
+          const float ux = wj.x - vi[q][0];
+          const float uy = wj.y - vi[q][1];
+          const float uz = wj.z - vi[q][2];
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+          float rinv;
+          if (MASK)
+            rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+          else
+            rinv = rsqrtf(r2);
+          const float rinv2 = rinv * rinv;
+          const float mr3 = (hj.w * rinv) * rinv2;
+          const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+          const float cc = (rv * rinv2) * mr3;
+          pa[q][0] = fmaf(mr3, dx, pa[q][0]);
+          pa[q][1] = fmaf(mr3, dy, pa[q][1]);
+          pa[q][2] = fmaf(mr3, dz, pa[q][2]);
+          p1[q][0] = fmaf(mr3, ux, p1[q][0]);
+          p1[q][1] = fmaf(mr3, uy, p1[q][1]);
+          p1[q][2] = fmaf(mr3, uz, p1[q][2]);
+          p2[q][0] = fmaf(cc, dx, p2[q][0]);
+          p2[q][1] = fmaf(cc, dy, p2[q][1]);
+          p2[q][2] = fmaf(cc, dz, p2[q][2]);
+        }
+      }
+      // fold the tile's partial sums (jerk = p1 - 3 p2)
+#pragma unroll
+      for (int q = 0; q < IPT; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float jt = fmaf(-3.f, p2[q][c], p1[q][c]);
+          if (PREC) {
+            ds_add(ah[q][c], al[q][c], pa[q][c]);
+            ds_add(jh[q][c], jl[q][c], jt);
+          } else {
+            ah[q][c] += pa[q][c];
+            jh[q][c] += jt;
+          }
+        }
+      if (__syncthreads_or(!ok)) {
+        // A copy never arrived: record it, wait (bounded) for the copies
+        // still in flight so none lands after exit, and leave.
+        if (tid == 0) {
+          atomicOr(A.err, kErrWaitTimeout);
+          const uint64_t last = (s_idx + kStages < nunits) ? s_idx + kStages : nunits;
+          for (uint64_t s2 = s_idx; s2 < last; ++s2)
+            (void)mbar_wait(&bars[s2 % kStages], static_cast<uint32_t>((s2 / kStages) & 1));
+        }
+        return;
+      }
+      if (tid == 0 && s_idx + kStages < nunits) issue(s_idx + kStages);
+    }
+
+    // epilogue: FP64 results of this segment
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      double o[6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[c] = static_cast<double>(ah[q][c]) + static_cast<double>(al[q][c]);
+        o[3 + c] = static_cast<double>(jh[q][c]) + static_cast<double>(jl[q][c]);
+      }
+      if (TPI > 1) {
+#pragma unroll
+        for (int off = 1; off < TPI; off <<= 1)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) o[c] += __shfl_xor_sync(0xffffffffu, o[c], off);
+      }
+      const int kk = g + q * NG;
+      const int64_t k = static_cast<int64_t>(ib) * BI + kk;
+      if (r == 0 && k < n_i) {
+        if (full) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            A.acc[3 * k + c] = A.G * o[c];
+            A.jerk[3 * k + c] = A.G * o[3 + c];
+          }
+        } else {
+          const int slot = (ib == ib_first) ? 0 : 1;
+          double *dst = A.part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) dst[static_cast<size_t>(c) * BI + kk] = o[c];
+        }
+      }
+    }
+    u += seg;
+  }
+}
+
+// Sum the partial segments of every split i-block in ascending CTA order.
+__global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
+                                   uint64_t n_jt, uint64_t U, int P, int BI,
+                                   double G, double *__restrict__ acc,
+                                   double *__restrict__ jerk) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n_i) return;
+  const uint64_t ib = static_cast<uint64_t>(k) / BI;
+  const int kk = static_cast<int>(static_cast<uint64_t>(k) % BI);
+  const int plo = owner_of(ib * n_jt, U, P);
+  const int phi = owner_of((ib + 1) * n_jt - 1, U, P);
+  if (plo == phi) return;  // written directly by its only CTA
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int p = plo; p <= phi; ++p) {
+    const uint64_t u0p = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
+    const int slot = (u0p / n_jt == ib) ? 0 : 1;
+    const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] += src[static_cast<size_t>(c) * BI + kk];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[3 * k + c] = G * s[c];
+    jerk[3 * k + c] = G * s[3 + c];
+  }
+}
+
+using KernelFn = void (*)(const ForceArgs, const uint64_t, const int);
+
+struct Entry {
+  Variant V;
+  KernelFn fn;
+};
+
+#define NB_V(PREC, IPT, TPI, NT, MASK) \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK}, &force_jerk_kernel<PREC, IPT, TPI, NT, MASK>}
+
+// The compiled shape table.  Index order is part of the tuning interface.
+const Entry kTable[] = {
+    NB_V(1, 4, 1, 256, 0),   // 0  DS, long lists
+    NB_V(1, 2, 1, 256, 0),   // 1
+    NB_V(1, 1, 1, 256, 0),   // 2
+    NB_V(1, 1, 4, 256, 0),   // 3  DS, short lists
+    NB_V(1, 1, 16, 256, 0),  // 4
+    NB_V(0, 4, 1, 256, 0),   // 5  FP32, long lists
+    NB_V(0, 2, 1, 256, 0),   // 6
+    NB_V(0, 1, 1, 256, 0),   // 7
+    NB_V(0, 1, 4, 256, 0),   // 8  FP32, short lists
+    NB_V(0, 1, 16, 256, 0),  // 9
+    NB_V(1, 1, 1, 256, 1),   // 10 DS, eps == 0
+    NB_V(0, 1, 1, 256, 1),   // 11 FP32, eps == 0
+};
+constexpr int kNumVariants = sizeof(kTable) / sizeof(kTable[0]);
+
+size_t smem_bytes(const Variant &V) {
+  return static_cast<size_t>(kStages) * (V.prec ? 3 : 2) * kJT * sizeof(float4);
+}
+
+std::mutex g_occ_mu;
+int g_occ[kNumVariants] = {0};
+
+}  // namespace
+
+int num_variants() { return kNumVariants; }
+const Variant &variant_at(int v) { return kTable[v].V; }
+int block_i(const Variant &V) { return V.threads / V.tpi * V.ipt; }
+
+int choose_variant(int prec, int mask, int64_t n_i) {
+  if (mask) return prec ? 10 : 11;
+  const int base = prec ? 0 : 5;
+  if (n_i >= 2048) return base + 0;
+  if (n_i >= 512) return base + 1;
+  if (n_i >= 256) return base + 2;
+  if (n_i >= 64) return base + 3;
+  return base + 4;
+}
+
+int ctas_per_sm(int v) {
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  if (g_occ[v] == 0) {
+    int nb = 0;
+    const Variant &V = kTable[v].V;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, kTable[v].fn, V.threads, smem_bytes(V)) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    g_occ[v] = nb;
+  }
+  return g_occ[v];
+}
+
+size_t part_bytes(int v, int grid) {
+  return static_cast<size_t>(grid) * 2 * 6 * block_i(kTable[v].V) * sizeof(double);
+}
+
+int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap) {
+  const Variant &V = kTable[v].V;
+  const int64_t BI = block_i(V);
+  const int64_t n_ib = (n_i + BI - 1) / BI;
+  const int64_t U = n_ib * n_jt;
+  int64_t P = static_cast<int64_t>(num_sms) * ctas_per_sm(v);
+  if (grid_cap > 0 && grid_cap < P) P = grid_cap;
+  if (U < P) P = U;
+  return static_cast<int>(P < 1 ? 1 : P);
+}
+
+cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
+                         int *launches) {
+  const Entry &E = kTable[v];
+  const int BI = block_i(E.V);
+  const uint64_t n_ib = static_cast<uint64_t>((A.n_i + BI - 1) / BI);
+  const uint64_t U = n_ib * static_cast<uint64_t>(A.n_jt);
+  E.fn<<<grid, E.V.threads, smem_bytes(E.V), s>>>(A, U, grid);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int nl = 1;
+  // Split i-blocks exist unless every CTA range is whole i-blocks.
+  if (!(U % static_cast<uint64_t>(grid) == 0 &&
+        (U / grid) % static_cast<uint64_t>(A.n_jt) == 0)) {
+    const int tb = 256;
+    const int64_t nb = (A.n_i + tb - 1) / tb;
+    force_fixup_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(
+        A.part, A.n_i, static_cast<uint64_t>(A.n_jt), U, grid, BI, A.G, A.acc,
+        A.jerk);
+    e = cudaGetLastError();
+    ++nl;
+  }
+  if (launches) *launches += nl;
+  return e;
+}
+
+}  // namespace nbi

@@ -1,0 +1,95 @@
+// Internal declarations shared by the CUDA translation units of libnbody.
+// Not part of the public C ABI (see include/nbody.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nbi {
+
+// Time is an integer count of 2^-20 ticks.
+constexpr int kTicksLog2 = 20;
+
+// j-records per shared-memory tile and pipeline depth of the force kernels.
+constexpr int kJT = 256;
+constexpr int kStages = 3;
+
+// Bound on the polls of any device-side wait; past it the kernel records an
+// error in the context's error word and returns instead of hanging.
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+// Device error-word bits.
+constexpr int kErrWaitTimeout = 1;
+
+// One force + jerk evaluation: active i-list against all (padded) j-records.
+struct ForceArgs {
+  const float4 *jhi;   // (x, y, z, m): FP32 values, or the high words (DS)
+  const float4 *jlo;   // (x_lo, y_lo, z_lo, 0): low words (DS only)
+  const float4 *jvel;  // (vx, vy, vz, 0)
+  int64_t n_jt;        // j-tiles; records are padded to n_jt * kJT
+  const int32_t *idx;  // i-list (n_i entries); nullptr = 0..n_i-1
+  int64_t n_i;
+  float eps2;
+  double G;
+  double *acc;         // (n_i, 3)
+  double *jerk;        // (n_i, 3)
+  double *part;        // partial sums of split i-blocks
+  int *err;            // device error word
+};
+
+struct Variant {
+  int prec;     // 0 = FP32, 1 = double-single
+  int ipt;      // i-particles per thread
+  int tpi;      // threads per i-particle (j split inside the CTA)
+  int threads;  // threads per CTA
+  int mask;     // 1: zero the i == j term (eps == 0)
+};
+
+int num_variants();
+const Variant &variant_at(int v);
+int block_i(const Variant &V);  // i-particles per i-block
+// Built-in variant for a precision, mask flag and active-list length.
+int choose_variant(int prec, int mask, int64_t n_i);
+// Resident CTAs per SM of a variant (occupancy query, cached).
+int ctas_per_sm(int v);
+// Bytes of partial-sum scratch a launch of variant v on `grid` CTAs needs.
+size_t part_bytes(int v, int grid);
+// Persistent grid for a variant, an active-list length and an optional cap.
+int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap);
+// Queue the force kernel (and its fix-up when i-blocks are split) on `s`.
+// Returns the number of kernel launches through *launches.
+cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
+                         int *launches);
+
+// --- Hermite and bookkeeping kernels (nb_hermite.cu) ---
+cudaError_t launch_predict(int64_t n, int64_t t_next, const double *x,
+                           const double *v, const double *a, const double *jk,
+                           const double *m, const int64_t *t_tick, int prec,
+                           float4 *jhi, float4 *jlo, float4 *jvel,
+                           cudaStream_t s);
+cudaError_t launch_pad_records(int64_t n, int64_t n_pad, float4 *jhi,
+                               float4 *jlo, float4 *jvel, cudaStream_t s);
+cudaError_t launch_correct(int64_t n_act, const int32_t *act, int64_t t_next,
+                           double *x, double *v, double *a, double *jk,
+                           int64_t *t_tick, int32_t *lev, const double *a1,
+                           const double *j1, double eta, int lev_min,
+                           int lev_max, int block_steps,
+                           unsigned long long *n_clamped, cudaStream_t s);
+cudaError_t launch_init_levels(int64_t n, const double *a, const double *jk,
+                               double eta_start, int lev_min, int lev_max,
+                               int block_steps, int lev_shared, int32_t *lev,
+                               int64_t *t_tick, cudaStream_t s);
+// Writes t_next (ticks) and n_act to d_scal[0], d_scal[1] and the active
+// list to act.  Returns the number of launches through *launches.
+cudaError_t launch_next_block(int64_t n, const int64_t *t_tick,
+                              const int32_t *lev, int32_t *act,
+                              int32_t *blk_count, int64_t *d_scal,
+                              cudaStream_t s, int *launches);
+int64_t next_block_scratch_ints(int64_t n);
+// Kinetic and softened potential energy in FP64; result in d_out[0..1].
+cudaError_t launch_energy(int64_t n, const double *m, const double *x,
+                          const double *v, double G, double eps, double *red,
+                          double *d_out, cudaStream_t s, int *launches);
+int64_t energy_scratch_doubles(int64_t n);
+
+}  // namespace nbi

@@ -1,0 +1,170 @@
+"""GPU parity of the force + jerk kernels against the FP64 oracle, through
+the C ABI (libnbody.so).
+
+Tolerance (the split-precision target is relative force error <= 1e-6):
+  e_i = |a_gpu - a_ref| / max(|a_ref|, 1e-3 rms|a_ref|)
+  split precision (DS): max e_i <= 1e-6 for the acceleration, <= 1e-5 for
+  the jerk; plain FP32: max e_i <= 1e-3 (positions are quantised to FP32,
+  so the error grows with N; reported, not a target).
+"""
+import numpy as np
+import pytest
+
+from paper_0909_0879_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"ds": (1e-6, 1e-5), "fp32": (1e-3, 1e-2)}
+
+
+def rel_err(got, ref):
+    scale = np.sqrt(np.mean(np.sum(ref * ref, axis=1))) if len(ref) else 1.0
+    den = np.maximum(np.linalg.norm(ref, axis=1), 1e-3 * scale)
+    return np.linalg.norm(got - ref, axis=1) / den
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0909_0879_gb300 import _lib
+
+    _lib.load()
+    return _lib
+
+
+def check(acc, jerk, ra, rj, prec):
+    ta, tj = TOL[prec]
+    ea, ej = rel_err(acc, ra), rel_err(jerk, rj)
+    assert ea.max() <= ta, f"{prec} acc err {ea.max():.3e}"
+    assert ej.max() <= tj, f"{prec} jerk err {ej.max():.3e}"
+    return ea.max(), ej.max()
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 255, 256, 257, 1023, 4097])
+def test_full_active_small_sizes(nb, oracle_mod, prec, n):
+    """Every particle active; sizes below, at and past one 256-record tile."""
+    m, x, v = ics.plummer(n, 500 + n) if n > 2 else (
+        np.array([0.3, 0.7, 0.5])[:n], np.array([[0.1, 0.2, 0.3], [-0.4, 0.1, 0.0], [0.2, -0.3, 0.5]])[:n],
+        np.array([[0.0, 0.1, 0.0], [0.2, 0.0, -0.1], [0.0, 0.3, 0.2]])[:n])
+    eps = 1e-3
+    ra, rj = oracle_mod.force_jerk(m, x, v, eps)
+    with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+        acc, jerk = s.force_jerk(np.arange(n, dtype=np.int32))
+    if n == 1:
+        assert np.all(acc == 0) and np.all(jerk == 0)
+        return
+    check(acc, jerk, ra, rj, prec)
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+def test_every_variant_and_split_grids(nb, oracle_mod, prec):
+    """Each compiled kernel shape of this precision, with the persistent grid
+    capped to force i-blocks split across CTAs (stream-K fix-up path), on a
+    ragged tail (N = 4097) and subsets of several lengths."""
+    n, eps = 4097, 1e-3
+    m, x, v = ics.plummer(n, 77)
+    subsets = [ics.random_active_subset(n, k, 3000 + k) for k in (1, 5, 64, 333, 1500, 4097)]
+    refs = [oracle_mod.force_jerk(m, x, v, eps, idx=ii) for ii in subsets]
+    with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+        for var in range(nb.num_variants()):
+            info = nb.variant_info(var)
+            if info["precision"] != (1 if prec == "ds" else 0):
+                continue
+            try:
+                s.set_force_variant(var, 0)
+            except nb.NBodyError:
+                continue  # eps == 0 variants
+            for cap in (0, 7, 150):
+                s.set_force_variant(var, cap)
+                for ii, (ra, rj) in zip(subsets, refs):
+                    acc, jerk = s.force_jerk(ii)
+                    check(acc, jerk, ra, rj, prec)
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+def test_eps_zero_masks_self_term(nb, oracle_mod, prec):
+    """eps = 0: the i == j term is masked; two-body closed form and a small
+    random system against the oracle."""
+    m = np.array([2.0, 5.0])
+    x = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+    v = np.array([[0.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    with nb.NBody(m, x, v, eps=0.0, precision=prec) as s:
+        acc, jerk = s.force_jerk(np.array([0, 1], dtype=np.int32))
+    tol = 1e-6 if prec == "ds" else 1e-5
+    np.testing.assert_allclose(acc[0], [0.12, 0.16, 0.0], atol=tol * 0.2)
+    np.testing.assert_allclose(jerk[0], [-0.0576, -0.0368, 0.0], atol=tol * 0.07)
+    m, x, v = ics.plummer(300, 9)
+    ra, rj = oracle_mod.force_jerk(m, x, v, 0.0)
+    with nb.NBody(m, x, v, eps=0.0, precision=prec) as s:
+        acc, jerk = s.force_jerk(np.arange(300, dtype=np.int32))
+    check(acc, jerk, ra, rj, prec)
+
+
+def test_deterministic_and_duplicate_indices(nb):
+    n = 5000
+    m, x, v = ics.plummer(n, 3)
+    idx = np.concatenate([np.arange(0, n, 7), np.arange(0, n, 7)]).astype(np.int32)
+    with nb.NBody(m, x, v, eps=1e-3) as s:
+        a1, j1 = s.force_jerk(idx)
+        a2, j2 = s.force_jerk(idx)
+    assert np.array_equal(a1, a2) and np.array_equal(j1, j2)
+    h = len(idx) // 2
+    assert np.array_equal(a1[:h], a1[h:])
+
+
+def test_salpeter_masses_close_pairs(nb, oracle_mod):
+    """Unequal masses spanning three decades and eps = 1e-4 (the block-step
+    workload's mass spectrum and softening) at N = 8192."""
+    n, eps = 8192, 1e-4
+    m, x, v = ics.plummer(n, 1002, masses=ics.salpeter_masses(n, 1002))
+    idx = ics.random_active_subset(n, 512, 2002)
+    ra, rj = oracle_mod.force_jerk(m, x, v, eps, idx=idx)
+    for prec in ("ds", "fp32"):
+        with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+            acc, jerk = s.force_jerk(idx)
+        check(acc, jerk, ra, rj, prec)
+
+
+def test_device_pointer_path_matches_host_path(nb):
+    import torch
+
+    n = 3000
+    m, x, v = ics.plummer(n, 4)
+    idx = ics.random_active_subset(n, 1000, 1)
+    with nb.NBody(m, x, v, eps=1e-3) as s:
+        acc_h, jerk_h = s.force_jerk(idx)
+        d_idx = torch.from_numpy(idx).cuda()
+        d_acc = torch.zeros((1000, 3), dtype=torch.float64, device="cuda")
+        d_jerk = torch.zeros_like(d_acc)
+        s.force_jerk_dev(d_idx, 1000, d_acc, d_jerk)
+        s.sync()
+    assert np.array_equal(d_acc.cpu().numpy(), acc_h)
+    assert np.array_equal(d_jerk.cpu().numpy(), jerk_h)
+
+
+def test_king_1m_sampled_parity(nb, oracle_mod):
+    """Full-size single evaluation (N = 1,048,576 King W0 = 7, eps = 1e-4),
+    every particle active, in the bench's launch configuration; 256 sampled
+    particles against the oracle."""
+    import torch
+
+    n, eps = 1 << 20, 1e-4
+    m, x, v = ics.king(n, 7.0, 1003)
+    sample = np.sort(np.random.default_rng(2003).choice(n, 256, replace=False))
+    ra, rj = oracle_mod.force_jerk(m, x, v, eps, idx=sample)
+    errs = {}
+    for prec in ("ds", "fp32"):
+        with nb.NBody(m, x, v, eps=eps, precision=prec, block_steps=False, lev_shared=10) as s:
+            d_acc = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+            d_jerk = torch.zeros_like(d_acc)
+            d_idx = torch.arange(n, dtype=torch.int32, device="cuda")
+            s.force_jerk_dev(d_idx, n, d_acc, d_jerk)
+            s.sync()
+            acc = d_acc[torch.from_numpy(sample).cuda()].cpu().numpy()
+            jerk = d_jerk[torch.from_numpy(sample).cuda()].cpu().numpy()
+        errs[prec] = check(acc, jerk, ra, rj, prec)
+    print("king 1M sampled errors", errs)
