@@ -182,6 +182,55 @@ nb_status nb_variant_info(int32_t v, int32_t *precision, int32_t *ipt,
  * (ctx required).  No GPU fault is ever caused. */
 nb_status nb_debug_inject(nb_ctx *ctx, int32_t kind);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent clusters, shared step dt = 2^-lev_shared,
+ * advanced by one persistent kernel per S steps (a CUDA graph of those
+ * launches is captured once and replayed).  Same force law, jerk and
+ * Hermite-4 corrector as above; cluster c holds particles
+ * [offsets[c], offsets[c+1]) of the concatenated arrays and interacts only
+ * with itself.  Cluster sizes 1..4096.
+ * ---------------------------------------------------------------------- */
+typedef struct nb_batch nb_batch; /* opaque, library-owned */
+
+/* Copy the clusters to the device and evaluate a, j at t = 0.  cfg must have
+ * block_steps == 0; cfg->lev_shared sets dt; cfg->precision and cfg->eps as
+ * for nb_init.  Errors: NB_ERR_INVALID_ARG, NB_ERR_OOM, NB_ERR_CUDA. */
+nb_status nb_batched_init(nb_batch **out, int32_t n_clusters,
+                          const int64_t *offsets, const double *m,
+                          const double *x, const double *v,
+                          const nb_config *cfg);
+void nb_batched_destroy(nb_batch *b);
+
+/* Advance every cluster nsteps shared steps: ceil(nsteps / S) persistent
+ * launches (S = steps per launch, see nb_batched_set_tuning), each a queue
+ * of all clusters largest first; captured once into a CUDA graph per
+ * (nsteps, tuning) and replayed.  Asynchronous. */
+nb_status nb_batched_run(nb_batch *b, int64_t nsteps);
+
+/* The same steps with one single-CTA launch per cluster per S steps (the
+ * per-cluster-launch baseline).  Results are bitwise equal to
+ * nb_batched_run's.  Asynchronous. */
+nb_status nb_batched_run_per_cluster(nb_batch *b, int64_t nsteps);
+
+/* Kernel shape (variant of nb_batched_variant_info, -1 = built-in), steps
+ * per launch S >= 1, persistent grid cap (0 = #SMs x resident CTAs) and
+ * graph use (0 = plain launches).  Used by the autotuner. */
+nb_status nb_batched_set_tuning(nb_batch *b, int32_t variant,
+                                int32_t steps_per_launch, int32_t grid_ctas,
+                                int32_t use_graph);
+nb_status nb_batched_variant_info(int32_t v, int32_t *precision, int32_t *ipt,
+                                  int32_t *threads);
+
+/* Per-cluster FP64 kinetic and softened potential energy into host arrays
+ * of n_clusters entries (either may be NULL).  Synchronises. */
+nb_status nb_batched_energy(nb_batch *b, double *kin, double *pot);
+
+/* Copy the concatenated state to host (N,3) arrays (any may be NULL). */
+nb_status nb_batched_get_state(nb_batch *b, double *x, double *v, double *a,
+                               double *jerk);
+nb_status nb_batched_sync(nb_batch *b);
+int64_t nb_batched_launch_count(const nb_batch *b);
+
 const char *nb_status_string(nb_status s);
 const char *nb_last_error(void); /* message of the last error on this thread */
 

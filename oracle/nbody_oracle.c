@@ -125,6 +125,38 @@ void orc_force_jerk(int64_t n, const double *m, const double *x,
   }
 }
 
+/* Condition of the force and jerk sums of particle i: the sums of the
+ * magnitudes of the individual pair terms, sum_j |G m_j d / s^3| and
+ * sum_j |G m_j (w / s^3 - 3 (d.w) d / s^5)|.  An error bound of a
+ * floating-point sum scales with these, not with the magnitude of the sum. */
+void orc_force_jerk_abs(int64_t n, const double *m, const double *x,
+                        const double *v, double G, double eps, int64_t n_i,
+                        const int64_t *idx, double *aabs, double *jabs) {
+  const double e2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t k = 0; k < n_i; ++k) {
+    int64_t i = idx ? idx[k] : k;
+    double sa = 0.0, sj = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double dx = x[3 * j + 0] - x[3 * i + 0];
+      double dy = x[3 * j + 1] - x[3 * i + 1];
+      double dz = x[3 * j + 2] - x[3 * i + 2];
+      double wx = v[3 * j + 0] - v[3 * i + 0];
+      double wy = v[3 * j + 1] - v[3 * i + 1];
+      double wz = v[3 * j + 2] - v[3 * i + 2];
+      double s2 = dx * dx + dy * dy + dz * dz + e2;
+      double f = m[j] / (s2 * sqrt(s2));
+      double c = 3.0 * (dx * wx + dy * wy + dz * wz) / s2;
+      double tx = wx - c * dx, ty = wy - c * dy, tz = wz - c * dz;
+      sa += f * sqrt(dx * dx + dy * dy + dz * dz);
+      sj += f * sqrt(tx * tx + ty * ty + tz * tz);
+    }
+    aabs[k] = G * sa;
+    jabs[k] = G * sj;
+  }
+}
+
 /* ------------------------------------------------------------------------
  * Energy: K = 1/2 sum m v^2, W = -G sum_{i<j} m_i m_j / sqrt(r^2 + eps^2).
  * Per-i partial sums are added in ascending i order (thread-independent).

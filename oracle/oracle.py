@@ -59,6 +59,7 @@ def lib():
             L.orc_max_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_force_jerk.argtypes = [i64, vp, vp, vp, d, d, i64, vp, vp, vp]
+            L.orc_force_jerk_abs.argtypes = [i64, vp, vp, vp, d, d, i64, vp, vp, vp]
             L.orc_energy.argtypes = [i64, vp, vp, vp, d, d, vp, vp]
             L.orc_predict.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
             L.orc_aarseth_dt.argtypes = [vp, vp, vp, vp, d]
@@ -120,6 +121,26 @@ def force_jerk(m, x, v, eps, G=1.0, idx=None):
     lib().orc_force_jerk(n, _p(m), _p(x), _p(v), float(G), float(eps), n_i, _p(ip),
                          _p(acc), _p(jerk))
     return acc, jerk
+
+
+def force_jerk_abs(m, x, v, eps, G=1.0, idx=None):
+    """Sums of the magnitudes of the pair terms of the acceleration and the
+    jerk on particles ``idx`` (the condition of each sum).  Returns two
+    arrays of shape (n_i,)."""
+    m = _f64(m)
+    n = m.shape[0]
+    x = _f64(x, (n, 3))
+    v = _f64(v, (n, 3))
+    if idx is None:
+        n_i, ip = n, None
+    else:
+        ip = np.ascontiguousarray(idx, dtype=np.int64)
+        n_i = ip.shape[0]
+    aabs = np.zeros(n_i)
+    jabs = np.zeros(n_i)
+    lib().orc_force_jerk_abs(n, _p(m), _p(x), _p(v), float(G), float(eps), n_i, _p(ip),
+                             _p(aabs), _p(jabs))
+    return aabs, jabs
 
 
 def acc(m, x, eps, G=1.0):

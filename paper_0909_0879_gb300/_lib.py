@@ -65,6 +65,16 @@ SIGNATURES = [
     ("nb_set_force_variant", C.c_int, [_vp, _i32, _i32]),
     ("nb_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     ("nb_debug_inject", C.c_int, [_vp, _i32]),
+    ("nb_batched_init", C.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _vp, _P(Config)]),
+    ("nb_batched_destroy", None, [_vp]),
+    ("nb_batched_run", C.c_int, [_vp, _i64]),
+    ("nb_batched_run_per_cluster", C.c_int, [_vp, _i64]),
+    ("nb_batched_set_tuning", C.c_int, [_vp, _i32, _i32, _i32, _i32]),
+    ("nb_batched_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32)]),
+    ("nb_batched_energy", C.c_int, [_vp, _vp, _vp]),
+    ("nb_batched_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    ("nb_batched_sync", C.c_int, [_vp]),
+    ("nb_batched_launch_count", _i64, [_vp]),
     ("nb_status_string", C.c_char_p, [C.c_int]),
     ("nb_last_error", C.c_char_p, []),
 ]
@@ -161,9 +171,12 @@ class NBody:
         cfg.block_steps = 1 if block_steps else 0
         cfg.lev_shared = int(lev_shared)
         cfg.sync_timeout_ms = int(sync_timeout_ms)
-        cfg.stream = _ptr(stream) if stream is not None and not isinstance(stream, int) else stream
-        if stream is not None and hasattr(stream, "cuda_stream"):
-            cfg.stream = stream.cuda_stream
+        if stream is None:
+            cfg.stream = None
+        elif hasattr(stream, "cuda_stream"):  # torch.cuda.Stream
+            cfg.stream = stream.cuda_stream or None
+        else:
+            cfg.stream = int(stream) or None
         self.cfg = cfg
         self.n = n
         h = C.c_void_p()
@@ -304,3 +317,93 @@ class NBody:
 
     def inject(self, kind: int):
         _check(self._L.nb_debug_inject(self._h, int(kind)))
+
+
+def batched_variant_info(v: int):
+    L = load()
+    p, i, t = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(L.nb_batched_variant_info(v, C.byref(p), C.byref(i), C.byref(t)))
+    return {"precision": p.value, "ipt": i.value, "threads": t.value}
+
+
+def num_batched_variants() -> int:
+    v = 0
+    L = load()
+    while L.nb_batched_variant_info(v, None, None, None) == NB_OK:
+        v += 1
+    return v
+
+
+class Batch:
+    """Many independent clusters advanced together with a shared step
+    (one libnbody batched context).  ``offsets`` has n_clusters + 1 entries;
+    cluster c is particles offsets[c]:offsets[c+1] of m, x, v."""
+
+    def __init__(self, offsets, m, x, v, *, G=1.0, eps=1e-3, lev_shared=8, precision="ds",
+                 stream=None):
+        L = load()
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        n = m.shape[0]
+        x = _f64(x, (n, 3))
+        v = _f64(v, (n, 3))
+        cfg = default_config()
+        cfg.G, cfg.eps = float(G), float(eps)
+        cfg.block_steps = 0
+        cfg.lev_shared = int(lev_shared)
+        cfg.precision = NB_DS if precision in ("ds", NB_DS) else NB_FP32
+        if stream is not None:
+            cfg.stream = (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)) or None
+        self.n_clusters = off.shape[0] - 1
+        self.n = n
+        self.offsets = off
+        h = C.c_void_p()
+        _check(L.nb_batched_init(C.byref(h), self.n_clusters, off.ctypes.data, m.ctypes.data,
+                                 x.ctypes.data, v.ctypes.data, C.byref(cfg)))
+        self._h = h
+        self._L = L
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.nb_batched_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, nsteps: int):
+        _check(self._L.nb_batched_run(self._h, int(nsteps)))
+
+    def run_per_cluster(self, nsteps: int):
+        _check(self._L.nb_batched_run_per_cluster(self._h, int(nsteps)))
+
+    def set_tuning(self, variant=-1, steps_per_launch=1000, grid_ctas=0, use_graph=True):
+        _check(self._L.nb_batched_set_tuning(self._h, int(variant), int(steps_per_launch),
+                                             int(grid_ctas), 1 if use_graph else 0))
+
+    def energy(self):
+        k = np.zeros(self.n_clusters)
+        w = np.zeros(self.n_clusters)
+        _check(self._L.nb_batched_energy(self._h, k.ctypes.data, w.ctypes.data))
+        return k, w
+
+    def get_state(self):
+        out = {k: np.zeros((self.n, 3)) for k in ("x", "v", "a", "jerk")}
+        _check(self._L.nb_batched_get_state(self._h, out["x"].ctypes.data, out["v"].ctypes.data,
+                                            out["a"].ctypes.data, out["jerk"].ctypes.data))
+        return out
+
+    def sync(self):
+        _check(self._L.nb_batched_sync(self._h))
+
+    def launch_count(self) -> int:
+        return int(self._L.nb_batched_launch_count(self._h))

@@ -30,6 +30,18 @@ nb_status fail(nb_status s, const char *fmt, ...) {
   return s;
 }
 
+}  // namespace
+
+int nbi::set_error(int status, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+namespace {
+
 #define NB_CUDA(call)                                                        \
   do {                                                                       \
     cudaError_t e_ = (call);                                                 \

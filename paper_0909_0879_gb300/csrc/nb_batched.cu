@@ -1,0 +1,632 @@
+// Batched form: thousands of independent small clusters advanced with the
+// shared-step Hermite-4 scheme by one persistent kernel.
+//
+// Each CTA takes a cluster from a work queue (largest first) and advances
+// it S steps without leaving the SM: the cluster's predicted j-records live
+// in shared memory, every thread owns IPT i-particles, the force + jerk sum
+// runs over the shared-memory records (split precision as in the main
+// kernel, paper Sec. 4 software double precision), and the owning thread
+// applies the FP64 corrector right after its sums are complete.  The FP64
+// state is read and written in global memory (it stays in L2 for the
+// workload's ~100 MB).  A sequence of such launches is captured in a CUDA
+// graph and replayed.
+//
+// Threads per i-particle adapt to the cluster size: small clusters spread
+// each i-particle's j-range over up to 32 lanes and meet by a warp-shuffle
+// butterfly, so a 16-body cluster still occupies the whole CTA.
+#include "../../include/nbody.h"
+#include "nb_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <vector>
+
+namespace nbi {
+namespace {
+
+constexpr int kBatchFold = 32;  // j per thread between acceleration folds
+
+struct BatchArgs {
+  int32_t n_items;        // clusters in this launch's queue
+  const int64_t *off;     // cluster offsets (n_clusters + 1)
+  const int32_t *order;   // queue -> cluster index
+  int *queue;             // work counter (zeroed before the launch)
+  double *x, *v, *a, *jk; // FP64 state, (N, 3)
+  const double *m;
+  double dt;              // shared step
+  float eps2;
+  double G;
+  int nsteps;             // steps per launch (>= 1)
+  int cap;                // shared-memory record capacity
+  int init_only;          // 1: evaluate a, j at the current state only
+};
+
+__device__ __forceinline__ void bds_add(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
+__device__ __forceinline__ void bpredict(const double *x, const double *v, const double *a,
+                                         const double *jk, int64_t i, double dt, double xp[3],
+                                         double vp[3]) {
+  const double h2 = 0.5 * dt, h3 = dt * (1.0 / 3.0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double xc = x[3 * i + c], vc = v[3 * i + c];
+    const double ac = a[3 * i + c], jc = jk[3 * i + c];
+    xp[c] = xc + dt * (vc + h2 * (ac + h3 * jc));
+    vp[c] = vc + dt * (ac + h2 * jc);
+  }
+}
+
+template <int PREC, int IPT, int NT, int MASK>
+__global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs B) {
+  constexpr int NARR = PREC ? 3 : 2;
+  extern __shared__ __align__(16) float4 srec[];
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  const float eps2 = B.eps2;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(B.queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= B.n_items) return;  // uniform
+    const int c = B.order[item];
+    const int64_t base = B.off[c];
+    const int n = static_cast<int>(B.off[c + 1] - base);
+    int tpi = 1;
+    while (tpi < 32 && (NT / (tpi * 2)) * IPT >= n) tpi *= 2;
+    const int ng = NT / tpi;
+    const int bi = ng * IPT;
+    const int g = tid / tpi;
+    const int r = tid % tpi;
+    float4 *s_hi = srec;
+    float4 *s_lo = srec + B.cap;
+    float4 *s_v = srec + (NARR - 1) * B.cap;
+    const double dt = B.init_only ? 0.0 : B.dt;
+    const int nsteps = B.init_only ? 1 : B.nsteps;
+
+    for (int step = 0; step < nsteps; ++step) {
+      for (int p = tid; p < n; p += NT) {
+        double xp[3], vp[3];
+        bpredict(B.x, B.v, B.a, B.jk, base + p, dt, xp, vp);
+        const float hx = __double2float_rn(xp[0]);
+        const float hy = __double2float_rn(xp[1]);
+        const float hz = __double2float_rn(xp[2]);
+        s_hi[p] = make_float4(hx, hy, hz, __double2float_rn(B.m[base + p]));
+        if (PREC)
+          s_lo[p] = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
+                                __double2float_rn(xp[1] - static_cast<double>(hy)),
+                                __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
+        s_v[p] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                             __double2float_rn(vp[2]), 0.f);
+      }
+      __syncthreads();
+      for (int i0 = 0; i0 < n; i0 += bi) {
+        float xh[IPT][3], xl[IPT][3], vi[IPT][3];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+          const int i = i0 + g + q * ng;
+          const int ii = i < n ? i : 0;
+          const float4 h = s_hi[ii];
+          const float4 w = s_v[ii];
+          xh[q][0] = h.x; xh[q][1] = h.y; xh[q][2] = h.z;
+          vi[q][0] = w.x; vi[q][1] = w.y; vi[q][2] = w.z;
+          if (PREC) {
+            const float4 l = s_lo[ii];
+            xl[q][0] = l.x; xl[q][1] = l.y; xl[q][2] = l.z;
+          } else {
+            xl[q][0] = xl[q][1] = xl[q][2] = 0.f;
+          }
+        }
+        float ah[IPT][3], al[IPT][3], p1[IPT][3], p2[IPT][3];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) ah[q][k] = al[q][k] = p1[q][k] = p2[q][k] = 0.f;
+        for (int j0 = r; j0 < n; j0 += kBatchFold * tpi) {
+          const int jend = min(n, j0 + kBatchFold * tpi);
+          float pa[IPT][3];
+#pragma unroll
+          for (int q = 0; q < IPT; ++q)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) pa[q][k] = 0.f;
+#pragma unroll 4
+          for (int j = j0; j < jend; j += tpi) {
+            const float4 hj = s_hi[j];
+            const float4 wj = s_v[j];
+            float4 lj;
+            if (PREC) lj = s_lo[j];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+              float dx, dy, dz;
+              if (PREC) {
+                dx = (hj.x - xh[q][0]) + (lj.x - xl[q][0]);
+                dy = (hj.y - xh[q][1]) + (lj.y - xl[q][1]);
+                dz = (hj.z - xh[q][2]) + (lj.z - xl[q][2]);
+              } else {
+                dx = hj.x - xh[q][0];
+                dy = hj.y - xh[q][1];
+                dz = hj.z - xh[q][2];
+              }
+              const float ux = wj.x - vi[q][0];
+              const float uy = wj.y - vi[q][1];
+              const float uz = wj.z - vi[q][2];
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+              float rinv;
+              if (MASK)
+                rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+              else
+                rinv = rsqrtf(r2);
+              const float rinv2 = rinv * rinv;
+              const float mr3 = (hj.w * rinv) * rinv2;
+              const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+              const float cc = (rv * rinv2) * mr3;
+              pa[q][0] = fmaf(mr3, dx, pa[q][0]);
+              pa[q][1] = fmaf(mr3, dy, pa[q][1]);
+              pa[q][2] = fmaf(mr3, dz, pa[q][2]);
+              p1[q][0] = fmaf(mr3, ux, p1[q][0]);
+              p1[q][1] = fmaf(mr3, uy, p1[q][1]);
+              p1[q][2] = fmaf(mr3, uz, p1[q][2]);
+              p2[q][0] = fmaf(cc, dx, p2[q][0]);
+              p2[q][1] = fmaf(cc, dy, p2[q][1]);
+              p2[q][2] = fmaf(cc, dz, p2[q][2]);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < IPT; ++q)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              if (PREC)
+                bds_add(ah[q][k], al[q][k], pa[q][k]);
+              else
+                ah[q][k] += pa[q][k];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+          double o[6];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            o[k] = static_cast<double>(ah[q][k]) + static_cast<double>(al[q][k]);
+            o[3 + k] = static_cast<double>(fmaf(-3.f, p2[q][k], p1[q][k]));
+          }
+          for (int off = 1; off < tpi; off <<= 1)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) o[k] += __shfl_xor_sync(0xffffffffu, o[k], off);
+          const int i = i0 + g + q * ng;
+          if (r == 0 && i < n) {
+            const int64_t gi = base + i;
+            if (B.init_only) {
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                B.a[3 * gi + k] = B.G * o[k];
+                B.jk[3 * gi + k] = B.G * o[3 + k];
+              }
+            } else {
+              double xp[3], vp[3];
+              bpredict(B.x, B.v, B.a, B.jk, gi, dt, xp, vp);
+              const double dt2 = dt * dt, dt3 = dt2 * dt;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const double a0 = B.a[3 * gi + k], j0v = B.jk[3 * gi + k];
+                const double an = B.G * o[k], jn = B.G * o[3 + k];
+                const double da = a0 - an;
+                const double snap = (-6.0 * da - dt * (4.0 * j0v + 2.0 * jn)) / dt2;
+                const double crackle = (12.0 * da + 6.0 * dt * (j0v + jn)) / dt3;
+                B.x[3 * gi + k] =
+                    xp[k] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
+                B.v[3 * gi + k] = vp[k] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
+                B.a[3 * gi + k] = an;
+                B.jk[3 * gi + k] = jn;
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Per-cluster FP64 energy: one CTA per cluster, fixed-order reductions.
+__global__ void batched_energy_kernel(int32_t n_clusters, const int64_t *__restrict__ off,
+                                      const double *__restrict__ m, const double *__restrict__ x,
+                                      const double *__restrict__ v, double G, double eps2,
+                                      double *__restrict__ kin, double *__restrict__ pot) {
+  __shared__ double sk[256], sw[256];
+  const int c = blockIdx.x;
+  if (c >= n_clusters) return;
+  const int64_t base = off[c];
+  const int n = static_cast<int>(off[c + 1] - base);
+  double k = 0.0, w = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t gi = base + i;
+    const double vx = v[3 * gi], vy = v[3 * gi + 1], vz = v[3 * gi + 2];
+    k += 0.5 * m[gi] * (vx * vx + vy * vy + vz * vz);
+    double wi = 0.0;
+    for (int j = i + 1; j < n; ++j) {
+      const int64_t gj = base + j;
+      const double dx = x[3 * gj] - x[3 * gi], dy = x[3 * gj + 1] - x[3 * gi + 1],
+                   dz = x[3 * gj + 2] - x[3 * gi + 2];
+      wi += m[gj] / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+    }
+    w += m[gi] * wi;
+  }
+  sk[threadIdx.x] = k;
+  sw[threadIdx.x] = w;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sk[threadIdx.x] += sk[threadIdx.x + s];
+      sw[threadIdx.x] += sw[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    kin[c] = sk[0];
+    pot[c] = -G * sw[0];
+  }
+}
+
+using BKernel = void (*)(const BatchArgs);
+struct BEntry {
+  int prec, ipt, threads, mask;
+  BKernel fn;
+};
+#define NB_BV(P, I, T, M) BEntry{P, I, T, M, &batched_hermite_kernel<P, I, T, M>}
+const BEntry kBTable[] = {
+    NB_BV(1, 2, 256, 0), NB_BV(1, 1, 256, 0), NB_BV(1, 2, 128, 0), NB_BV(1, 1, 128, 0),
+    NB_BV(0, 2, 256, 0), NB_BV(0, 1, 256, 0), NB_BV(0, 2, 128, 0), NB_BV(0, 1, 128, 0),
+    NB_BV(1, 2, 256, 1), NB_BV(0, 2, 256, 1),
+};
+constexpr int kNumBVariants = sizeof(kBTable) / sizeof(kBTable[0]);
+
+}  // namespace
+}  // namespace nbi
+
+using namespace nbi;
+
+struct nb_batch {
+  int32_t n_clusters = 0;
+  int64_t n = 0;
+  int max_n = 0;
+  nb_config cfg{};
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  double *m = nullptr, *x = nullptr, *v = nullptr, *a = nullptr, *jk = nullptr;
+  int64_t *off = nullptr;
+  int32_t *order = nullptr;   // largest cluster first
+  int32_t *ident = nullptr;   // 0..n_clusters-1 (per-cluster launches)
+  int *counters = nullptr;
+  int n_counters = 0;
+  double *ekin = nullptr, *epot = nullptr;
+  int variant = -1, steps_per_launch = 1000, grid_cap = 0, use_graph = 1;
+  int64_t launches = 0;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_steps = -1;
+  int graph_key[4] = {0, 0, 0, 0};
+  cudaEvent_t ev = nullptr;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+nb_status bfail(nb_status s, const char *msg, cudaError_t e = cudaSuccess) {
+  if (e != cudaSuccess)
+    return static_cast<nb_status>(
+        set_error(e == cudaErrorMemoryAllocation ? NB_ERR_OOM : s, "%s: %s", msg,
+                  cudaGetErrorString(e)));
+  return static_cast<nb_status>(set_error(s, "%s", msg));
+}
+
+#define BCUDA(call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return bfail(NB_ERR_CUDA, #call, e_); \
+  } while (0)
+
+int pick_bvariant(const nb_batch *b) {
+  if (b->variant >= 0) return b->variant;
+  const int mask = b->cfg.eps == 0.0 ? 1 : 0;
+  if (mask) return b->cfg.precision ? 8 : 9;
+  return b->cfg.precision ? 0 : 4;
+}
+
+size_t bsmem(const BEntry &E, int cap) {
+  return static_cast<size_t>(E.prec ? 3 : 2) * cap * sizeof(float4);
+}
+
+int bgrid(nb_batch *b, int v) {
+  const BEntry &E = kBTable[v];
+  const size_t sm = bsmem(E, b->max_n);
+  cudaFuncSetAttribute(E.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+  int per = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, E.fn, E.threads, sm) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  int grid = b->num_sms * per;
+  if (b->grid_cap > 0 && b->grid_cap < grid) grid = b->grid_cap;
+  return std::min(grid, std::max(1, b->n_clusters));
+}
+
+nb_status launch_batch(nb_batch *b, int v, int grid, int32_t n_items, const int32_t *order,
+                       int *counter, int nsteps, int init_only) {
+  const BEntry &E = kBTable[v];
+  BatchArgs A;
+  A.n_items = n_items;
+  A.off = b->off;
+  A.order = order;
+  A.queue = counter;
+  A.x = b->x;
+  A.v = b->v;
+  A.a = b->a;
+  A.jk = b->jk;
+  A.m = b->m;
+  A.dt = std::ldexp(1.0, -b->cfg.lev_shared);
+  A.eps2 = static_cast<float>(b->cfg.eps * b->cfg.eps);
+  A.G = b->cfg.G;
+  A.nsteps = nsteps;
+  A.cap = b->max_n;
+  A.init_only = init_only;
+  E.fn<<<grid, E.threads, bsmem(E, b->max_n), b->stream>>>(A);
+  BCUDA(cudaGetLastError());
+  b->launches += 1;
+  return NB_OK;
+}
+
+nb_status bsync(nb_batch *b) {
+  BCUDA(cudaEventRecord(b->ev, b->stream));
+  BCUDA(cudaEventSynchronize(b->ev));
+  return NB_OK;
+}
+
+// Queue the persistent launches for nsteps steps on the stream (variant v
+// on `grid` CTAs, both chosen before any stream capture begins).
+nb_status queue_persistent(nb_batch *b, int64_t nsteps, int v, int grid) {
+  const int S = std::max(1, b->steps_per_launch);
+  const int64_t nl = (nsteps + S - 1) / S;
+  if (nl > b->n_counters) return bfail(NB_ERR_INVALID_ARG, "too many launches for the counter array");
+  BCUDA(cudaMemsetAsync(b->counters, 0, sizeof(int) * nl, b->stream));
+  for (int64_t k = 0; k < nl; ++k) {
+    const int s = static_cast<int>(std::min<int64_t>(S, nsteps - k * S));
+    nb_status st = launch_batch(b, v, grid, b->n_clusters, b->order, b->counters + k, s, 0);
+    if (st != NB_OK) return st;
+  }
+  return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nb_status nb_batched_init(nb_batch **out, int32_t n_clusters, const int64_t *offsets,
+                          const double *m, const double *x, const double *v,
+                          const nb_config *cfg) {
+  if (!out) return bfail(NB_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (n_clusters < 1 || !offsets || !m || !x || !v || !cfg)
+    return bfail(NB_ERR_INVALID_ARG, "need n_clusters >= 1 and non-null arrays");
+  if (offsets[0] != 0) return bfail(NB_ERR_INVALID_ARG, "offsets[0] must be 0");
+  int max_n = 0;
+  for (int32_t c = 0; c < n_clusters; ++c) {
+    const int64_t nc = offsets[c + 1] - offsets[c];
+    if (nc < 1 || nc > 4096) return bfail(NB_ERR_INVALID_ARG, "cluster sizes must be in [1, 4096]");
+    max_n = std::max<int>(max_n, static_cast<int>(nc));
+  }
+  const int64_t n = offsets[n_clusters];
+  if (cfg->block_steps) return bfail(NB_ERR_INVALID_ARG, "the batched form uses a shared step (block_steps = 0)");
+  if (cfg->lev_shared < 0 || cfg->lev_shared > kTicksLog2)
+    return bfail(NB_ERR_INVALID_ARG, "need 0 <= lev_shared <= 20");
+  if (!(std::isfinite(cfg->eps) && cfg->eps >= 0) || !(std::isfinite(cfg->G) && cfg->G > 0))
+    return bfail(NB_ERR_INVALID_ARG, "bad eps or G");
+  if (cfg->precision != NB_FP32 && cfg->precision != NB_DS)
+    return bfail(NB_ERR_INVALID_ARG, "precision must be NB_FP32 or NB_DS");
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(x[i]) || !std::isfinite(v[i]))
+      return bfail(NB_ERR_INVALID_ARG, "non-finite position or velocity");
+  for (int64_t i = 0; i < n; ++i)
+    if (!(m[i] >= 0)) return bfail(NB_ERR_INVALID_ARG, "negative or non-finite mass");
+
+  nb_batch *b = new nb_batch();
+  b->n_clusters = n_clusters;
+  b->n = n;
+  b->max_n = max_n;
+  b->cfg = *cfg;
+  b->stream = static_cast<cudaStream_t>(cfg->stream);
+  int dev = 0;
+  auto cleanup = [&](nb_status s) {
+    nb_batched_destroy(b);
+    return s;
+  };
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cleanup(bfail(NB_ERR_CUDA, "no CUDA device"));
+  auto alloc = [&](void **p, size_t bytes) -> nb_status {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      return bfail(NB_ERR_CUDA, "cudaMalloc", e);
+    }
+    b->allocs.push_back(*p);
+    return NB_OK;
+  };
+  const size_t n3 = 3 * static_cast<size_t>(n) * sizeof(double);
+  b->n_counters = std::max(1024, n_clusters);
+  nb_status st = NB_OK;
+  if ((st = alloc(reinterpret_cast<void **>(&b->m), n * sizeof(double))) ||
+      (st = alloc(reinterpret_cast<void **>(&b->x), n3)) ||
+      (st = alloc(reinterpret_cast<void **>(&b->v), n3)) ||
+      (st = alloc(reinterpret_cast<void **>(&b->a), n3)) ||
+      (st = alloc(reinterpret_cast<void **>(&b->jk), n3)) ||
+      (st = alloc(reinterpret_cast<void **>(&b->off), (n_clusters + 1) * sizeof(int64_t))) ||
+      (st = alloc(reinterpret_cast<void **>(&b->order), n_clusters * sizeof(int32_t))) ||
+      (st = alloc(reinterpret_cast<void **>(&b->ident), n_clusters * sizeof(int32_t))) ||
+      (st = alloc(reinterpret_cast<void **>(&b->counters), b->n_counters * sizeof(int))) ||
+      (st = alloc(reinterpret_cast<void **>(&b->ekin), n_clusters * sizeof(double))) ||
+      (st = alloc(reinterpret_cast<void **>(&b->epot), n_clusters * sizeof(double))))
+    return cleanup(st);
+  if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(bfail(NB_ERR_CUDA, "event creation failed"));
+  // processing order: largest cost (n^2) first, ties by index
+  std::vector<int32_t> order(n_clusters), ident(n_clusters);
+  std::iota(order.begin(), order.end(), 0);
+  std::iota(ident.begin(), ident.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t q) {
+    return (offsets[p + 1] - offsets[p]) > (offsets[q + 1] - offsets[q]);
+  });
+  cudaStream_t s = b->stream;
+  if (cudaMemcpyAsync(b->m, m, n * sizeof(double), cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(b->x, x, n3, cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(b->v, v, n3, cudaMemcpyHostToDevice, s) ||
+      cudaMemsetAsync(b->a, 0, n3, s) || cudaMemsetAsync(b->jk, 0, n3, s) ||
+      cudaMemcpyAsync(b->off, offsets, (n_clusters + 1) * sizeof(int64_t),
+                      cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(b->order, order.data(), n_clusters * sizeof(int32_t),
+                      cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(b->ident, ident.data(), n_clusters * sizeof(int32_t),
+                      cudaMemcpyHostToDevice, s) ||
+      cudaMemsetAsync(b->counters, 0, b->n_counters * sizeof(int), s))
+    return cleanup(bfail(NB_ERR_CUDA, "initial copies failed"));
+  const int vv = pick_bvariant(b);
+  st = launch_batch(b, vv, bgrid(b, vv), n_clusters, b->order, b->counters, 1, 1);
+  if (st != NB_OK) return cleanup(st);
+  st = bsync(b);
+  if (st != NB_OK) return cleanup(st);
+  *out = b;
+  return NB_OK;
+}
+
+void nb_batched_destroy(nb_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void *p : b->allocs)
+    if (p) cudaFree(p);
+  if (b->ev) cudaEventDestroy(b->ev);
+  delete b;
+}
+
+nb_status nb_batched_set_tuning(nb_batch *b, int32_t variant, int32_t steps_per_launch,
+                                int32_t grid_ctas, int32_t use_graph) {
+  if (!b) return bfail(NB_ERR_INVALID_ARG, "null batch");
+  if (variant >= kNumBVariants || variant < -1)
+    return bfail(NB_ERR_INVALID_ARG, "unknown batched variant");
+  if (variant >= 0) {
+    const BEntry &E = kBTable[variant];
+    if (E.prec != b->cfg.precision || E.mask != (b->cfg.eps == 0.0 ? 1 : 0))
+      return bfail(NB_ERR_INVALID_ARG, "variant precision or eps == 0 masking differs from the batch");
+  }
+  if (steps_per_launch < 1) return bfail(NB_ERR_INVALID_ARG, "steps_per_launch must be >= 1");
+  b->variant = variant;
+  b->steps_per_launch = steps_per_launch;
+  b->grid_cap = grid_ctas > 0 ? grid_ctas : 0;
+  b->use_graph = use_graph ? 1 : 0;
+  return NB_OK;
+}
+
+nb_status nb_batched_variant_info(int32_t v, int32_t *precision, int32_t *ipt, int32_t *threads) {
+  if (v < 0 || v >= kNumBVariants) return bfail(NB_ERR_INVALID_ARG, "unknown batched variant");
+  if (precision) *precision = kBTable[v].prec;
+  if (ipt) *ipt = kBTable[v].ipt;
+  if (threads) *threads = kBTable[v].threads;
+  return NB_OK;
+}
+
+nb_status nb_batched_run(nb_batch *b, int64_t nsteps) {
+  if (!b) return bfail(NB_ERR_INVALID_ARG, "null batch");
+  if (nsteps < 0) return bfail(NB_ERR_INVALID_ARG, "negative step count");
+  if (nsteps == 0) return NB_OK;
+  const int v = pick_bvariant(b);
+  const int grid = bgrid(b, v);
+  if (!b->use_graph) return queue_persistent(b, nsteps, v, grid);
+  const int key[4] = {v, b->steps_per_launch, b->grid_cap, grid};
+  if (!b->graph || b->graph_steps != nsteps || std::memcmp(key, b->graph_key, sizeof(key)) != 0) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    // Capture on a private stream so that capture never interferes with
+    // work another caller queued on the context stream.
+    cudaStream_t cs;
+    BCUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = b->stream;
+    b->stream = cs;
+    const int64_t l0 = b->launches;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    nb_status st = e == cudaSuccess ? queue_persistent(b, nsteps, v, grid) : NB_ERR_CUDA;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    b->stream = saved;
+    b->launches = l0;
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || e2 != cudaSuccess || st != NB_OK)
+      return bfail(NB_ERR_CUDA, "graph capture failed", e != cudaSuccess ? e : e2);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(NB_ERR_CUDA, "graph instantiation failed", e);
+    b->graph_steps = nsteps;
+    std::memcpy(b->graph_key, key, sizeof(key));
+  }
+  BCUDA(cudaGraphLaunch(b->graph, b->stream));
+  b->launches += (nsteps + b->steps_per_launch - 1) / b->steps_per_launch;
+  return NB_OK;
+}
+
+nb_status nb_batched_run_per_cluster(nb_batch *b, int64_t nsteps) {
+  if (!b) return bfail(NB_ERR_INVALID_ARG, "null batch");
+  if (nsteps < 0) return bfail(NB_ERR_INVALID_ARG, "negative step count");
+  const int v = pick_bvariant(b);
+  (void)bgrid(b, v);  // sets the kernel's shared-memory attribute
+  const int S = std::max(1, b->steps_per_launch);
+  for (int64_t k = 0; k * S < nsteps; ++k) {
+    const int s = static_cast<int>(std::min<int64_t>(S, nsteps - k * S));
+    BCUDA(cudaMemsetAsync(b->counters, 0, sizeof(int) * b->n_clusters, b->stream));
+    for (int32_t c = 0; c < b->n_clusters; ++c) {
+      nb_status st = launch_batch(b, v, 1, 1, b->ident + c, b->counters + c, s, 0);
+      if (st != NB_OK) return st;
+    }
+  }
+  return NB_OK;
+}
+
+nb_status nb_batched_energy(nb_batch *b, double *kin, double *pot) {
+  if (!b) return bfail(NB_ERR_INVALID_ARG, "null batch");
+  batched_energy_kernel<<<b->n_clusters, 256, 0, b->stream>>>(
+      b->n_clusters, b->off, b->m, b->x, b->v, b->cfg.G, b->cfg.eps * b->cfg.eps, b->ekin,
+      b->epot);
+  BCUDA(cudaGetLastError());
+  b->launches += 1;
+  if (kin)
+    BCUDA(cudaMemcpyAsync(kin, b->ekin, b->n_clusters * sizeof(double), cudaMemcpyDeviceToHost,
+                          b->stream));
+  if (pot)
+    BCUDA(cudaMemcpyAsync(pot, b->epot, b->n_clusters * sizeof(double), cudaMemcpyDeviceToHost,
+                          b->stream));
+  return bsync(b);
+}
+
+nb_status nb_batched_get_state(nb_batch *b, double *x, double *v, double *a, double *jerk) {
+  if (!b) return bfail(NB_ERR_INVALID_ARG, "null batch");
+  const size_t n3 = 3 * static_cast<size_t>(b->n) * sizeof(double);
+  if (x) BCUDA(cudaMemcpyAsync(x, b->x, n3, cudaMemcpyDeviceToHost, b->stream));
+  if (v) BCUDA(cudaMemcpyAsync(v, b->v, n3, cudaMemcpyDeviceToHost, b->stream));
+  if (a) BCUDA(cudaMemcpyAsync(a, b->a, n3, cudaMemcpyDeviceToHost, b->stream));
+  if (jerk) BCUDA(cudaMemcpyAsync(jerk, b->jk, n3, cudaMemcpyDeviceToHost, b->stream));
+  return bsync(b);
+}
+
+nb_status nb_batched_sync(nb_batch *b) {
+  if (!b) return bfail(NB_ERR_INVALID_ARG, "null batch");
+  return bsync(b);
+}
+
+int64_t nb_batched_launch_count(const nb_batch *b) { return b ? b->launches : -1; }
+
+}  // extern "C"

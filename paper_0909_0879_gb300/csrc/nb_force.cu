@@ -18,10 +18,11 @@
 //    issuing.  No cluster multicast.
 //  * Split precision ("double-single", after Gaburov, Harfst & Portegies
 //    Zwart 2009, cited in the paper's Sec. 4): positions are hi + lo FP32
-//    pairs and d = (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo); the per-tile FP32
-//    partial sums are folded into hi + lo accumulators with an error-free
-//    two-sum once per tile, so the split-precision overhead is per tile, not
-//    per pair, except for the three extra subtractions per coordinate.
+//    pairs and d = (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo); FP32 partial sums
+//    over short runs of j (32 per thread for the acceleration, a 256-record
+//    tile for the jerk) are folded into hi + lo accumulators with an
+//    error-free two-sum, so the split-precision overhead is per run, not per
+//    pair, except for the three extra subtractions per coordinate.
 //  * Work decomposition: the (i-block, j-tile) space is cut into equal
 //    contiguous ranges, one per persistent CTA (a "stream-K" split), so every
 //    active-list length fills the GPU evenly.  An i-block whose j-range spans
@@ -38,6 +39,10 @@
 namespace nbi {
 
 namespace {
+
+// j-records per thread between two folds of the acceleration sums into the
+// split-precision accumulators.
+constexpr int kFoldChunk = 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -190,67 +195,87 @@ __global__ void __launch_bounds__(NT, 1)
       const float4 *sl = sh + kJT;
       const float4 *sv = sh + (NARR - 1) * kJT;
 
-      float pa[IPT][3], p1[IPT][3], p2[IPT][3];
+      float p1[IPT][3], p2[IPT][3];
 #pragma unroll
       for (int q = 0; q < IPT; ++q)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) pa[q][c] = p1[q][c] = p2[q][c] = 0.f;
+        for (int c = 0; c < 3; ++c) p1[q][c] = p2[q][c] = 0.f;
 
-#pragma unroll 4
-      for (int jj = r; jj < kJT; jj += TPI) {
-        const float4 hj = sh[jj];
-        const float4 wj = sv[jj];
-        float4 lj;
-        if (PREC) lj = sl[jj];
+      // The tile is walked in chunks of CH j-records per thread; the
+      // acceleration's FP32 chunk sums are folded into the accumulators after
+      // every chunk (a large close-pair term then only inflates the rounding
+      // of the few additions that follow it in its chunk), the jerk's once
+      // per tile (its tolerance is ten times looser).
+      constexpr int CH = (PREC && kFoldChunk < kJT / TPI) ? kFoldChunk : kJT / TPI;
+#pragma unroll 1
+      for (int c0 = r; c0 < kJT; c0 += CH * TPI) {
+        float pa[IPT][3];
 #pragma unroll
-        for (int q = 0; q < IPT; ++q) {
-          float dx, dy, dz;
-          if (PREC) {
-            dx = (hj.x - xh[q][0]) + (lj.x - xl[q][0]);
-            dy = (hj.y - xh[q][1]) + (lj.y - xl[q][1]);
-            dz = (hj.z - xh[q][2]) + (lj.z - xl[q][2]);
-          } else {
-            dx = hj.x - xh[q][0];
-            dy = hj.y - xh[q][1];
-            dz = hj.z - xh[q][2];
+        for (int q = 0; q < IPT; ++q)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) pa[q][c] = 0.f;
+#pragma unroll 4
+        for (int jj = c0; jj < c0 + CH * TPI; jj += TPI) {
+          const float4 hj = sh[jj];
+          const float4 wj = sv[jj];
+          float4 lj;
+          if (PREC) lj = sl[jj];
+#pragma unroll
+          for (int q = 0; q < IPT; ++q) {
+            float dx, dy, dz;
+            if (PREC) {
+              dx = (hj.x - xh[q][0]) + (lj.x - xl[q][0]);
+              dy = (hj.y - xh[q][1]) + (lj.y - xl[q][1]);
+              dz = (hj.z - xh[q][2]) + (lj.z - xl[q][2]);
+            } else {
+              dx = hj.x - xh[q][0];
+              dy = hj.y - xh[q][1];
+              dz = hj.z - xh[q][2];
+            }
+            const float ux = wj.x - vi[q][0];
+            const float uy = wj.y - vi[q][1];
+            const float uz = wj.z - vi[q][2];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            float rinv;
+            if (MASK)
+              rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+            else
+              rinv = rsqrtf(r2);
+            const float rinv2 = rinv * rinv;
+            const float mr3 = (hj.w * rinv) * rinv2;
+            const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+            const float cc = (rv * rinv2) * mr3;
+            pa[q][0] = fmaf(mr3, dx, pa[q][0]);
+            pa[q][1] = fmaf(mr3, dy, pa[q][1]);
+            pa[q][2] = fmaf(mr3, dz, pa[q][2]);
+            p1[q][0] = fmaf(mr3, ux, p1[q][0]);
+            p1[q][1] = fmaf(mr3, uy, p1[q][1]);
+            p1[q][2] = fmaf(mr3, uz, p1[q][2]);
+            p2[q][0] = fmaf(cc, dx, p2[q][0]);
+            p2[q][1] = fmaf(cc, dy, p2[q][1]);
+            p2[q][2] = fmaf(cc, dz, p2[q][2]);
           }
-          const float ux = wj.x - vi[q][0];
-          const float uy = wj.y - vi[q][1];
-          const float uz = wj.z - vi[q][2];
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-          float rinv;
-          if (MASK)
-            rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-          else
-            rinv = rsqrtf(r2);
-          const float rinv2 = rinv * rinv;
-          const float mr3 = (hj.w * rinv) * rinv2;
-          const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-          const float cc = (rv * rinv2) * mr3;
-          pa[q][0] = fmaf(mr3, dx, pa[q][0]);
-          pa[q][1] = fmaf(mr3, dy, pa[q][1]);
-          pa[q][2] = fmaf(mr3, dz, pa[q][2]);
-          p1[q][0] = fmaf(mr3, ux, p1[q][0]);
-          p1[q][1] = fmaf(mr3, uy, p1[q][1]);
-          p1[q][2] = fmaf(mr3, uz, p1[q][2]);
-          p2[q][0] = fmaf(cc, dx, p2[q][0]);
-          p2[q][1] = fmaf(cc, dy, p2[q][1]);
-          p2[q][2] = fmaf(cc, dz, p2[q][2]);
         }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (PREC)
+              ds_add(ah[q][c], al[q][c], pa[q][c]);
+            else
+              ah[q][c] += pa[q][c];
+          }
       }
-      // fold the tile's partial sums (jerk = p1 - 3 p2)
+      // fold the tile's jerk partial sums (jerk = p1 - 3 p2)
 #pragma unroll
       for (int q = 0; q < IPT; ++q)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float jt = fmaf(-3.f, p2[q][c], p1[q][c]);
-          if (PREC) {
-            ds_add(ah[q][c], al[q][c], pa[q][c]);
+          if (PREC)
             ds_add(jh[q][c], jl[q][c], jt);
-          } else {
-            ah[q][c] += pa[q][c];
+          else
             jh[q][c] += jt;
-          }
         }
       if (__syncthreads_or(!ok)) {
         // A copy never arrived: record it, wait (bounded) for the copies

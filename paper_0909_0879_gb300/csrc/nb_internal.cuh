@@ -37,6 +37,13 @@ struct ForceArgs {
   int *err;            // device error word
 };
 
+// Records the per-thread error message returned by nb_last_error() and
+// returns status unchanged (defined in nb_api.cu, shared by every C-ABI file).
+int set_error(int status, const char *fmt, ...);
+
+// Bytes of one j-record set per particle: FP32 (hi, vel) or DS (hi, lo, vel).
+inline int record_bytes(int prec) { return prec ? 48 : 32; }
+
 struct Variant {
   int prec;     // 0 = FP32, 1 = double-single
   int ipt;      // i-particles per thread

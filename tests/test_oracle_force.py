@@ -214,3 +214,29 @@ def test_interaction_count_matches_table1(oracle_mod):
         n, nf = float(n), float(nf)
         mine = 30.0 * pair_count(n)
         assert abs(mine - nf) / nf < 0.01, (name, mine, nf)
+
+
+def test_condition_sums(oracle_mod):
+    """sum_j |f_ij| >= |a_i| (triangle inequality), with equality when every
+    pair term points the same way (all other bodies on one ray from i), and
+    it is |a| for two bodies."""
+    m, x, v = ics.plummer(300, 17)
+    acc, jerk = oracle_mod.force_jerk(m, x, v, 1e-3)
+    aabs, jabs = oracle_mod.force_jerk_abs(m, x, v, 1e-3)
+    assert np.all(aabs >= np.linalg.norm(acc, axis=1) * (1 - 1e-14))
+    assert np.all(jabs >= np.linalg.norm(jerk, axis=1) * (1 - 1e-14))
+    xr = np.zeros((5, 3))
+    xr[:, 0] = [0.0, 1.0, 2.5, 3.0, 7.0]
+    vr = np.zeros((5, 3))
+    vr[:, 0] = [0.0, 0.1, 0.3, -0.2, 0.5]
+    mr = np.array([1.0, 0.5, 2.0, 0.25, 3.0])
+    a, jk = oracle_mod.force_jerk(mr, xr, vr, 0.0)
+    aa, ja = oracle_mod.force_jerk_abs(mr, xr, vr, 0.0)
+    assert abs(aa[0] - np.linalg.norm(a[0])) < 1e-14 * aa[0]
+    # on a line with radial velocities every jerk term is radial too, but the
+    # signs differ; the sum of magnitudes bounds it
+    assert ja[0] >= np.linalg.norm(jk[0])
+    a2, j2 = oracle_mod.force_jerk(mr[:2], xr[:2], vr[:2] + [[0, 0.3, 0]] * 2, 0.1)
+    aa2, ja2 = oracle_mod.force_jerk_abs(mr[:2], xr[:2], vr[:2] + [[0, 0.3, 0]] * 2, 0.1)
+    assert np.allclose(aa2, np.linalg.norm(a2, axis=1), rtol=1e-14)
+    assert np.allclose(ja2, np.linalg.norm(j2, axis=1), rtol=1e-14)

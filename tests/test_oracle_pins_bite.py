@@ -21,7 +21,8 @@ MUTANTS = {
                        "double s2 = dx * dx + dy * dy + dz * dz;\n    double sinv = 1.0 / sqrt(s2);\n    double sinv3"),
     "transposed_difference": ("double dy = x[3 * j + 1] - x[3 * i + 1];\n    double dz = x[3 * j + 2] - x[3 * i + 2];\n    double s2 = dx * dx + dy * dy + dz * dz + e2;\n    double sinv = 1.0 / sqrt(s2);\n    double sinv3",
                               "double dy = x[3 * i + 1] - x[3 * j + 1];\n    double dz = x[3 * j + 2] - x[3 * i + 2];\n    double s2 = dx * dx + dy * dy + dz * dz + e2;\n    double sinv = 1.0 / sqrt(s2);\n    double sinv3"),
-    "jerk_wrong_velocity_index": ("double wy = v[3 * j + 1] - v[3 * i + 1];", "double wy = v[3 * j + 1] - v[3 * i + 0];"),
+    "jerk_wrong_velocity_index": ("double wy = v[3 * j + 1] - v[3 * i + 1];\n      double wz = v[3 * j + 2] - v[3 * i + 2];\n      double dw",
+                                  "double wy = v[3 * j + 1] - v[3 * i + 0];\n      double wz = v[3 * j + 2] - v[3 * i + 2];\n      double dw"),
     "energy_half": ("k += 0.5 * m[i] * vv;", "k += m[i] * vv;"),
     "energy_unsoftened": ("w += m[j] / sqrt(dx * dx + dy * dy + dz * dz + e2);", "w += m[j] / sqrt(dx * dx + dy * dy + dz * dz);"),
     "predictor_coefficient": ("jk[c] * dt3 / 6.0;", "jk[c] * dt3 / 2.0;"),
