@@ -231,6 +231,46 @@ nb_status nb_batched_get_state(nb_batch *b, double *x, double *v, double *a,
 nb_status nb_batched_sync(nb_batch *b);
 int64_t nb_batched_launch_count(const nb_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free force + jerk.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let the library allocate device
+ * memory -- programs whose device memory all belongs to another allocator
+ * (a framework's caching allocator, a pool sized once at start-up), code
+ * that must not risk the device-wide synchronisation cudaMalloc/cudaFree can
+ * cause, and hosts that forbid allocation after initialisation.  It needs
+ * no context and calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ * Computes, on the caller's stream, the acceleration and jerk (eq. 1 and its
+ * time derivative, Plummer softening eps, constant G) on the particles
+ * d_idx[0..n_idx) (NULL: 0..n_idx-1, n_idx <= n) from all n particles.
+ * Inputs: d_m (n), d_x and d_v ((n,3) row-major), all float64 device
+ * arrays; outputs d_acc and d_jerk, float64 (n_idx,3), device.  precision:
+ * NB_FP32 or NB_DS.  Indices must lie in [0, n) (not checked on the device).
+ *
+ * Scratch: the partial sums of i-blocks split across CTAs live in one
+ * static device array of 2^20 doubles (8 MiB) that every GPU loading the
+ * library holds until the process exits; a launch uses at most 341 CTAs so
+ * that they fit, whatever n and n_idx are.  Every call shares that array
+ * and it keeps the last call's contents; each call writes every partial it
+ * later reads, so nothing needs clearing, but calls whose work overlaps on
+ * the GPU (other streams, or other host threads on the same device) race on
+ * it and must be serialised by the caller.
+ *
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current) and the kernel's
+ * occupancy; make that first call before any stream capture begins.
+ * Errors: NB_ERR_INVALID_ARG for n outside [1, 2^31-1], n_idx outside
+ * [0, 2^31-1] (or above n without an index list), a NULL pointer, eps < 0,
+ * G <= 0 or an unknown precision; NB_ERR_CUDA for a failed launch or set-up.
+ * Asynchronous; n_idx == 0 is a no-op.
+ * ---------------------------------------------------------------------- */
+nb_status nb_force_jerk_noalloc(int64_t n, const double *d_m,
+                                const double *d_x, const double *d_v,
+                                const int32_t *d_idx, int64_t n_idx,
+                                double eps, double G, int32_t precision,
+                                double *d_acc, double *d_jerk, void *stream);
+
 const char *nb_status_string(nb_status s);
 const char *nb_last_error(void); /* message of the last error on this thread */
 

@@ -75,6 +75,8 @@ SIGNATURES = [
     ("nb_batched_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("nb_batched_sync", C.c_int, [_vp]),
     ("nb_batched_launch_count", _i64, [_vp]),
+    ("nb_force_jerk_noalloc", C.c_int, [_i64, _vp, _vp, _vp, _vp, _i64, _d, _d, _i32, _vp,
+                                         _vp, _vp]),
     ("nb_status_string", C.c_char_p, [C.c_int]),
     ("nb_last_error", C.c_char_p, []),
 ]
@@ -407,3 +409,21 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(self._L.nb_batched_launch_count(self._h))
+
+
+def force_jerk_noalloc(n, d_m, d_x, d_v, d_idx, n_idx, d_acc, d_jerk, *, eps, G=1.0,
+                       precision="ds", stream=None):
+    """Allocation-free force + jerk on caller-owned device arrays (see
+    nb_force_jerk_noalloc in include/nbody.h).  Asynchronous on ``stream``
+    (a torch stream, a raw handle, or None for the default stream)."""
+    L = load()
+    if stream is None:
+        sp = None
+    elif hasattr(stream, "cuda_stream"):
+        sp = stream.cuda_stream or None
+    else:
+        sp = int(stream) or None
+    prec = NB_DS if precision in ("ds", NB_DS) else NB_FP32
+    _check(L.nb_force_jerk_noalloc(int(n), _ptr(d_m), _ptr(d_x), _ptr(d_v), _ptr(d_idx),
+                                   int(n_idx), float(eps), float(G), prec, _ptr(d_acc),
+                                   _ptr(d_jerk), sp))
