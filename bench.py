@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--variant", type=int, default=-1)
     p.add_argument("--grid", type=int, default=0)
+    p.add_argument("--workload", default="king1m",
+                   choices=["king1m", "shared1024", "block65536", "batched", "adjoint"],
+                   help="king1m is the headline; the others time the remaining workloads "
+                        "and print their own JSON line")
     p.add_argument("--sweep", action="store_true",
                    help="also time single evaluations at active fractions 2^-10..1")
     return p.parse_args()
@@ -416,8 +420,202 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------- other workloads
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_shared1024(args):
+    """N = 1024 equal-mass Plummer (seed 1001), eps = 1e-3, shared dt = 1/256
+    for one time unit (256 steps): interactions/s and conservation, FP32 and
+    DS."""
+    import torch
+
+    from paper_0909_0879_gb300 import _lib
+
+    n, eps, lev, steps = 1024, 1e-3, 8, 256
+    m, x, v = ics.plummer(n, 1001)
+    out = {"metric": "G pair-interactions/s (acc+jerk, Hermite shared dt, N=1024)",
+           "unit": UNIT, "workload": "plummer_n1024_eps1e-3_dt2^-8_t1", "results": {}}
+    for prec in ("ds", "fp32"):
+        with _lib.NBody(m, x, v, eps=eps, precision=prec, block_steps=False, lev_shared=lev) as s:
+            E0 = s.energy()[2]
+            L0 = (m[:, None] * np.cross(x, v)).sum(0)
+            e0, e1 = _events(torch)
+            e0.record()
+            for _ in range(steps):
+                s.step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = s.get_state(want=("x", "v"))
+            E1 = s.energy()[2]
+        P = (m[:, None] * st["v"]).sum(0)
+        L = (m[:, None] * np.cross(st["x"], st["v"])).sum(0)
+        out["results"][prec] = {"value": steps * n * n / ms / 1e6, "ms": ms,
+                                "dE_over_E": abs(E1 - E0) / abs(E0),
+                                "dP": float(np.abs(P).max()), "dL": float(np.abs(L - L0).max())}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_block65536(args):
+    """N = 65536 Plummer with Salpeter masses (seed 1002), eps = 1e-4, Aarseth
+    block steps (eta = 0.01, levels 3..20) to t = 1/8: interactions/s over
+    the run, block-step count, active-list histogram, |dE/E| at t = 1/8
+    (all particles synchronised), FP32 and DS."""
+    import torch
+
+    from paper_0909_0879_gb300 import _lib
+
+    n, eps = 65536, 1e-4
+    m, x, v = ics.plummer(n, 1002, masses=ics.salpeter_masses(n, 1002))
+    out = {"metric": "G pair-interactions/s (acc+jerk, Hermite block steps, N=65536)",
+           "unit": UNIT, "workload": "plummer_salpeter_n65536_eps1e-4_eta0.01_t0.125",
+           "results": {}}
+    t_end = 1 << 17
+    for prec in ("ds", "fp32"):
+        with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3, lev_max=20) as s:
+            E0 = s.energy()[2]
+            hist = {}
+            blocks = 0
+            t0 = time.perf_counter()
+            e0, e1 = _events(torch)
+            e0.record()
+            tick = 0
+            while tick < t_end:
+                t, na = s.step()
+                tick = int(round(t * 2**20))
+                blocks += 1
+                b = int(np.log2(max(1, na)))
+                hist[b] = hist.get(b, 0) + 1
+            e1.record()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            ms = e0.elapsed_time(e1)
+            cnt = s.counters()
+            E1 = s.energy()[2]
+        out["results"][prec] = {
+            "value": cnt["interactions"] / ms / 1e6, "ms": ms, "wall_s": wall,
+            "block_steps": blocks, "interactions": cnt["interactions"],
+            "clamped": cnt["clamped"], "dE_over_E": abs(E1 - E0) / abs(E0),
+            "n_act_log2_histogram": {str(k): v for k, v in sorted(hist.items())}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_batched(args):
+    """4096 Plummer clusters of log-uniform size in [16, 1024] (seeds
+    (1004, c)), eps = 1e-3, shared dt = 1/256, 1000 steps: the persistent
+    kernel under a CUDA graph (autotuned shape) against one launch per
+    cluster, FP32 and DS."""
+    import torch
+
+    from paper_0909_0879_gb300 import _lib, tune
+
+    sizes = ics.cluster_sizes(4096, 1004)
+    parts = [ics.plummer(int(nc), (1004, c)) for c, nc in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    m = np.concatenate([p[0] for p in parts])
+    x = np.concatenate([p[1] for p in parts])
+    v = np.concatenate([p[2] for p in parts])
+    inter = float((sizes.astype(np.float64) ** 2).sum())
+    steps = 1000
+    out = {"metric": "G pair-interactions/s (acc+jerk, 4096 clusters, 1000 shared steps)",
+           "unit": UNIT, "workload": "plummer_clusters_4096_n16-1024_eps1e-3_dt2^-8_1000steps",
+           "sum_n": int(off[-1]), "sum_n2": inter, "results": {}}
+    for prec in ("ds", "fp32"):
+        with _lib.Batch(off, m, x, v, eps=1e-3, lev_shared=8, precision=prec) as b:
+            best, timings = tune.tune_batched(b, steps=20)
+            k0, w0 = b.energy()
+            b.run(steps)  # capture + warm
+            b.sync()
+            e0, e1 = _events(torch)
+            l0 = b.launch_count()
+            e0.record()
+            b.run(steps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            launches = b.launch_count() - l0
+            k1, w1 = b.energy()
+            dE = np.abs((k1 + w1) - (k0 + w0)) / np.abs(k0 + w0)
+            # one launch per cluster and step chunk, timed over a few steps
+            b.set_tuning(best[0], 1, 0, False)
+            pc_steps = 5
+            b.run_per_cluster(1)
+            b.sync()
+            e2, e3 = _events(torch)
+            e2.record()
+            b.run_per_cluster(pc_steps)
+            e3.record()
+            torch.cuda.synchronize()
+            pc_ms = e2.elapsed_time(e3)
+        out["results"][prec] = {
+            "value": inter * steps / ms / 1e6, "ms": ms, "launches": launches,
+            "tuned": {"variant": best[0], "steps_per_launch": best[1]},
+            "per_cluster_launches": {"value": inter * pc_steps / pc_ms / 1e6, "steps": pc_steps,
+                                     "ms": pc_ms},
+            "dE_over_E_median_after_2000_steps": float(np.median(dE)),
+            "note": "dt = 1/256 with eps = 1e-3 does not resolve close encounters in small "
+                    "clusters; the FP64 oracle loses energy at the same level"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_adjoint(args):
+    """N = 4096 Plummer (seed 1005), eps = 1e-3, 64 KDK steps of dt = 1/128
+    in FP32, checkpoints every 8 steps, L = sum |x(T) - y|^2: forward time,
+    forward + backward time and buffer memory."""
+    import torch
+
+    from paper_0909_0879_gb300 import _lib
+    from paper_0909_0879_gb300.autograd import leapfrog
+
+    n, eps, dt, steps, ck = 4096, 1e-3, 1.0 / 128, 64, 8
+    m, x, v = ics.plummer(n, 1005)
+    y = torch.tensor(x + np.random.default_rng(5).normal(0.0, 0.05, x.shape),
+                     dtype=torch.float32, device="cuda")
+    x0 = torch.tensor(x, dtype=torch.float32, device="cuda", requires_grad=True)
+    v0 = torch.tensor(v, dtype=torch.float32, device="cuda", requires_grad=True)
+    mm = torch.tensor(m, dtype=torch.float32, device="cuda", requires_grad=True)
+    fwd, both = [], []
+    for rep in range(4):
+        e0, e1 = _events(torch)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        xT, vT = leapfrog(x0, v0, mm, steps, dt, eps, ckpt_every=ck)
+        loss = ((xT - y) ** 2).sum()
+        e1.record()
+        loss.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        if rep:
+            fwd.append(e0.elapsed_time(e1))
+            both.append(e0.elapsed_time(e2))
+        for t in (x0, v0, mm):
+            t.grad = None
+    per_eval = n * n
+    evals_fwd = steps + 1
+    out = {"metric": "ms per forward and forward+backward (leapfrog adjoint, N=4096)",
+           "unit": "ms", "workload": "plummer_n4096_eps1e-3_kdk_dt2^-7_64steps_ckpt8",
+           "forward_ms": float(np.median(fwd)), "forward_backward_ms": float(np.median(both)),
+           "ratio": float(np.median(both) / np.median(fwd)),
+           "forward_ginter_s": evals_fwd * per_eval / np.median(fwd) / 1e6,
+           "checkpoint_bytes": 4 * _lib.lf_ckpt_floats(n, steps, ck),
+           "work_bytes": 4 * _lib.lf_work_floats(n, ck),
+           "full_tape_bytes_for_comparison": 4 * (steps + 1) * 6 * n}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload != "king1m" and args.impl == "ours":
+        return {"shared1024": run_shared1024, "block65536": run_block65536,
+                "batched": run_batched, "adjoint": run_adjoint}[args.workload](args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

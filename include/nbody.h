@@ -170,11 +170,22 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * one whose precision differs from the context's. */
 nb_status nb_set_force_variant(nb_ctx *ctx, int32_t variant, int32_t grid_ctas);
 
+/* Install a tuning table for the built-in variant choice: for an active
+ * list of n_i particles the first entry k (in order) with n_i >= min_n[k]
+ * gives the variant; lists shorter than every min_n fall back to the
+ * built-in choice.  count == 0 removes the table.  Variants must match the
+ * context's precision and eps == 0 masking (NB_ERR_INVALID_ARG); at most 32
+ * entries.  An explicit nb_set_force_variant still takes precedence. */
+nb_status nb_set_force_table(nb_ctx *ctx, int32_t count, const int64_t *min_n,
+                             const int32_t *variant);
+
 /* Describe compiled force-kernel variant v: precision, i-particles per
- * thread, threads per i-particle, threads per CTA.  NB_ERR_INVALID_ARG past
- * the end of the table. */
+ * thread, threads per i-particle, threads per CTA, and whether it packs two
+ * i-particles into each FP32x2 instruction (results are bit-identical to
+ * the unpacked variant of the same shape).  Any output may be NULL.
+ * NB_ERR_INVALID_ARG past the end of the table. */
 nb_status nb_variant_info(int32_t v, int32_t *precision, int32_t *ipt,
-                          int32_t *tpi, int32_t *threads);
+                          int32_t *tpi, int32_t *threads, int32_t *packed);
 
 /* Host-side fault injection for tests: kind 1 makes the next device
  * allocation of nb_init fail with NB_ERR_OOM (process-wide, one shot);
@@ -230,6 +241,51 @@ nb_status nb_batched_get_state(nb_batch *b, double *x, double *v, double *a,
                                double *jerk);
 nb_status nb_batched_sync(nb_batch *b);
 int64_t nb_batched_launch_count(const nb_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Differentiable leapfrog (paper Sec. 3.1, the classic second-order
+ * symplectic scheme, kick-drift-kick form) in FP32, with the adjoint of the
+ * force sum.  All pointers are caller-owned device arrays (float32):
+ * x, v (n,3) row-major, m (n).  Work is queued on `stream` (NULL = default
+ * stream); nothing is allocated.  Errors: NB_ERR_INVALID_ARG for n outside
+ * [1, 2^30], eps < 0, G <= 0, a NULL pointer or a bad step count;
+ * NB_ERR_CUDA for a failed launch.
+ * ---------------------------------------------------------------------- */
+
+/* acc = a(x): G sum_{j != i} m_j d / (|d|^2 + eps^2)^(3/2) (eq. 1,
+ * softened).  acc is (n,3). */
+nb_status nb_lf_acc(int64_t n, const float *d_x, const float *d_m, float eps,
+                    float G, float *d_acc, void *stream);
+
+/* Vector-Jacobian product of the acceleration map for a cotangent g
+ * ((n,3), g_i = dL/da_i): gx_k = G sum_{j != k} T(x_j - x_k)(m_k g_j -
+ * m_j g_k) with T(d) = I/s^3 - 3 d d^T/s^5, and gm_k = G sum_{i != k}
+ * g_i . (x_k - x_i)/s^3.  gx (n,3) and gm (n) are overwritten. */
+nb_status nb_lf_acc_vjp(int64_t n, const float *d_x, const float *d_m,
+                        const float *d_g, float eps, float G, float *d_gx,
+                        float *d_gm, void *stream);
+
+/* Floats of the checkpoint buffer (ceil(nsteps/ckpt_every) slots of (x, v))
+ * and of the reverse pass's work buffer; -1 for bad arguments. */
+int64_t nb_lf_ckpt_floats(int64_t n, int64_t nsteps, int32_t ckpt_every);
+int64_t nb_lf_work_floats(int64_t n, int32_t ckpt_every);
+
+/* nsteps KDK steps of dt in place on d_x, d_v (d_acc (n,3) receives the
+ * final acceleration).  If d_ckpt is not NULL, (x, v) at every step that is
+ * a multiple of ckpt_every is stored in it (nb_lf_ckpt_floats floats). */
+nb_status nb_lf_forward(int64_t n, const float *d_m, float *d_x, float *d_v,
+                        float *d_acc, int64_t nsteps, float dt, float eps,
+                        float G, int32_t ckpt_every, float *d_ckpt,
+                        void *stream);
+
+/* Reverse pass of nb_lf_forward from its checkpoints: on entry d_lx, d_lv
+ * hold dL/dx(T), dL/dv(T); on exit dL/dx(0), dL/dv(0), and d_lm (n) holds
+ * dL/dm.  Each segment of ckpt_every steps is re-run from its checkpoint
+ * into d_work (nb_lf_work_floats floats) and walked backwards. */
+nb_status nb_lf_backward(int64_t n, const float *d_m, const float *d_ckpt,
+                         int64_t nsteps, float dt, float eps, float G,
+                         int32_t ckpt_every, float *d_lx, float *d_lv,
+                         float *d_lm, float *d_work, void *stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free force + jerk.  The paper has no counterpart: this entry

@@ -448,15 +448,45 @@ void orc_acc_vjp(int64_t n, const double *m, const double *x, double G,
   }
 }
 
-/* Loss L = sum_i |x_i(T) - y_i|^2 after nsteps KDK steps from (x0, v0) and
- * its exact gradient with respect to x0, v0 and m, by the discrete adjoint
- * of the KDK map (all intermediate positions kept; no checkpointing here).
+/* Reverse sweep of nsteps KDK steps along a given path of positions
+ * xs[s] (s = 0..nsteps, each (n,3)).  On entry lx, lv hold dL/dx(T) and
+ * dL/dv(T); on exit dL/dx(0), dL/dv(0); lm receives dL/dm.
  * Reverse of one step (x, v) -> (x', v'):
  *   v_h = v + A(x) dt/2, x' = x + v_h dt, v' = v_h + A(x') dt/2
  * adjoint:  lv_h = lv' ;  (lx', lm) += vjp_A(x'; lv' dt/2)
  *           lx = lx' ; lv_h += lx' dt
- *           lv = lv_h ; (lx, lm) += vjp_A(x; lv_h dt/2)
- * Returns L. */
+ *           lv = lv_h ; (lx, lm) += vjp_A(x; lv_h dt/2) */
+void orc_leapfrog_adjoint_path(int64_t n, const double *m, const double *xs,
+                               double G, double eps, double dt, int64_t nsteps,
+                               double *lx, double *lv, double *lm) {
+  size_t n3 = 3 * (size_t)n;
+  double *g = (double *)malloc(sizeof(double) * n3);
+  double *tx = (double *)malloc(sizeof(double) * n3);
+  double *tm = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int64_t k = 0; k < n; ++k) lm[k] = 0.0;
+  for (int64_t s = nsteps - 1; s >= 0; --s) {
+    const double *xa = xs + n3 * (size_t)s;       /* x at step start */
+    const double *xb = xs + n3 * (size_t)(s + 1); /* x' */
+    /* second kick */
+    for (size_t q = 0; q < n3; ++q) g[q] = lv[q] * dt / 2.0;
+    orc_acc_vjp(n, m, xb, G, eps, g, tx, tm);
+    for (size_t q = 0; q < n3; ++q) lx[q] += tx[q];
+    for (int64_t k = 0; k < n; ++k) lm[k] += tm[k];
+    /* drift */
+    for (size_t q = 0; q < n3; ++q) lv[q] += lx[q] * dt;
+    /* first kick */
+    for (size_t q = 0; q < n3; ++q) g[q] = lv[q] * dt / 2.0;
+    orc_acc_vjp(n, m, xa, G, eps, g, tx, tm);
+    for (size_t q = 0; q < n3; ++q) lx[q] += tx[q];
+    for (int64_t k = 0; k < n; ++k) lm[k] += tm[k];
+  }
+  free(g); free(tx); free(tm);
+}
+
+/* Loss L = sum_i |x_i(T) - y_i|^2 after nsteps KDK steps from (x0, v0) and
+ * its exact gradient with respect to x0, v0 and m: the forward pass keeps
+ * every position (no checkpointing here), then the reverse sweep above
+ * starts from dL/dx(T) = 2 (x(T) - y), dL/dv(T) = 0.  Returns L. */
 double orc_leapfrog_loss_grad(int64_t n, const double *m, const double *x0,
                               const double *v0, const double *y, double G,
                               double eps, double dt, int64_t nsteps,
@@ -478,37 +508,13 @@ double orc_leapfrog_loss_grad(int64_t n, const double *m, const double *x0,
     memcpy(xs + n3 * (size_t)(s + 1), x, sizeof(double) * n3);
   }
   double L = 0.0;
-  double *lx = (double *)malloc(sizeof(double) * n3);
-  double *lv = (double *)calloc(n3, sizeof(double));
-  double *lm = (double *)calloc((size_t)n, sizeof(double));
-  double *g = (double *)malloc(sizeof(double) * n3);
-  double *tx = (double *)malloc(sizeof(double) * n3);
-  double *tm = (double *)malloc(sizeof(double) * (size_t)n);
   for (size_t q = 0; q < n3; ++q) {
     double d = x[q] - y[q];
     L += d * d;
-    lx[q] = 2.0 * d;
+    gx0[q] = 2.0 * d;
+    gv0[q] = 0.0;
   }
-  for (int64_t s = nsteps - 1; s >= 0; --s) {
-    const double *xa = xs + n3 * (size_t)s;       /* x at step start */
-    const double *xb = xs + n3 * (size_t)(s + 1); /* x' */
-    /* second kick */
-    for (size_t q = 0; q < n3; ++q) g[q] = lv[q] * dt / 2.0;
-    orc_acc_vjp(n, m, xb, G, eps, g, tx, tm);
-    for (size_t q = 0; q < n3; ++q) lx[q] += tx[q];
-    for (int64_t k = 0; k < n; ++k) lm[k] += tm[k];
-    /* drift */
-    for (size_t q = 0; q < n3; ++q) lv[q] += lx[q] * dt;
-    /* first kick */
-    for (size_t q = 0; q < n3; ++q) g[q] = lv[q] * dt / 2.0;
-    orc_acc_vjp(n, m, xa, G, eps, g, tx, tm);
-    for (size_t q = 0; q < n3; ++q) lx[q] += tx[q];
-    for (int64_t k = 0; k < n; ++k) lm[k] += tm[k];
-  }
-  memcpy(gx0, lx, sizeof(double) * n3);
-  memcpy(gv0, lv, sizeof(double) * n3);
-  memcpy(gmass, lm, sizeof(double) * (size_t)n);
-  free(xs); free(x); free(v); free(acc); free(lx); free(lv); free(lm);
-  free(g); free(tx); free(tm);
+  orc_leapfrog_adjoint_path(n, m, xs, G, eps, dt, nsteps, gx0, gv0, gmass);
+  free(xs); free(x); free(v); free(acc);
   return L;
 }

@@ -81,6 +81,7 @@ def lib():
             L.orc_leapfrog_loss_grad.argtypes = [i64, vp, vp, vp, vp, d, d, d, i64,
                                                  vp, vp, vp]
             L.orc_leapfrog_loss_grad.restype = d
+            L.orc_leapfrog_adjoint_path.argtypes = [i64, vp, vp, d, d, d, i64, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -280,3 +281,18 @@ def leapfrog_loss_grad(m, x0, v0, y, eps, dt, nsteps, G=1.0):
     L = lib().orc_leapfrog_loss_grad(n, _p(m), _p(x0), _p(v0), _p(y), float(G), float(eps),
                                      float(dt), int(nsteps), _p(gx), _p(gv), _p(gm))
     return L, gx, gv, gm
+
+
+def leapfrog_adjoint_path(m, xs, lx_T, lv_T, eps, dt, G=1.0):
+    """Reverse sweep along given positions xs ((nsteps+1, n, 3)); returns
+    (dL/dx0, dL/dv0, dL/dm) for the terminal adjoints lx_T, lv_T."""
+    m = _f64(m)
+    n = m.shape[0]
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    nsteps = xs.shape[0] - 1
+    lx = _f64(lx_T, (n, 3)).copy()
+    lv = _f64(lv_T, (n, 3)).copy()
+    lm = np.zeros(n)
+    lib().orc_leapfrog_adjoint_path(n, _p(m), _p(xs), float(G), float(eps), float(dt),
+                                    int(nsteps), _p(lx), _p(lv), _p(lm))
+    return lx, lv, lm

@@ -63,7 +63,8 @@ SIGNATURES = [
     ("nb_sync", C.c_int, [_vp]),
     ("nb_launch_count", _i64, [_vp]),
     ("nb_set_force_variant", C.c_int, [_vp, _i32, _i32]),
-    ("nb_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
+    ("nb_set_force_table", C.c_int, [_vp, _i32, _vp, _vp]),
+    ("nb_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     ("nb_debug_inject", C.c_int, [_vp, _i32]),
     ("nb_batched_init", C.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _vp, _P(Config)]),
     ("nb_batched_destroy", None, [_vp]),
@@ -75,6 +76,14 @@ SIGNATURES = [
     ("nb_batched_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("nb_batched_sync", C.c_int, [_vp]),
     ("nb_batched_launch_count", _i64, [_vp]),
+    ("nb_lf_acc", C.c_int, [_i64, _vp, _vp, C.c_float, C.c_float, _vp, _vp]),
+    ("nb_lf_acc_vjp", C.c_int, [_i64, _vp, _vp, _vp, C.c_float, C.c_float, _vp, _vp, _vp]),
+    ("nb_lf_ckpt_floats", _i64, [_i64, _i64, _i32]),
+    ("nb_lf_work_floats", _i64, [_i64, _i32]),
+    ("nb_lf_forward", C.c_int, [_i64, _vp, _vp, _vp, _vp, _i64, C.c_float, C.c_float,
+                                C.c_float, _i32, _vp, _vp]),
+    ("nb_lf_backward", C.c_int, [_i64, _vp, _vp, _i64, C.c_float, C.c_float, C.c_float, _i32,
+                                 _vp, _vp, _vp, _vp, _vp]),
     ("nb_force_jerk_noalloc", C.c_int, [_i64, _vp, _vp, _vp, _vp, _i64, _d, _d, _i32, _vp,
                                          _vp, _vp]),
     ("nb_status_string", C.c_char_p, [C.c_int]),
@@ -133,15 +142,16 @@ def _f64(a, shape):
 
 def variant_info(v: int):
     L = load()
-    p, i, t, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-    _check(L.nb_variant_info(v, C.byref(p), C.byref(i), C.byref(t), C.byref(n)))
-    return {"precision": p.value, "ipt": i.value, "tpi": t.value, "threads": n.value}
+    p, i, t, n, k = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(L.nb_variant_info(v, C.byref(p), C.byref(i), C.byref(t), C.byref(n), C.byref(k)))
+    return {"precision": p.value, "ipt": i.value, "tpi": t.value, "threads": n.value,
+            "packed": k.value}
 
 
 def num_variants() -> int:
     v = 0
     L = load()
-    while L.nb_variant_info(v, None, None, None, None) == NB_OK:
+    while L.nb_variant_info(v, None, None, None, None, None) == NB_OK:
         v += 1
     return v
 
@@ -317,6 +327,14 @@ class NBody:
     def set_force_variant(self, variant: int = -1, grid_ctas: int = 0):
         _check(self._L.nb_set_force_variant(self._h, int(variant), int(grid_ctas)))
 
+    def set_force_table(self, table):
+        """table: list of (min_active, variant), checked in order."""
+        mins = np.ascontiguousarray([t[0] for t in table], dtype=np.int64)
+        vars_ = np.ascontiguousarray([t[1] for t in table], dtype=np.int32)
+        _check(self._L.nb_set_force_table(self._h, len(table),
+                                          mins.ctypes.data if len(table) else None,
+                                          vars_.ctypes.data if len(table) else None))
+
     def inject(self, kind: int):
         _check(self._L.nb_debug_inject(self._h, int(kind)))
 
@@ -427,3 +445,43 @@ def force_jerk_noalloc(n, d_m, d_x, d_v, d_idx, n_idx, d_acc, d_jerk, *, eps, G=
     _check(L.nb_force_jerk_noalloc(int(n), _ptr(d_m), _ptr(d_x), _ptr(d_v), _ptr(d_idx),
                                    int(n_idx), float(eps), float(G), prec, _ptr(d_acc),
                                    _ptr(d_jerk), sp))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream or None
+    return int(stream) or None
+
+
+def lf_acc(n, d_x, d_m, d_acc, *, eps, G=1.0, stream=None):
+    _check(load().nb_lf_acc(int(n), _ptr(d_x), _ptr(d_m), float(eps), float(G), _ptr(d_acc),
+                            _stream_ptr(stream)))
+
+
+def lf_acc_vjp(n, d_x, d_m, d_g, d_gx, d_gm, *, eps, G=1.0, stream=None):
+    _check(load().nb_lf_acc_vjp(int(n), _ptr(d_x), _ptr(d_m), _ptr(d_g), float(eps), float(G),
+                                _ptr(d_gx), _ptr(d_gm), _stream_ptr(stream)))
+
+
+def lf_ckpt_floats(n, nsteps, ckpt_every) -> int:
+    return int(load().nb_lf_ckpt_floats(int(n), int(nsteps), int(ckpt_every)))
+
+
+def lf_work_floats(n, ckpt_every) -> int:
+    return int(load().nb_lf_work_floats(int(n), int(ckpt_every)))
+
+
+def lf_forward(n, d_m, d_x, d_v, d_acc, nsteps, dt, d_ckpt, *, eps, G=1.0, ckpt_every=8,
+               stream=None):
+    _check(load().nb_lf_forward(int(n), _ptr(d_m), _ptr(d_x), _ptr(d_v), _ptr(d_acc),
+                                int(nsteps), float(dt), float(eps), float(G), int(ckpt_every),
+                                _ptr(d_ckpt), _stream_ptr(stream)))
+
+
+def lf_backward(n, d_m, d_ckpt, nsteps, dt, d_lx, d_lv, d_lm, d_work, *, eps, G=1.0,
+                ckpt_every=8, stream=None):
+    _check(load().nb_lf_backward(int(n), _ptr(d_m), _ptr(d_ckpt), int(nsteps), float(dt),
+                                 float(eps), float(G), int(ckpt_every), _ptr(d_lx), _ptr(d_lv),
+                                 _ptr(d_lm), _ptr(d_work), _stream_ptr(stream)))

@@ -99,6 +99,9 @@ struct nb_ctx {
   bool have_block = false;
   bool force_done = false;
   int variant_override = -1;
+  int table_count = 0;
+  int64_t table_min[32];
+  int32_t table_var[32];
   int grid_cap = 0;
   int64_t launches = 0, n_blocks = 0, interactions = 0;
   bool inject_timeout = false;
@@ -170,6 +173,8 @@ nb_status check_ctx(nb_ctx *c) {
 
 int pick_variant(nb_ctx *c, int64_t n_i) {
   if (c->variant_override >= 0) return c->variant_override;
+  for (int k = 0; k < c->table_count; ++k)
+    if (n_i >= c->table_min[k]) return c->table_var[k];
   return choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, n_i);
 }
 
@@ -685,14 +690,44 @@ nb_status nb_set_force_variant(nb_ctx *c, int32_t variant, int32_t grid_ctas) {
   return NB_OK;
 }
 
+nb_status nb_set_force_table(nb_ctx *c, int32_t count, const int64_t *min_n,
+                             const int32_t *variant) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (count < 0 || count > 32) return fail(NB_ERR_INVALID_ARG, "table holds 0..32 entries");
+  if (count > 0 && (!min_n || !variant)) return fail(NB_ERR_INVALID_ARG, "null table arrays");
+  for (int k = 0; k < count; ++k) {
+    if (variant[k] < 0 || variant[k] >= num_variants())
+      return fail(NB_ERR_INVALID_ARG, "unknown force variant %d", variant[k]);
+    const Variant &V = variant_at(variant[k]);
+    if (V.prec != c->cfg.precision || V.mask != (c->cfg.eps == 0.0 ? 1 : 0))
+      return fail(NB_ERR_INVALID_ARG, "variant %d does not match the context", variant[k]);
+  }
+  // partial-sum scratch for the largest grid any table entry can use
+  size_t pb = 0;
+  for (int k = 0; k < count; ++k) {
+    const size_t b = part_bytes(variant[k], c->num_sms * ctas_per_sm(variant[k]));
+    pb = b > pb ? b : pb;
+  }
+  s = ensure_part(c, pb);
+  if (s != NB_OK) return s;
+  c->table_count = count;
+  for (int k = 0; k < count; ++k) {
+    c->table_min[k] = min_n[k];
+    c->table_var[k] = variant[k];
+  }
+  return NB_OK;
+}
+
 nb_status nb_variant_info(int32_t v, int32_t *precision, int32_t *ipt, int32_t *tpi,
-                          int32_t *threads) {
+                          int32_t *threads, int32_t *packed) {
   if (v < 0 || v >= num_variants()) return fail(NB_ERR_INVALID_ARG, "unknown variant %d", v);
   const Variant &V = variant_at(v);
   if (precision) *precision = V.prec;
   if (ipt) *ipt = V.ipt;
   if (tpi) *tpi = V.tpi;
   if (threads) *threads = V.threads;
+  if (packed) *packed = V.pack;
   return NB_OK;
 }
 

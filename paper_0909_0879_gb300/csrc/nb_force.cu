@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 namespace nbi {
 
@@ -106,14 +107,61 @@ __device__ __forceinline__ void ds_add(float &hi, float &lo, float x) {
   lo += e;
 }
 
+// Scalar and packed (two lanes per instruction, sm_100+ f32x2) FP32 ops
+// with identical per-lane IEEE round-to-nearest results, so the scalar and
+// packed kernels give bit-identical sums.
+template <class V>
+struct VOps;
+template <>
+struct VOps<float> {
+  static constexpr int W = 1;
+  static __device__ __forceinline__ float bc(float s) { return s; }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+  template <int MASK>
+  static __device__ __forceinline__ float rsq(float r2) {
+    if (MASK) return r2 > 0.f ? rsqrtf(r2) : 0.f;
+    return rsqrtf(r2);
+  }
+  static __device__ __forceinline__ float lane(float a, int) { return a; }
+  static __device__ __forceinline__ void set(float &a, int, float s) { a = s; }
+};
+template <>
+struct VOps<float2> {
+  static constexpr int W = 2;
+  static __device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+  }
+  template <int MASK>
+  static __device__ __forceinline__ float2 rsq(float2 r2) {
+    return make_float2(VOps<float>::rsq<MASK>(r2.x), VOps<float>::rsq<MASK>(r2.y));
+  }
+  static __device__ __forceinline__ float lane(float2 a, int w) { return w ? a.y : a.x; }
+  static __device__ __forceinline__ void set(float2 &a, int w, float s) {
+    if (w)
+      a.y = s;
+    else
+      a.x = s;
+  }
+};
+
 // CTA owning unit u of U units split over P CTAs (ranges [U p / P, U (p+1) / P)).
 __host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) {
   return static_cast<int>(((u + 1) * static_cast<uint64_t>(P) - 1) / U);
 }
 
-template <int PREC, int IPT, int TPI, int NT, int MASK>
+template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK>
 __global__ void __launch_bounds__(NT, 1)
     force_jerk_kernel(const ForceArgs A, const uint64_t U, const int P) {
+  using V = typename std::conditional<PACK != 0, float2, float>::type;
+  using O = VOps<V>;
+  constexpr int W = O::W;         // i-particles per packed lane group
+  static_assert(IPT % W == 0, "packed kernels need an even IPT");
+  constexpr int NQ = IPT / W;     // packed i-groups per thread
   constexpr int NG = NT / TPI;    // i-slots per CTA (per q)
   constexpr int BI = NG * IPT;    // i-particles per i-block
   constexpr int NARR = PREC ? 3 : 2;
@@ -164,7 +212,8 @@ __global__ void __launch_bounds__(NT, 1)
     const uint64_t seg = (n_jt - jt0) < (u1 - u) ? (n_jt - jt0) : (u1 - u);
     const bool full = (jt0 == 0) && (seg == n_jt);
 
-    float xh[IPT][3], xl[IPT][3], vi[IPT][3];
+    // i-particle data, negated so that every difference is an addition
+    V nxh[NQ][3], nxl[NQ][3], nvi[NQ][3];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
       const int64_t k = static_cast<int64_t>(ib) * BI + g + q * NG;
@@ -172,15 +221,14 @@ __global__ void __launch_bounds__(NT, 1)
       if (k < n_i) i = A.idx ? A.idx[k] : k;
       const float4 h = A.jhi[i];
       const float4 w = A.jvel[i];
-      xh[q][0] = h.x; xh[q][1] = h.y; xh[q][2] = h.z;
-      vi[q][0] = w.x; vi[q][1] = w.y; vi[q][2] = w.z;
-      if (PREC) {
-        const float4 l = A.jlo[i];
-        xl[q][0] = l.x; xl[q][1] = l.y; xl[q][2] = l.z;
-      } else {
-        xl[q][0] = xl[q][1] = xl[q][2] = 0.f;
-      }
+      float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (PREC) l = A.jlo[i];
+      const int qq = q / W, wl = q % W;
+      O::set(nxh[qq][0], wl, -h.x); O::set(nxh[qq][1], wl, -h.y); O::set(nxh[qq][2], wl, -h.z);
+      O::set(nxl[qq][0], wl, -l.x); O::set(nxl[qq][1], wl, -l.y); O::set(nxl[qq][2], wl, -l.z);
+      O::set(nvi[qq][0], wl, -w.x); O::set(nvi[qq][1], wl, -w.y); O::set(nvi[qq][2], wl, -w.z);
     }
+    const V veps2 = O::bc(eps2);
     float ah[IPT][3], al[IPT][3], jh[IPT][3], jl[IPT][3];
 #pragma unroll
     for (int q = 0; q < IPT; ++q)
@@ -195,11 +243,11 @@ __global__ void __launch_bounds__(NT, 1)
       const float4 *sl = sh + kJT;
       const float4 *sv = sh + (NARR - 1) * kJT;
 
-      float p1[IPT][3], p2[IPT][3];
+      V p1[NQ][3], p2[NQ][3];
 #pragma unroll
-      for (int q = 0; q < IPT; ++q)
+      for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p1[q][c] = p2[q][c] = 0.f;
+        for (int c = 0; c < 3; ++c) p1[q][c] = p2[q][c] = O::bc(0.f);
 
       // The tile is walked in chunks of CH j-records per thread; the
       // acceleration's FP32 chunk sums are folded into the accumulators after
@@ -209,61 +257,60 @@ __global__ void __launch_bounds__(NT, 1)
       constexpr int CH = (PREC && kFoldChunk < kJT / TPI) ? kFoldChunk : kJT / TPI;
 #pragma unroll 1
       for (int c0 = r; c0 < kJT; c0 += CH * TPI) {
-        float pa[IPT][3];
+        V pa[NQ][3];
 #pragma unroll
-        for (int q = 0; q < IPT; ++q)
+        for (int q = 0; q < NQ; ++q)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) pa[q][c] = 0.f;
+          for (int c = 0; c < 3; ++c) pa[q][c] = O::bc(0.f);
 #pragma unroll 4
         for (int jj = c0; jj < c0 + CH * TPI; jj += TPI) {
           const float4 hj = sh[jj];
           const float4 wj = sv[jj];
           float4 lj;
           if (PREC) lj = sl[jj];
+          const V xj = O::bc(hj.x), yj = O::bc(hj.y), zj = O::bc(hj.z), mj = O::bc(hj.w);
+          const V vxj = O::bc(wj.x), vyj = O::bc(wj.y), vzj = O::bc(wj.z);
 #pragma unroll
-          for (int q = 0; q < IPT; ++q) {
-            float dx, dy, dz;
+          for (int q = 0; q < NQ; ++q) {
+            V dx, dy, dz;
             if (PREC) {
-              dx = (hj.x - xh[q][0]) + (lj.x - xl[q][0]);
-              dy = (hj.y - xh[q][1]) + (lj.y - xl[q][1]);
-              dz = (hj.z - xh[q][2]) + (lj.z - xl[q][2]);
+              dx = O::add(O::add(xj, nxh[q][0]), O::add(O::bc(lj.x), nxl[q][0]));
+              dy = O::add(O::add(yj, nxh[q][1]), O::add(O::bc(lj.y), nxl[q][1]));
+              dz = O::add(O::add(zj, nxh[q][2]), O::add(O::bc(lj.z), nxl[q][2]));
             } else {
-              dx = hj.x - xh[q][0];
-              dy = hj.y - xh[q][1];
-              dz = hj.z - xh[q][2];
+              dx = O::add(xj, nxh[q][0]);
+              dy = O::add(yj, nxh[q][1]);
+              dz = O::add(zj, nxh[q][2]);
             }
-            const float ux = wj.x - vi[q][0];
-            const float uy = wj.y - vi[q][1];
-            const float uz = wj.z - vi[q][2];
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-            float rinv;
-            if (MASK)
-              rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-            else
-              rinv = rsqrtf(r2);
-            const float rinv2 = rinv * rinv;
-            const float mr3 = (hj.w * rinv) * rinv2;
-            const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-            const float cc = (rv * rinv2) * mr3;
-            pa[q][0] = fmaf(mr3, dx, pa[q][0]);
-            pa[q][1] = fmaf(mr3, dy, pa[q][1]);
-            pa[q][2] = fmaf(mr3, dz, pa[q][2]);
-            p1[q][0] = fmaf(mr3, ux, p1[q][0]);
-            p1[q][1] = fmaf(mr3, uy, p1[q][1]);
-            p1[q][2] = fmaf(mr3, uz, p1[q][2]);
-            p2[q][0] = fmaf(cc, dx, p2[q][0]);
-            p2[q][1] = fmaf(cc, dy, p2[q][1]);
-            p2[q][2] = fmaf(cc, dz, p2[q][2]);
+            const V ux = O::add(vxj, nvi[q][0]);
+            const V uy = O::add(vyj, nvi[q][1]);
+            const V uz = O::add(vzj, nvi[q][2]);
+            const V r2 = O::fma(dx, dx, O::fma(dy, dy, O::fma(dz, dz, veps2)));
+            const V rinv = O::template rsq<MASK>(r2);
+            const V rinv2 = O::mul(rinv, rinv);
+            const V mr3 = O::mul(O::mul(mj, rinv), rinv2);
+            const V rv = O::fma(dx, ux, O::fma(dy, uy, O::mul(dz, uz)));
+            const V cc = O::mul(O::mul(rv, rinv2), mr3);
+            pa[q][0] = O::fma(mr3, dx, pa[q][0]);
+            pa[q][1] = O::fma(mr3, dy, pa[q][1]);
+            pa[q][2] = O::fma(mr3, dz, pa[q][2]);
+            p1[q][0] = O::fma(mr3, ux, p1[q][0]);
+            p1[q][1] = O::fma(mr3, uy, p1[q][1]);
+            p1[q][2] = O::fma(mr3, uz, p1[q][2]);
+            p2[q][0] = O::fma(cc, dx, p2[q][0]);
+            p2[q][1] = O::fma(cc, dy, p2[q][1]);
+            p2[q][2] = O::fma(cc, dz, p2[q][2]);
           }
         }
 #pragma unroll
         for (int q = 0; q < IPT; ++q)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
+            const float x = O::lane(pa[q / W][c], q % W);
             if (PREC)
-              ds_add(ah[q][c], al[q][c], pa[q][c]);
+              ds_add(ah[q][c], al[q][c], x);
             else
-              ah[q][c] += pa[q][c];
+              ah[q][c] += x;
           }
       }
       // fold the tile's jerk partial sums (jerk = p1 - 3 p2)
@@ -271,7 +318,8 @@ __global__ void __launch_bounds__(NT, 1)
       for (int q = 0; q < IPT; ++q)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float jt = fmaf(-3.f, p2[q][c], p1[q][c]);
+          const float jt =
+              fmaf(-3.f, O::lane(p2[q / W][c], q % W), O::lane(p1[q / W][c], q % W));
           if (PREC)
             ds_add(jh[q][c], jl[q][c], jt);
           else
@@ -361,23 +409,34 @@ struct Entry {
   KernelFn fn;
 };
 
-#define NB_V(PREC, IPT, TPI, NT, MASK) \
-  Entry{Variant{PREC, IPT, TPI, NT, MASK}, &force_jerk_kernel<PREC, IPT, TPI, NT, MASK>}
+#define NB_V(PREC, IPT, TPI, NT, MASK, PACK)             \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK},          \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK>}
 
 // The compiled shape table.  Index order is part of the tuning interface.
 const Entry kTable[] = {
-    NB_V(1, 4, 1, 256, 0),   // 0  DS, long lists
-    NB_V(1, 2, 1, 256, 0),   // 1
-    NB_V(1, 1, 1, 256, 0),   // 2
-    NB_V(1, 1, 4, 256, 0),   // 3  DS, short lists
-    NB_V(1, 1, 16, 256, 0),  // 4
-    NB_V(0, 4, 1, 256, 0),   // 5  FP32, long lists
-    NB_V(0, 2, 1, 256, 0),   // 6
-    NB_V(0, 1, 1, 256, 0),   // 7
-    NB_V(0, 1, 4, 256, 0),   // 8  FP32, short lists
-    NB_V(0, 1, 16, 256, 0),  // 9
-    NB_V(1, 1, 1, 256, 1),   // 10 DS, eps == 0
-    NB_V(0, 1, 1, 256, 1),   // 11 FP32, eps == 0
+    NB_V(1, 4, 1, 256, 0, 0),   // 0  DS, long lists
+    NB_V(1, 2, 1, 256, 0, 0),   // 1
+    NB_V(1, 1, 1, 256, 0, 0),   // 2
+    NB_V(1, 1, 4, 256, 0, 0),   // 3  DS, short lists
+    NB_V(1, 1, 16, 256, 0, 0),  // 4
+    NB_V(0, 4, 1, 256, 0, 0),   // 5  FP32, long lists
+    NB_V(0, 2, 1, 256, 0, 0),   // 6
+    NB_V(0, 1, 1, 256, 0, 0),   // 7
+    NB_V(0, 1, 4, 256, 0, 0),   // 8  FP32, short lists
+    NB_V(0, 1, 16, 256, 0, 0),  // 9
+    NB_V(1, 1, 1, 256, 1, 0),   // 10 DS, eps == 0
+    NB_V(0, 1, 1, 256, 1, 0),   // 11 FP32, eps == 0
+    NB_V(1, 4, 1, 256, 0, 1),   // 12 DS, packed pairs of i
+    NB_V(1, 2, 1, 256, 0, 1),   // 13
+    NB_V(0, 4, 1, 256, 0, 1),   // 14 FP32, packed pairs of i
+    NB_V(0, 2, 1, 256, 0, 1),   // 15
+    NB_V(1, 2, 4, 256, 0, 1),   // 16 DS, packed, short lists
+    NB_V(1, 2, 1, 128, 0, 1),   // 17 DS, packed, 128 threads
+    NB_V(1, 4, 1, 384, 0, 1),   // 18 DS, packed, 12 warps per CTA
+    NB_V(1, 4, 2, 384, 0, 1),   // 19
+    NB_V(0, 4, 1, 384, 0, 1),   // 20 FP32, packed, 12 warps per CTA
+    NB_V(0, 4, 2, 384, 0, 1),   // 21
 };
 constexpr int kNumVariants = sizeof(kTable) / sizeof(kTable[0]);
 
@@ -395,13 +454,21 @@ const Variant &variant_at(int v) { return kTable[v].V; }
 int block_i(const Variant &V) { return V.threads / V.tpi * V.ipt; }
 
 int choose_variant(int prec, int mask, int64_t n_i) {
+  // Built-in choice from timings on a GB300 (N = 1M King, every shape):
+  // packed FP32x2 variants for long lists, more threads per i-particle as
+  // the list shortens.  nb_set_force_table overrides it per workload.
   if (mask) return prec ? 10 : 11;
-  const int base = prec ? 0 : 5;
-  if (n_i >= 2048) return base + 0;
-  if (n_i >= 512) return base + 1;
-  if (n_i >= 256) return base + 2;
-  if (n_i >= 64) return base + 3;
-  return base + 4;
+  if (prec) {
+    if (n_i >= 2048) return 12;
+    if (n_i >= 512) return 13;
+    if (n_i >= 128) return 16;
+    if (n_i >= 64) return 3;
+    return 4;
+  }
+  if (n_i >= 512) return 15;
+  if (n_i >= 256) return 7;
+  if (n_i >= 64) return 8;
+  return 9;
 }
 
 int ctas_per_sm(int v) {

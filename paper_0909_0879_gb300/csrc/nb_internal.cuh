@@ -50,6 +50,7 @@ struct Variant {
   int tpi;      // threads per i-particle (j split inside the CTA)
   int threads;  // threads per CTA
   int mask;     // 1: zero the i == j term (eps == 0)
+  int pack;     // 1: two i-particles per packed FP32x2 instruction
 };
 
 int num_variants();

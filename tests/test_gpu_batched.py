@@ -31,15 +31,22 @@ def make_clusters(n_clusters, seed, lo=16, hi=1024):
     return off, np.concatenate(ms), np.concatenate(xs), np.concatenate(vs)
 
 
+def energy_floor(steps):
+    """Noise floor of |dE/E| from FP32 pair arithmetic: a relative force
+    error of ~1e-7 changes the energy by ~1e-7 v a dt / |E| ~ 1e-9 per step
+    (Henon units, dt = 1/256), accumulating as a random walk."""
+    return 1e-9 * np.sqrt(steps)
+
+
 def test_batched_vs_oracle_per_cluster(nb, oracle_mod):
     """24 clusters (16..1024 bodies), eps = 1e-3, dt = 1/256, 64 steps:
-    per-cluster energy error within 2x the oracle's, positions close."""
+    per-cluster energy error within 2x the oracle's (or the FP32-arithmetic
+    floor when the oracle's is below it)."""
     off, m, x, v = make_clusters(24, 1004)
     eps, lev, steps = 1e-3, 8, 64
     with nb.Batch(off, m, x, v, eps=eps, lev_shared=lev) as b:
         k0, w0 = b.energy()
         b.run(steps)
-        st = b.get_state()
         k1, w1 = b.energy()
     bad = []
     for c in range(len(off) - 1):
@@ -49,22 +56,51 @@ def test_batched_vs_oracle_per_cluster(nb, oracle_mod):
         xo, vo, _, _ = oracle_mod.hermite_shared(m[s], x[s], v[s], eps, lev, steps)
         dEo = abs(oracle_mod.energy(m[s], xo, vo, eps)[2] - E0o) / abs(E0o)
         dEg = abs(k1[c] + w1[c] - E0o) / abs(E0o)
-        if dEg > 2 * max(dEo, 1e-10):
+        if dEg > 2 * max(dEo, energy_floor(steps)):
             bad.append((c, off[c + 1] - off[c], dEg, dEo))
     assert not bad, bad
 
 
-def test_batched_positions_track_oracle_short(nb, oracle_mod):
-    off, m, x, v = make_clusters(12, 77)
-    eps, lev = 1e-3, 8
+def test_batched_long_run_energy_statistics(nb, oracle_mod):
+    """1000 steps of dt = 1/256 with eps = 1e-3 leave close encounters
+    unresolved: the FP64 oracle itself loses energy at the percent level and
+    beyond in small clusters, and trajectories diverge chaotically.  Over 32
+    sampled clusters the GPU's median |dE/E| stays within 2x the oracle's."""
+    off, m, x, v = make_clusters(32, 2004, lo=16, hi=256)
+    eps, lev, steps = 1e-3, 8, 1000
     with nb.Batch(off, m, x, v, eps=eps, lev_shared=lev) as b:
-        b.run(4)
+        k0, w0 = b.energy()
+        b.run(steps)
+        k1, w1 = b.energy()
+    dEg = np.abs((k1 + w1) - (k0 + w0)) / np.abs(k0 + w0)
+    dEo = []
+    for c in range(len(off) - 1):
+        s = slice(off[c], off[c + 1])
+        E0o = oracle_mod.energy(m[s], x[s], v[s], eps)[2]
+        xo, vo, _, _ = oracle_mod.hermite_shared(m[s], x[s], v[s], eps, lev, steps)
+        dEo.append(abs(oracle_mod.energy(m[s], xo, vo, eps)[2] - E0o) / abs(E0o))
+    dEo = np.array(dEo)
+    print("median dE/E gpu %.3e oracle %.3e" % (np.median(dEg), np.median(dEo)))
+    assert np.median(dEg) <= 2 * np.median(dEo)
+
+
+def test_batched_positions_track_oracle_short(nb, oracle_mod):
+    """After 4 steps every position agrees with the oracle to the size a
+    1e-6 relative force error can cause, 1e-6 |a| (4 dt)^2 / 2."""
+    off, m, x, v = make_clusters(12, 77)
+    eps, lev, steps = 1e-3, 8, 4
+    dt = 2.0**-lev
+    with nb.Batch(off, m, x, v, eps=eps, lev_shared=lev) as b:
+        b.run(steps)
         st = b.get_state()
     for c in range(len(off) - 1):
         s = slice(off[c], off[c + 1])
-        xo, vo, ao, jo = oracle_mod.hermite_shared(m[s], x[s], v[s], eps, lev, 4)
-        assert np.abs(st["x"][s] - xo).max() < 1e-9
-        assert np.abs(st["v"][s] - vo).max() < 1e-7
+        xo, vo, ao, jo = oracle_mod.hermite_shared(m[s], x[s], v[s], eps, lev, steps)
+        amag = np.linalg.norm(ao, axis=1)
+        tol_x = 1e-6 * amag * (steps * dt) ** 2 / 2 + 1e-12
+        tol_v = 1e-6 * amag * steps * dt + 1e-12
+        assert np.all(np.linalg.norm(st["x"][s] - xo, axis=1) <= tol_x), c
+        assert np.all(np.linalg.norm(st["v"][s] - vo, axis=1) <= tol_v), c
 
 
 def test_batched_modes_bitwise_equal(nb):
@@ -110,8 +146,11 @@ def test_batched_every_variant(nb, oracle_mod):
             ref = {}
             for c in range(len(off) - 1):
                 s = slice(off[c], off[c + 1])
-                ref[c] = oracle_mod.hermite_shared(m[s], x[s], v[s], 1e-3, 8, 10)[0]
-        tol = 1e-8 if prec == "ds" else 1e-5
+                xo, _, ao, _ = oracle_mod.hermite_shared(m[s], x[s], v[s], 1e-3, 8, 10)
+                ref[c] = (xo, ao)
+        rel = 1e-5 if prec == "ds" else 1e-2
         for c in range(len(off) - 1):
             s = slice(off[c], off[c + 1])
-            assert np.abs(st["x"][s] - ref[c]).max() < tol, (var, c)
+            xo, ao = ref[c]
+            tol = rel * np.linalg.norm(ao, axis=1) * (10 * 2.0**-8) ** 2 / 2 + 1e-12
+            assert np.all(np.linalg.norm(st["x"][s] - xo, axis=1) <= tol), (var, c)

@@ -187,3 +187,33 @@ def test_king_1m_sampled_parity(nb, oracle_mod):
         errs[prec] = check(acc, jerk, ra, rj, prec, cond)
     print("king 1M sampled errors (max e_i acc, jerk, norm acc, jerk)", errs)
     assert errs["ds"][0] <= 1e-6, "per-particle DS force error at N = 1M"
+
+
+def test_packed_variants_bitwise_equal_scalar(nb):
+    """The packed FP32x2 kernels round every lane like the scalar kernels,
+    so a packed variant and the scalar variant of the same shape give
+    bit-identical sums."""
+    n = 6000
+    m, x, v = ics.plummer(n, 12, masses=ics.salpeter_masses(n, 12))
+    idx = ics.random_active_subset(n, 2500, 5)
+    infos = [nb.variant_info(k) for k in range(nb.num_variants())]
+    pairs = []
+    for k, inf in enumerate(infos):
+        if not inf["packed"]:
+            continue
+        for j, jnf in enumerate(infos):
+            if (not jnf["packed"] and jnf["precision"] == inf["precision"] and
+                    jnf["ipt"] == inf["ipt"] and jnf["tpi"] == inf["tpi"] and
+                    jnf["threads"] == inf["threads"]):
+                pairs.append((k, j))
+    assert len(pairs) >= 4
+    for prec in ("ds", "fp32"):
+        with nb.NBody(m, x, v, eps=1e-4, precision=prec) as s:
+            for k, j in pairs:
+                if infos[k]["precision"] != (1 if prec == "ds" else 0):
+                    continue
+                s.set_force_variant(k, 0)
+                ak, jk = s.force_jerk(idx)
+                s.set_force_variant(j, 0)
+                aj, jj = s.force_jerk(idx)
+                assert np.array_equal(ak, aj) and np.array_equal(jk, jj), (k, j)

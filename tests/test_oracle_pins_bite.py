@@ -34,6 +34,7 @@ MUTANTS = {
     "adjoint_index": ("oz += uz * s3 - 3.0 * du * s5 * dz;", "oz += uz * s3 - 3.0 * du * s5 * dy;"),
     "adjoint_mass_sign": ("om += -(g[3 * j + 0] * dx", "om += (g[3 * j + 0] * dx"),
     "adjoint_drift": ("for (size_t q = 0; q < n3; ++q) lv[q] += lx[q] * dt;", "for (size_t q = 0; q < n3; ++q) lv[q] += lx[q] * dt / 2.0;"),
+    "adjoint_kick_order": ("orc_acc_vjp(n, m, xb, G, eps, g, tx, tm);", "orc_acc_vjp(n, m, xa, G, eps, g, tx, tm);"),
 }
 
 
