@@ -66,6 +66,10 @@ def parse():
                    choices=["king1m", "shared1024", "block65536", "batched", "adjoint"],
                    help="king1m is the headline; the others time the remaining workloads "
                         "and print their own JSON line")
+    p.add_argument("--block-steps", type=int, default=0,
+                   help="block65536: stop after this many block steps (0 = run to t = 1/8)")
+    p.add_argument("--precisions", default="ds,fp32",
+                   help="workloads other than king1m: comma-separated precisions to run")
     p.add_argument("--sweep", action="store_true",
                    help="also time single evaluations at active fractions 2^-10..1")
     return p.parse_args()
@@ -294,17 +298,8 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     force_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    t_total = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
-        it = torch.tensor([inter], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(it, op=torch.distributed.ReduceOp.SUM)
-        inter_all = float(it.item())
-    else:
-        inter_all = float(inter)
-    value = inter_all / t_total / 1e9
+    rate, t_total, inter_all = metrics.aggregate_throughput(sum(step_ms) / 1e3, inter, dev)
+    value = rate / 1e9
 
     dE = None
     if E0 is not None:
@@ -327,9 +322,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_t = time.perf_counter() - t0
     e2e_val = e2e_steps * n * n / e2e_t / 1e9
     if world > 1:
-        et = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(et, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = world * e2e_steps * n * n / float(et.item()) / 1e9
+        e2e_val = metrics.aggregate_throughput(e2e_t, e2e_steps * n * n, dev)[0] / 1e9
 
     sweep = None
     if args.sweep:
@@ -439,7 +432,7 @@ def run_shared1024(args):
     m, x, v = ics.plummer(n, 1001)
     out = {"metric": "G pair-interactions/s (acc+jerk, Hermite shared dt, N=1024)",
            "unit": UNIT, "workload": "plummer_n1024_eps1e-3_dt2^-8_t1", "results": {}}
-    for prec in ("ds", "fp32"):
+    for prec in args.precisions.split(","):
         with _lib.NBody(m, x, v, eps=eps, precision=prec, block_steps=False, lev_shared=lev) as s:
             E0 = s.energy()[2]
             L0 = (m[:, None] * np.cross(x, v)).sum(0)
@@ -476,7 +469,8 @@ def run_block65536(args):
            "unit": UNIT, "workload": "plummer_salpeter_n65536_eps1e-4_eta0.01_t0.125",
            "results": {}}
     t_end = 1 << 17
-    for prec in ("ds", "fp32"):
+    max_blocks = args.block_steps if args.block_steps > 0 else 1 << 62
+    for prec in args.precisions.split(","):
         with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3, lev_max=20) as s:
             E0 = s.energy()[2]
             hist = {}
@@ -485,7 +479,7 @@ def run_block65536(args):
             e0, e1 = _events(torch)
             e0.record()
             tick = 0
-            while tick < t_end:
+            while tick < t_end and blocks < max_blocks:
                 t, na = s.step()
                 tick = int(round(t * 2**20))
                 blocks += 1
@@ -496,7 +490,7 @@ def run_block65536(args):
             wall = time.perf_counter() - t0
             ms = e0.elapsed_time(e1)
             cnt = s.counters()
-            E1 = s.energy()[2]
+            E1 = s.energy()[2] if tick >= t_end else float("nan")
         out["results"][prec] = {
             "value": cnt["interactions"] / ms / 1e6, "ms": ms, "wall_s": wall,
             "block_steps": blocks, "interactions": cnt["interactions"],
@@ -526,7 +520,7 @@ def run_batched(args):
     out = {"metric": "G pair-interactions/s (acc+jerk, 4096 clusters, 1000 shared steps)",
            "unit": UNIT, "workload": "plummer_clusters_4096_n16-1024_eps1e-3_dt2^-8_1000steps",
            "sum_n": int(off[-1]), "sum_n2": inter, "results": {}}
-    for prec in ("ds", "fp32"):
+    for prec in args.precisions.split(","):
         with _lib.Batch(off, m, x, v, eps=1e-3, lev_shared=8, precision=prec) as b:
             best, timings = tune.tune_batched(b, steps=20)
             k0, w0 = b.energy()

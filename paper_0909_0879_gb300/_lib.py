@@ -377,6 +377,8 @@ class Batch:
         self.n_clusters = off.shape[0] - 1
         self.n = n
         self.offsets = off
+        self.precision = cfg.precision
+        self.mask = 1 if cfg.eps == 0.0 else 0
         h = C.c_void_p()
         _check(L.nb_batched_init(C.byref(h), self.n_clusters, off.ctypes.data, m.ctypes.data,
                                  x.ctypes.data, v.ctypes.data, C.byref(cfg)))

@@ -5,6 +5,8 @@
 #include "../../include/nbody.h"
 #include "nb_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -21,6 +23,13 @@ namespace {
 
 thread_local char g_err[512] = "";
 std::atomic<int> g_inject_oom{0};
+
+// NVTX range for one phase of a block step (visible in Nsight timelines;
+// a no-op when no tool is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 nb_status fail(nb_status s, const char *fmt, ...) {
   va_list ap;
@@ -135,12 +144,9 @@ nb_status dev_alloc_t(nb_ctx *c, T **p, size_t count) {
 // Wait for the stream with a host watchdog, then read the device error word
 // and the small scalars into pinned memory.
 nb_status sync_ctx(nb_ctx *c) {
-  NB_CUDA(cudaMemcpyAsync(c->h_scal, c->scal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+  // scal holds [t_next, n_act, err, clamped] contiguously: one copy back
+  NB_CUDA(cudaMemcpyAsync(c->h_scal, c->scal, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost,
                           c->stream));
-  NB_CUDA(cudaMemcpyAsync(&c->h_scal[2], c->err, sizeof(int), cudaMemcpyDeviceToHost,
-                          c->stream));
-  NB_CUDA(cudaMemcpyAsync(&c->h_scal[3], c->clamped, sizeof(unsigned long long),
-                          cudaMemcpyDeviceToHost, c->stream));
   NB_CUDA(cudaEventRecord(c->ev, c->stream));
   if (c->inject_timeout) {
     c->inject_timeout = false;
@@ -149,15 +155,17 @@ nb_status sync_ctx(nb_ctx *c) {
   }
   const int ms = c->cfg.sync_timeout_ms > 0 ? c->cfg.sync_timeout_ms : 600000;
   const auto t0 = std::chrono::steady_clock::now();
-  for (;;) {
+  for (int64_t polls = 0;; ++polls) {
     cudaError_t e = cudaEventQuery(c->ev);
     if (e == cudaSuccess) break;
     if (e != cudaErrorNotReady)
       return fail(NB_ERR_CUDA, "stream execution failed: %s", cudaGetErrorString(e));
     const auto el = std::chrono::steady_clock::now() - t0;
-    if (std::chrono::duration_cast<std::chrono::milliseconds>(el).count() > ms)
+    const auto us = std::chrono::duration_cast<std::chrono::microseconds>(el).count();
+    if (us > static_cast<int64_t>(ms) * 1000)
       return fail(NB_ERR_TIMEOUT, "GPU work did not finish within %d ms", ms);
-    std::this_thread::sleep_for(std::chrono::microseconds(20));
+    // spin for the first 2 ms (block steps wait microseconds), then yield
+    if (us > 2000) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
   const int err = static_cast<int>(c->h_scal[2] & 0xffffffff);
   if (err != 0)
@@ -350,9 +358,10 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRY(dev_alloc_t(c, &c->act, n));
   TRY(dev_alloc_t(c, &c->blk, next_block_scratch_ints(n) + 1));
   TRY(dev_alloc_t(c, &c->scal, 4));
+  // the device error word and the clamp counter live in scal[2] and scal[3]
+  c->err = reinterpret_cast<int *>(c->scal + 2);
+  c->clamped = reinterpret_cast<unsigned long long *>(c->scal + 3);
   TRY(dev_alloc_t(c, &c->red, energy_scratch_doubles(n)));
-  TRY(dev_alloc_t(c, &c->err, 4));
-  TRY(dev_alloc_t(c, &c->clamped, 1));
   // Partial-sum scratch for the largest built-in grid of every variant of
   // this precision, so the default path never allocates after init.
   size_t pb = 0;
@@ -387,8 +396,6 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRYC(cudaMemsetAsync(c->jk, 0, n3 * sizeof(double), st));
   TRYC(cudaMemsetAsync(c->t_tick, 0, n * sizeof(int64_t), st));
   TRYC(cudaMemsetAsync(c->scal, 0, 4 * sizeof(int64_t), st));
-  TRYC(cudaMemsetAsync(c->err, 0, 4 * sizeof(int), st));
-  TRYC(cudaMemsetAsync(c->clamped, 0, sizeof(unsigned long long), st));
   TRYC(launch_pad_records(n, c->n_pad, c->jhi, c->jlo, c->jvel, st));
   c->launches += 1;
   TRY(queue_predict(c, 0));
@@ -415,6 +422,7 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
 }
 
 nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
+  Range r("nb_next_block");
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   int nl = 0;
@@ -433,6 +441,7 @@ nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
 }
 
 nb_status nb_predict(nb_ctx *c, double t) {
+  Range r("nb_predict");
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   bool ok;
@@ -446,6 +455,7 @@ nb_status nb_predict(nb_ctx *c, double t) {
 
 nb_status nb_force_jerk_dev(nb_ctx *c, const int32_t *d_idx, int64_t n_idx, double *d_acc,
                             double *d_jerk) {
+  Range r("nb_force_jerk");
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   if (c->t_pred < 0) return fail(NB_ERR_STATE, "nb_predict must come first");
@@ -538,6 +548,7 @@ nb_status nb_force_jerk(nb_ctx *c, const int32_t *idx, int64_t n_idx, double *ac
 }
 
 nb_status nb_correct(nb_ctx *c, double t) {
+  Range r("nb_correct");
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   bool ok;
@@ -572,6 +583,7 @@ nb_status nb_step(nb_ctx *c, double *t_next, int64_t *n_active) {
 }
 
 nb_status nb_energy(nb_ctx *c, double *kin, double *pot, double *tot) {
+  Range r("nb_energy");
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   int nl = 0;

@@ -213,13 +213,15 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
               double xp[3], vp[3];
               bpredict(B.x, B.v, B.a, B.jk, gi, dt, xp, vp);
               const double dt2 = dt * dt, dt3 = dt2 * dt;
+              // dt is a power of two: exact reciprocals, identical results
+              const double idt2 = 1.0 / dt2, idt3 = 1.0 / dt3;
 #pragma unroll
               for (int k = 0; k < 3; ++k) {
                 const double a0 = B.a[3 * gi + k], j0v = B.jk[3 * gi + k];
                 const double an = B.G * o[k], jn = B.G * o[3 + k];
                 const double da = a0 - an;
-                const double snap = (-6.0 * da - dt * (4.0 * j0v + 2.0 * jn)) / dt2;
-                const double crackle = (12.0 * da + 6.0 * dt * (j0v + jn)) / dt3;
+                const double snap = (-6.0 * da - dt * (4.0 * j0v + 2.0 * jn)) * idt2;
+                const double crackle = (12.0 * da + 6.0 * dt * (j0v + jn)) * idt3;
                 B.x[3 * gi + k] =
                     xp[k] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
                 B.v[3 * gi + k] = vp[k] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));

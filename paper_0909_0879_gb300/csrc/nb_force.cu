@@ -149,12 +149,46 @@ struct VOps<float2> {
   }
 };
 
+// Split-precision accumulators of IPT i-particles: acceleration and jerk,
+// high and low words.  In registers, or (SMEM) in shared memory at a
+// per-thread slot so that wide IPT shapes keep registers for the pair
+// arithmetic; the slots are touched only at folds, every 32 j.
+template <int IPT, int NT, bool SMEM>
+struct DsAcc;
+template <int IPT, int NT>
+struct DsAcc<IPT, NT, false> {
+  float ah[IPT][3], al[IPT][3], jh[IPT][3], jl[IPT][3];
+  __device__ __forceinline__ void init(float *, int) {
+#pragma unroll
+    for (int q = 0; q < IPT; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ah[q][c] = al[q][c] = jh[q][c] = jl[q][c] = 0.f;
+  }
+  __device__ __forceinline__ float &AH(int q, int c) { return ah[q][c]; }
+  __device__ __forceinline__ float &AL(int q, int c) { return al[q][c]; }
+  __device__ __forceinline__ float &JH(int q, int c) { return jh[q][c]; }
+  __device__ __forceinline__ float &JL(int q, int c) { return jl[q][c]; }
+};
+template <int IPT, int NT>
+struct DsAcc<IPT, NT, true> {
+  float *b;
+  __device__ __forceinline__ void init(float *smem, int tid) {
+    b = smem + tid;
+#pragma unroll
+    for (int k = 0; k < 12 * IPT; ++k) b[k * NT] = 0.f;
+  }
+  __device__ __forceinline__ float &AH(int q, int c) { return b[(12 * q + c) * NT]; }
+  __device__ __forceinline__ float &AL(int q, int c) { return b[(12 * q + 3 + c) * NT]; }
+  __device__ __forceinline__ float &JH(int q, int c) { return b[(12 * q + 6 + c) * NT]; }
+  __device__ __forceinline__ float &JL(int q, int c) { return b[(12 * q + 9 + c) * NT]; }
+};
+
 // CTA owning unit u of U units split over P CTAs (ranges [U p / P, U (p+1) / P)).
 __host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) {
   return static_cast<int>(((u + 1) * static_cast<uint64_t>(P) - 1) / U);
 }
 
-template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK>
+template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK, int SACC>
 __global__ void __launch_bounds__(NT, 1)
     force_jerk_kernel(const ForceArgs A, const uint64_t U, const int P) {
   using V = typename std::conditional<PACK != 0, float2, float>::type;
@@ -229,11 +263,8 @@ __global__ void __launch_bounds__(NT, 1)
       O::set(nvi[qq][0], wl, -w.x); O::set(nvi[qq][1], wl, -w.y); O::set(nvi[qq][2], wl, -w.z);
     }
     const V veps2 = O::bc(eps2);
-    float ah[IPT][3], al[IPT][3], jh[IPT][3], jl[IPT][3];
-#pragma unroll
-    for (int q = 0; q < IPT; ++q)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) ah[q][c] = al[q][c] = jh[q][c] = jl[q][c] = 0.f;
+    DsAcc<IPT, NT, SACC != 0> D;
+    D.init(reinterpret_cast<float *>(sbase + static_cast<size_t>(kStages) * NARR * kJT), tid);
 
     for (uint64_t t = 0; t < seg; ++t, ++s_idx) {
       const int st = static_cast<int>(s_idx % kStages);
@@ -308,9 +339,9 @@ __global__ void __launch_bounds__(NT, 1)
           for (int c = 0; c < 3; ++c) {
             const float x = O::lane(pa[q / W][c], q % W);
             if (PREC)
-              ds_add(ah[q][c], al[q][c], x);
+              ds_add(D.AH(q, c), D.AL(q, c), x);
             else
-              ah[q][c] += x;
+              D.AH(q, c) += x;
           }
       }
       // fold the tile's jerk partial sums (jerk = p1 - 3 p2)
@@ -321,9 +352,9 @@ __global__ void __launch_bounds__(NT, 1)
           const float jt =
               fmaf(-3.f, O::lane(p2[q / W][c], q % W), O::lane(p1[q / W][c], q % W));
           if (PREC)
-            ds_add(jh[q][c], jl[q][c], jt);
+            ds_add(D.JH(q, c), D.JL(q, c), jt);
           else
-            jh[q][c] += jt;
+            D.JH(q, c) += jt;
         }
       if (__syncthreads_or(!ok)) {
         // A copy never arrived: record it, wait (bounded) for the copies
@@ -345,8 +376,8 @@ __global__ void __launch_bounds__(NT, 1)
       double o[6];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        o[c] = static_cast<double>(ah[q][c]) + static_cast<double>(al[q][c]);
-        o[3 + c] = static_cast<double>(jh[q][c]) + static_cast<double>(jl[q][c]);
+        o[c] = static_cast<double>(D.AH(q, c)) + static_cast<double>(D.AL(q, c));
+        o[3 + c] = static_cast<double>(D.JH(q, c)) + static_cast<double>(D.JL(q, c));
       }
       if (TPI > 1) {
 #pragma unroll
@@ -375,20 +406,24 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
-// Sum the partial segments of every split i-block in ascending CTA order.
+// Sum the partial segments of every split i-block: one warp per
+// i-particle, lanes stride over the CTAs that hold a partial (ascending
+// within a lane) and meet by a butterfly; the order is fixed for a given
+// grid, so results are deterministic.
 __global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
                                    uint64_t n_jt, uint64_t U, int P, int BI,
                                    double G, double *__restrict__ acc,
                                    double *__restrict__ jerk) {
-  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= n_i) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (k >= n_i) return;  // uniform per warp
   const uint64_t ib = static_cast<uint64_t>(k) / BI;
   const int kk = static_cast<int>(static_cast<uint64_t>(k) % BI);
   const int plo = owner_of(ib * n_jt, U, P);
   const int phi = owner_of((ib + 1) * n_jt - 1, U, P);
   if (plo == phi) return;  // written directly by its only CTA
   double s[6] = {0, 0, 0, 0, 0, 0};
-  for (int p = plo; p <= phi; ++p) {
+  for (int p = plo + lane; p <= phi; p += 32) {
     const uint64_t u0p = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
     const int slot = (u0p / n_jt == ib) ? 0 : 1;
     const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
@@ -396,9 +431,15 @@ __global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
     for (int c = 0; c < 6; ++c) s[c] += src[static_cast<size_t>(c) * BI + kk];
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    acc[3 * k + c] = G * s[c];
-    jerk[3 * k + c] = G * s[3 + c];
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[3 * k + c] = G * s[c];
+      jerk[3 * k + c] = G * s[3 + c];
+    }
   }
 }
 
@@ -410,8 +451,11 @@ struct Entry {
 };
 
 #define NB_V(PREC, IPT, TPI, NT, MASK, PACK)             \
-  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK},          \
-        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK>}
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0},       \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0>}
+#define NB_VS(PREC, IPT, TPI, NT, MASK, PACK)            \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 1},       \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 1>}
 
 // The compiled shape table.  Index order is part of the tuning interface.
 const Entry kTable[] = {
@@ -437,11 +481,16 @@ const Entry kTable[] = {
     NB_V(1, 4, 2, 384, 0, 1),   // 19
     NB_V(0, 4, 1, 384, 0, 1),   // 20 FP32, packed, 12 warps per CTA
     NB_V(0, 4, 2, 384, 0, 1),   // 21
+    NB_VS(1, 4, 1, 256, 0, 1),  // 22 DS, packed, accumulators in shared memory
+    NB_VS(1, 8, 1, 256, 0, 1),  // 23 DS, packed, 8 i-particles per thread
+    NB_VS(1, 6, 1, 256, 0, 1),  // 24
+    NB_VS(0, 8, 1, 256, 0, 1),  // 25 FP32, packed, 8 i-particles per thread
 };
 constexpr int kNumVariants = sizeof(kTable) / sizeof(kTable[0]);
 
 size_t smem_bytes(const Variant &V) {
-  return static_cast<size_t>(kStages) * (V.prec ? 3 : 2) * kJT * sizeof(float4);
+  return static_cast<size_t>(kStages) * (V.prec ? 3 : 2) * kJT * sizeof(float4) +
+         (V.sacc ? static_cast<size_t>(12) * V.ipt * V.threads * sizeof(float) : 0);
 }
 
 std::mutex g_occ_mu;
@@ -476,6 +525,8 @@ int ctas_per_sm(int v) {
   if (g_occ[v] == 0) {
     int nb = 0;
     const Variant &V = kTable[v].V;
+    cudaFuncSetAttribute(kTable[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem_bytes(V)));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &nb, kTable[v].fn, V.threads, smem_bytes(V)) != cudaSuccess ||
         nb < 1)
@@ -496,7 +547,10 @@ int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap) {
   const int64_t U = n_ib * n_jt;
   int64_t P = static_cast<int64_t>(num_sms) * ctas_per_sm(v);
   if (grid_cap > 0 && grid_cap < P) P = grid_cap;
-  if (U < P) P = U;
+  // at least kMinUnits j-tiles per CTA: short lists are latency-bound, and
+  // fewer split segments keep the fix-up short
+  constexpr int64_t kMinUnits = 4;
+  if ((U + kMinUnits - 1) / kMinUnits < P) P = (U + kMinUnits - 1) / kMinUnits;
   return static_cast<int>(P < 1 ? 1 : P);
 }
 
@@ -513,8 +567,8 @@ cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
   // Split i-blocks exist unless every CTA range is whole i-blocks.
   if (!(U % static_cast<uint64_t>(grid) == 0 &&
         (U / grid) % static_cast<uint64_t>(A.n_jt) == 0)) {
-    const int tb = 256;
-    const int64_t nb = (A.n_i + tb - 1) / tb;
+    const int tb = 256;  // 8 warps, one i-particle each
+    const int64_t nb = (A.n_i + 7) / 8;
     force_fixup_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(
         A.part, A.n_i, static_cast<uint64_t>(A.n_jt), U, grid, BI, A.G, A.acc,
         A.jerk);

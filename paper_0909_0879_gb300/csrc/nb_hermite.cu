@@ -105,6 +105,9 @@ __global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, i
   double xp[3], vp[3];
   predict_pos_vel(x, v, a, jk, i, dt, xp, vp);
   const double dt2 = dt * dt, dt3 = dt2 * dt;
+  // every step is a power of two, so these reciprocals are exact and the
+  // products below equal the quotients bit for bit
+  const double idt2 = 1.0 / dt2, idt3 = 1.0 / dt3;
   double a1v[3], j1v[3], a2e[3], a3e[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -112,8 +115,8 @@ __global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, i
     const double an = a1[3 * k + c], jn = j1[3 * k + c];
     const double da = a0 - an;
     // second and third derivatives of a at the start of the step
-    const double snap = (-6.0 * da - dt * (4.0 * j0 + 2.0 * jn)) / dt2;
-    const double crackle = (12.0 * da + 6.0 * dt * (j0 + jn)) / dt3;
+    const double snap = (-6.0 * da - dt * (4.0 * j0 + 2.0 * jn)) * idt2;
+    const double crackle = (12.0 * da + 6.0 * dt * (j0 + jn)) * idt3;
     x[3 * i + c] = xp[c] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
     v[3 * i + c] = vp[c] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
     a[3 * i + c] = an;

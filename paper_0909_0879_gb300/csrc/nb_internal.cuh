@@ -51,6 +51,7 @@ struct Variant {
   int threads;  // threads per CTA
   int mask;     // 1: zero the i == j term (eps == 0)
   int pack;     // 1: two i-particles per packed FP32x2 instruction
+  int sacc;     // 1: split-precision accumulators in shared memory
 };
 
 int num_variants();

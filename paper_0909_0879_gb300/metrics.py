@@ -38,3 +38,21 @@ def interactions(n_act: int, n: int) -> int:
 def fp32_peak_tflops(n_sm: int, sm_mhz: float) -> float:
     """FP32 peak in TFLOP/s: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
     return n_sm * FP32_LANES_PER_SM * 2.0 * sm_mhz * 1e6 / 1e12
+
+
+def aggregate_throughput(local_seconds: float, local_units: float, device=None):
+    """Whole-job throughput of independent replicas (weak scaling): the
+    units every rank processed divided by the slowest rank's time.  Uses
+    torch.distributed when initialised (one all-reduce MAX of the time and
+    one SUM of the units); otherwise the local values.  Returns
+    (units_per_second, max_seconds, total_units)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_units / local_seconds, local_seconds, local_units
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())

@@ -116,13 +116,13 @@ def tune_force(s: "_lib.NBody", fractions=(1.0, 1 / 8, 1 / 64, 1 / 1024), seed=7
     return table, timings
 
 
-def tune_batched(b: "_lib.Batch", steps=20, spl=(1000, 100, 25), use_cache=True):
+def tune_batched(b: "_lib.Batch", steps=50, spl=(1000, 10), use_cache=True):
     """Time every compatible batched variant and steps-per-launch value on
     the batch itself (its state advances by the timed steps); install and
     return the best (variant, steps_per_launch)."""
     sizes = np.diff(b.offsets)
     sig = f"{len(sizes)}:{int(sizes.sum())}:{int((sizes.astype(np.int64) ** 2).sum())}"
-    key = f"batched|{_gpu_key()}|{sig}|steps{steps}"
+    key = f"batched|{_gpu_key()}|p{b.precision}|m{b.mask}|{sig}|steps{steps}"
     cache = _load_cache() if use_cache else {}
     if key in cache:
         best = tuple(cache[key]["best"])
