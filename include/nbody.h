@@ -126,6 +126,19 @@ nb_status nb_correct(nb_ctx *ctx, double t);
  * active list, nb_correct.  Returns t_next and the active count. */
 nb_status nb_step(nb_ctx *ctx, double *t_next, int64_t *n_active);
 
+/* Block steps without a host round trip per step: the active count, the
+ * force shape and the stream-K split are taken on the device, and a CUDA
+ * graph of 32 block steps (scheduling, predictor, force + jerk, corrector)
+ * is replayed until the next block would pass t_end or max_blocks steps
+ * (0 = no limit) have run; the host synchronises once per replay.  The
+ * steps are the ones nb_step takes with the built-in force shapes (an
+ * installed tuning table or a forced variant is not used here), so the
+ * results are bit-identical to an nb_step loop under the built-in choice.
+ * Returns the number of block steps taken and the time of the last one.
+ * t_end must be a tick multiple; particles due later stay where they are. */
+nb_status nb_run_blocks(nb_ctx *ctx, double t_end, int64_t max_blocks,
+                        int64_t *blocks_done, double *t_last);
+
 /* Energy of the current (synchronised) state in FP64 on the GPU:
  * K = 1/2 sum m v^2, W = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)
  * (the softened pair potential consistent with the force).  Uses the

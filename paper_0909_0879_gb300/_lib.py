@@ -55,6 +55,7 @@ SIGNATURES = [
     ("nb_force_jerk_dev", C.c_int, [_vp, _vp, _i64, _vp, _vp]),
     ("nb_correct", C.c_int, [_vp, _d]),
     ("nb_step", C.c_int, [_vp, _P(_d), _P(_i64)]),
+    ("nb_run_blocks", C.c_int, [_vp, _d, _i64, _P(_i64), _P(_d)]),
     ("nb_energy", C.c_int, [_vp, _P(_d), _P(_d), _P(_d)]),
     ("nb_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -254,6 +255,14 @@ class NBody:
         t, na = C.c_double(), C.c_int64()
         _check(self._L.nb_step(self._h, C.byref(t), C.byref(na)))
         return t.value, na.value
+
+    def run_blocks(self, t_end: float, max_blocks: int = 0):
+        """Device-resident block steps until t_end (graph replays); returns
+        (block steps taken, time of the last block)."""
+        nb, tl = C.c_int64(), C.c_double()
+        _check(self._L.nb_run_blocks(self._h, float(t_end), int(max_blocks), C.byref(nb),
+                                     C.byref(tl)))
+        return nb.value, tl.value
 
     def run_until(self, t_end: float):
         """Block steps until every particle has reached t_end (a tick multiple

@@ -114,6 +114,8 @@ struct nb_ctx {
   int grid_cap = 0;
   int64_t launches = 0, n_blocks = 0, interactions = 0;
   bool inject_timeout = false;
+  cudaGraphExec_t blk_graph = nullptr;  // device-resident block steps
+  double *blk_graph_part = nullptr;
   std::vector<void *> allocs;
 };
 
@@ -144,9 +146,10 @@ nb_status dev_alloc_t(nb_ctx *c, T **p, size_t count) {
 // Wait for the stream with a host watchdog, then read the device error word
 // and the small scalars into pinned memory.
 nb_status sync_ctx(nb_ctx *c) {
-  // scal holds [t_next, n_act, err, clamped] contiguously: one copy back
-  NB_CUDA(cudaMemcpyAsync(c->h_scal, c->scal, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                          c->stream));
+  // the control slots (t_next, n_act, error word, clamps, device counters)
+  // are contiguous: one copy back
+  NB_CUDA(cudaMemcpyAsync(c->h_scal, c->scal, kCtlSlots * sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, c->stream));
   NB_CUDA(cudaEventRecord(c->ev, c->stream));
   if (c->inject_timeout) {
     c->inject_timeout = false;
@@ -167,7 +170,7 @@ nb_status sync_ctx(nb_ctx *c) {
     // spin for the first 2 ms (block steps wait microseconds), then yield
     if (us > 2000) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
-  const int err = static_cast<int>(c->h_scal[2] & 0xffffffff);
+  const int err = static_cast<int>(c->h_scal[kCtlErr] & 0xffffffff);
   if (err != 0)
     return fail(NB_ERR_DEVICE, "a force kernel's bounded wait for a shared-memory tile ran out "
                                "(device error word 0x%x)", err);
@@ -304,6 +307,7 @@ void nb_destroy(nb_ctx *c) {
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_energy) cudaFreeHost(c->h_energy);
   if (c->ev) cudaEventDestroy(c->ev);
+  if (c->blk_graph) cudaGraphExecDestroy(c->blk_graph);
   delete c;
 }
 
@@ -357,10 +361,10 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRY(dev_alloc_t(c, &c->jvel, c->n_pad));
   TRY(dev_alloc_t(c, &c->act, n));
   TRY(dev_alloc_t(c, &c->blk, next_block_scratch_ints(n) + 1));
-  TRY(dev_alloc_t(c, &c->scal, 4));
+  TRY(dev_alloc_t(c, &c->scal, kCtlSlots));
   // the device error word and the clamp counter live in scal[2] and scal[3]
-  c->err = reinterpret_cast<int *>(c->scal + 2);
-  c->clamped = reinterpret_cast<unsigned long long *>(c->scal + 3);
+  c->err = reinterpret_cast<int *>(c->scal + kCtlErr);
+  c->clamped = reinterpret_cast<unsigned long long *>(c->scal + kCtlClamped);
   TRY(dev_alloc_t(c, &c->red, energy_scratch_doubles(n)));
   // Partial-sum scratch for the largest built-in grid of every variant of
   // this precision, so the default path never allocates after init.
@@ -373,13 +377,14 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   }
   TRY(dev_alloc(c, reinterpret_cast<void **>(&c->part), pb));
   c->part_cap = pb;
-  if (cudaMallocHost(reinterpret_cast<void **>(&c->h_scal), 8 * sizeof(int64_t)) != cudaSuccess ||
+  if (cudaMallocHost(reinterpret_cast<void **>(&c->h_scal), 2 * kCtlSlots * sizeof(int64_t)) !=
+          cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void **>(&c->h_energy), 4 * sizeof(double)) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
     nb_destroy(c);
     return fail(NB_ERR_CUDA, "pinned host buffers / event creation failed");
   }
-  std::memset(c->h_scal, 0, 8 * sizeof(int64_t));
+  std::memset(c->h_scal, 0, 2 * kCtlSlots * sizeof(int64_t));
 #define TRYC(call)                                                                  \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \
@@ -395,7 +400,12 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRYC(cudaMemsetAsync(c->a, 0, n3 * sizeof(double), st));
   TRYC(cudaMemsetAsync(c->jk, 0, n3 * sizeof(double), st));
   TRYC(cudaMemsetAsync(c->t_tick, 0, n * sizeof(int64_t), st));
-  TRYC(cudaMemsetAsync(c->scal, 0, 4 * sizeof(int64_t), st));
+  TRYC(cudaMemsetAsync(c->scal, 0, kCtlSlots * sizeof(int64_t), st));
+  // no end time and no block budget unless nb_run_blocks sets them
+  c->h_scal[kCtlSlots + 0] = INT64_MAX;
+  c->h_scal[kCtlSlots + 1] = INT64_MAX;
+  TRYC(cudaMemcpyAsync(c->scal + kCtlTend, c->h_scal + kCtlSlots, 2 * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, st));
   TRYC(launch_pad_records(n, c->n_pad, c->jhi, c->jlo, c->jvel, st));
   c->launches += 1;
   TRY(queue_predict(c, 0));
@@ -430,8 +440,8 @@ nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
   c->launches += nl;
   s = sync_ctx(c);
   if (s != NB_OK) return s;
-  c->t_block = c->h_scal[0];
-  c->n_act = c->h_scal[1];
+  c->t_block = c->h_scal[kCtlTnext];
+  c->n_act = c->h_scal[kCtlNact];
   c->have_block = true;
   c->force_done = false;
   c->n_blocks += 1;
@@ -582,6 +592,142 @@ nb_status nb_step(nb_ctx *c, double *t_next, int64_t *n_active) {
   return NB_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr int kGraphSteps = 32;  // block steps per graph replay
+
+// Queue kGraphSteps device-resident block steps on stream s.
+nb_status queue_device_blocks(nb_ctx *c, cudaStream_t s) {
+  struct Bucket {
+    int64_t lo, hi;
+    int v;
+  };
+  Bucket b[3];
+  int nbk = 0;
+  const int prec = c->cfg.precision;
+  if (c->cfg.eps == 0.0) {
+    b[nbk++] = {1, INT64_MAX, choose_variant(prec, 1, 1)};
+  } else {
+    b[nbk++] = {1, kBucketMid, choose_variant(prec, 0, 1)};
+    b[nbk++] = {kBucketMid, kBucketLong, choose_variant(prec, 0, kBucketMid)};
+    b[nbk++] = {kBucketLong, INT64_MAX, choose_variant(prec, 0, kBucketLong)};
+  }
+  for (int step = 0; step < kGraphSteps; ++step) {
+    int nl = 0;
+    NB_CUDA(launch_next_block(c->n, c->t_tick, c->lev, c->act, c->blk, c->scal, s, &nl));
+    NB_CUDA(launch_predict(c->n, 0, c->x, c->v, c->a, c->jk, c->m, c->t_tick, prec, c->jhi,
+                           c->jlo, c->jvel, s, c->scal));
+    for (int k = 0; k < nbk; ++k) {
+      if (b[k].lo > c->n) continue;
+      ForceArgs A;
+      A.jhi = c->jhi;
+      A.jlo = c->jlo;
+      A.jvel = c->jvel;
+      A.n_jt = c->n_jt;
+      A.idx = c->act;
+      A.n_i = 0;
+      A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
+      A.G = c->cfg.G;
+      A.acc = c->a1;
+      A.jerk = c->j1;
+      A.part = c->part;
+      A.err = c->err;
+      A.ctl = c->scal;
+      A.lo = b[k].lo;
+      A.hi = b[k].hi;
+      const int grid = c->num_sms * ctas_per_sm(b[k].v);
+      NB_CUDA(launch_force_dev(b[k].v, A, grid, c->n, s, &nl));
+    }
+    NB_CUDA(launch_correct(c->n, c->act, 0, c->x, c->v, c->a, c->jk, c->t_tick, c->lev, c->a1,
+                           c->j1, c->cfg.eta, c->cfg.lev_min, c->cfg.lev_max,
+                           c->cfg.block_steps, c->clamped, s, c->scal));
+  }
+  return NB_OK;
+}
+
+}  // namespace
+
+extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
+                                   int64_t *blocks_done, double *t_last) {
+  Range r("nb_run_blocks");
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  bool ok;
+  const int64_t tend = tick_of(t_end, &ok);
+  if (!ok) return fail(NB_ERR_INVALID_ARG, "t_end %.17g is not a non-negative multiple of 2^-20",
+                       t_end);
+  if (max_blocks < 0) return fail(NB_ERR_INVALID_ARG, "negative block budget");
+  // partial-sum scratch for every shape the device-resident steps may run
+  size_t pb = 0;
+  for (int64_t n_probe : {int64_t(1), kBucketMid, kBucketLong}) {
+    const int v = choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, n_probe);
+    const size_t bytes = part_bytes(v, c->num_sms * ctas_per_sm(v));
+    pb = bytes > pb ? bytes : pb;
+  }
+  s = ensure_part(c, pb);
+  if (s != NB_OK) return s;
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  const int64_t b0 = c->h_scal[kCtlBlocks];
+  const int64_t i0 = c->h_scal[kCtlInter];
+  c->h_scal[kCtlSlots + 0] = tend;
+  c->h_scal[kCtlSlots + 1] = max_blocks > 0 ? b0 + max_blocks : INT64_MAX;
+  NB_CUDA(cudaMemcpyAsync(c->scal + kCtlTend, c->h_scal + kCtlSlots, 2 * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, c->stream));
+  if (!c->blk_graph || c->blk_graph_part != c->part) {
+    if (c->blk_graph) {
+      cudaGraphExecDestroy(c->blk_graph);
+      c->blk_graph = nullptr;
+    }
+    // warm the occupancy cache and the shared-memory attributes before the
+    // capture, then capture on a private stream
+    cudaStream_t cs;
+    NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    nb_status qs = e == cudaSuccess ? queue_device_blocks(c, cs) : NB_ERR_CUDA;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || e2 != cudaSuccess || qs != NB_OK)
+      return fail(NB_ERR_CUDA, "capture of the block-step graph failed: %s",
+                  cudaGetErrorString(e != cudaSuccess ? e : e2));
+    e = cudaGraphInstantiate(&c->blk_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+      return fail(NB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    c->blk_graph_part = c->part;
+  }
+  int64_t last_blocks = b0;
+  for (;;) {
+    NB_CUDA(cudaGraphLaunch(c->blk_graph, c->stream));
+    c->launches += kGraphSteps * 9;
+    s = sync_ctx(c);
+    if (s != NB_OK) return s;
+    const int64_t nb = c->h_scal[kCtlBlocks];
+    if (c->h_scal[kCtlTnext] < 0 || nb == last_blocks) break;
+    last_blocks = nb;
+  }
+  c->h_scal[kCtlSlots + 0] = INT64_MAX;
+  c->h_scal[kCtlSlots + 1] = INT64_MAX;
+  NB_CUDA(cudaMemcpyAsync(c->scal + kCtlTend, c->h_scal + kCtlSlots, 2 * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, c->stream));
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  const int64_t done = c->h_scal[kCtlBlocks] - b0;
+  c->n_blocks += done;
+  c->interactions += c->h_scal[kCtlInter] - i0;
+  c->have_block = false;
+  c->force_done = false;
+  c->t_pred = -1;
+  if (blocks_done) *blocks_done = done;
+  if (t_last) *t_last = std::ldexp(static_cast<double>(c->h_scal[kCtlLastT]), -kTicksLog2);
+  return NB_OK;
+}
+
+extern "C" {
+
 nb_status nb_energy(nb_ctx *c, double *kin, double *pot, double *tot) {
   Range r("nb_energy");
   nb_status s = check_ctx(c);
@@ -673,7 +819,7 @@ nb_status nb_get_counters(nb_ctx *c, int64_t *n_blocks, int64_t *n_interactions,
   if (s != NB_OK) return s;
   if (n_blocks) *n_blocks = c->n_blocks;
   if (n_interactions) *n_interactions = c->interactions;
-  if (n_clamped) *n_clamped = c->h_scal[3];
+  if (n_clamped) *n_clamped = c->h_scal[kCtlClamped];
   return NB_OK;
 }
 

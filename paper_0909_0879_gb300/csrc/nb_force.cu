@@ -190,7 +190,7 @@ __host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) 
 
 template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK, int SACC>
 __global__ void __launch_bounds__(NT, 1)
-    force_jerk_kernel(const ForceArgs A, const uint64_t U, const int P) {
+    force_jerk_kernel(const ForceArgs A, uint64_t U, int P) {
   using V = typename std::conditional<PACK != 0, float2, float>::type;
   using O = VOps<V>;
   constexpr int W = O::W;         // i-particles per packed lane group
@@ -209,12 +209,21 @@ __global__ void __launch_bounds__(NT, 1)
   const int g = tid / TPI;
   const int r = tid % TPI;
   const int p = blockIdx.x;
+  const uint64_t n_jt = static_cast<uint64_t>(A.n_jt);
+  int64_t n_i = A.n_i;
+  if (A.ctl) {
+    // device-resident block step: size the split from the device's count
+    n_i = A.ctl[kCtlNact];
+    if (n_i < A.lo || n_i >= A.hi || n_i <= 0) return;
+    U = static_cast<uint64_t>((n_i + BI - 1) / BI) * n_jt;
+    const uint64_t pmax = (U + kMinUnits - 1) / kMinUnits;
+    P = static_cast<int>(pmax < gridDim.x ? pmax : gridDim.x);
+    if (p >= P) return;
+  }
   const uint64_t u0 = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
   const uint64_t u1 = U * static_cast<uint64_t>(p + 1) / static_cast<uint64_t>(P);
   if (u0 >= u1) return;  // uniform over the CTA
   const uint64_t nunits = u1 - u0;
-  const uint64_t n_jt = static_cast<uint64_t>(A.n_jt);
-  const int64_t n_i = A.n_i;
   const float eps2 = A.eps2;
 
   if (tid == 0) {
@@ -413,9 +422,18 @@ __global__ void __launch_bounds__(NT, 1)
 __global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
                                    uint64_t n_jt, uint64_t U, int P, int BI,
                                    double G, double *__restrict__ acc,
-                                   double *__restrict__ jerk) {
+                                   double *__restrict__ jerk, const int64_t *ctl,
+                                   int64_t lo, int64_t hi) {
   const int lane = threadIdx.x & 31;
   const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (ctl) {
+    // P arrives as the force kernel's grid; derive the split as it did
+    n_i = ctl[kCtlNact];
+    if (n_i < lo || n_i >= hi || n_i <= 0) return;
+    U = static_cast<uint64_t>((n_i + BI - 1) / BI) * n_jt;
+    const uint64_t pmax = (U + kMinUnits - 1) / kMinUnits;
+    if (pmax < static_cast<uint64_t>(P)) P = static_cast<int>(pmax);
+  }
   if (k >= n_i) return;  // uniform per warp
   const uint64_t ib = static_cast<uint64_t>(k) / BI;
   const int kk = static_cast<int>(static_cast<uint64_t>(k) % BI);
@@ -443,7 +461,7 @@ __global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
   }
 }
 
-using KernelFn = void (*)(const ForceArgs, const uint64_t, const int);
+using KernelFn = void (*)(const ForceArgs, uint64_t, int);
 
 struct Entry {
   Variant V;
@@ -505,18 +523,17 @@ int block_i(const Variant &V) { return V.threads / V.tpi * V.ipt; }
 int choose_variant(int prec, int mask, int64_t n_i) {
   // Built-in choice from timings on a GB300 (N = 1M King, every shape):
   // packed FP32x2 variants for long lists, more threads per i-particle as
-  // the list shortens.  nb_set_force_table overrides it per workload.
+  // the list shortens.  The bucket edges (kBucketMid, kBucketLong) are the
+  // ones the device-resident block steps use, so both paths run the same
+  // shapes.  nb_set_force_table overrides it per workload.
   if (mask) return prec ? 10 : 11;
   if (prec) {
-    if (n_i >= 2048) return 12;
-    if (n_i >= 512) return 13;
-    if (n_i >= 128) return 16;
-    if (n_i >= 64) return 3;
+    if (n_i >= kBucketLong) return 12;
+    if (n_i >= kBucketMid) return 16;
     return 4;
   }
-  if (n_i >= 512) return 15;
-  if (n_i >= 256) return 7;
-  if (n_i >= 64) return 8;
+  if (n_i >= kBucketLong) return 15;
+  if (n_i >= kBucketMid) return 8;
   return 9;
 }
 
@@ -547,11 +564,25 @@ int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap) {
   const int64_t U = n_ib * n_jt;
   int64_t P = static_cast<int64_t>(num_sms) * ctas_per_sm(v);
   if (grid_cap > 0 && grid_cap < P) P = grid_cap;
-  // at least kMinUnits j-tiles per CTA: short lists are latency-bound, and
-  // fewer split segments keep the fix-up short
-  constexpr int64_t kMinUnits = 4;
+  // at least kMinUnits j-tiles per CTA
   if ((U + kMinUnits - 1) / kMinUnits < P) P = (U + kMinUnits - 1) / kMinUnits;
   return static_cast<int>(P < 1 ? 1 : P);
+}
+
+cudaError_t launch_force_dev(int v, const ForceArgs &A, int grid, int64_t n_max,
+                             cudaStream_t s, int *launches) {
+  const Entry &E = kTable[v];
+  const int BI = block_i(E.V);
+  E.fn<<<grid, E.V.threads, smem_bytes(E.V), s>>>(A, 0, grid);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t cap = A.hi < n_max ? A.hi : n_max;
+  const int64_t nb = (cap + 7) / 8;
+  force_fixup_kernel<<<static_cast<unsigned>(nb > 0 ? nb : 1), 256, 0, s>>>(
+      A.part, 0, static_cast<uint64_t>(A.n_jt), 0, grid, BI, A.G, A.acc, A.jerk, A.ctl, A.lo,
+      A.hi);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
@@ -571,7 +602,7 @@ cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
     const int64_t nb = (A.n_i + 7) / 8;
     force_fixup_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(
         A.part, A.n_i, static_cast<uint64_t>(A.n_jt), U, grid, BI, A.G, A.acc,
-        A.jerk);
+        A.jerk, nullptr, 0, 0);
     e = cudaGetLastError();
     ++nl;
   }

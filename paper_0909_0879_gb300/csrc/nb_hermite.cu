@@ -38,7 +38,11 @@ __global__ void predict_kernel(int64_t n, int64_t t_next, const double *__restri
                                const double *__restrict__ jk, const double *__restrict__ m,
                                const int64_t *__restrict__ t_tick, int prec,
                                float4 *__restrict__ jhi, float4 *__restrict__ jlo,
-                               float4 *__restrict__ jvel) {
+                               float4 *__restrict__ jvel, const int64_t *ctl) {
+  if (ctl) {
+    t_next = ctl[kCtlTnext];
+    if (t_next < 0) return;
+  }
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const double dt = static_cast<double>(t_next - t_tick[i]) * kTick;
@@ -91,15 +95,13 @@ __device__ __forceinline__ int level_from_dt(double dt, int lev_min, int lev_max
   return lev;
 }
 
-__global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, int64_t t_next,
-                               double *__restrict__ x, double *__restrict__ v,
-                               double *__restrict__ a, double *__restrict__ jk,
-                               int64_t *__restrict__ t_tick, int32_t *__restrict__ lev,
-                               const double *__restrict__ a1, const double *__restrict__ j1,
-                               double eta, int lev_min, int lev_max, int block_steps,
-                               unsigned long long *n_clamped) {
-  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= n_act) return;
+// Hermite corrector, step criterion and new level of active particle k.
+__device__ __forceinline__ void correct_one(
+    int64_t k, const int32_t *__restrict__ act, int64_t t_next, double *__restrict__ x,
+    double *__restrict__ v, double *__restrict__ a, double *__restrict__ jk,
+    int64_t *__restrict__ t_tick, int32_t *__restrict__ lev, const double *__restrict__ a1,
+    const double *__restrict__ j1, double eta, int lev_min, int lev_max, int block_steps,
+    unsigned long long *n_clamped) {
   const int64_t i = act[k];
   const double dt = static_cast<double>(t_next - t_tick[i]) * kTick;
   double xp[3], vp[3];
@@ -143,6 +145,24 @@ __global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, i
     }
     lev[i] = nl;
   }
+}
+
+__global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, int64_t t_next,
+                               double *__restrict__ x, double *__restrict__ v,
+                               double *__restrict__ a, double *__restrict__ jk,
+                               int64_t *__restrict__ t_tick, int32_t *__restrict__ lev,
+                               const double *__restrict__ a1, const double *__restrict__ j1,
+                               double eta, int lev_min, int lev_max, int block_steps,
+                               unsigned long long *n_clamped, const int64_t *ctl) {
+  if (ctl) {
+    t_next = ctl[kCtlTnext];
+    n_act = ctl[kCtlNact];
+    if (t_next < 0) return;
+  }
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n_act;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    correct_one(k, act, t_next, x, v, a, jk, t_tick, lev, a1, j1, eta, lev_min, lev_max,
+                block_steps, n_clamped);
 }
 
 __global__ void init_levels_kernel(int64_t n, const double *__restrict__ a,
@@ -220,7 +240,7 @@ __global__ void due_count_kernel(int64_t n, const int64_t *__restrict__ t_tick,
 
 // Exclusive scan of the per-chunk counts in one CTA; total -> d_scal[1].
 __global__ void count_scan_kernel(int64_t nblk, int32_t *__restrict__ blk_count,
-                                  int64_t *d_scal) {
+                                  int64_t *d_scal, int64_t n_total) {
   __shared__ int64_t warp_tot[32];
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -255,7 +275,20 @@ __global__ void count_scan_kernel(int64_t nblk, int32_t *__restrict__ blk_count,
     if (threadIdx.x == blockDim.x - 1) carry = excl + c;
     __syncthreads();
   }
-  if (threadIdx.x == 0) d_scal[1] = carry;
+  if (threadIdx.x == 0) {
+    const int64_t t_next = d_scal[kCtlTnext];
+    if (t_next > d_scal[kCtlTend] || d_scal[kCtlBlocks] >= d_scal[kCtlMaxBlk]) {
+      // stop: nothing is due before the end time (or the step budget is
+      // spent); the scatter and every later kernel of the step do nothing
+      d_scal[kCtlTnext] = -1;
+      d_scal[kCtlNact] = 0;
+    } else {
+      d_scal[kCtlNact] = carry;
+      d_scal[kCtlBlocks] += 1;
+      d_scal[kCtlInter] += carry * n_total;
+      d_scal[kCtlLastT] = t_next;
+    }
+  }
 }
 
 // Ordered compaction: chunk b writes its due indices, ascending, from the
@@ -372,12 +405,12 @@ __global__ void final_sum_kernel(int64_t cnt, const double *__restrict__ part, d
 cudaError_t launch_predict(int64_t n, int64_t t_next, const double *x, const double *v,
                            const double *a, const double *jk, const double *m,
                            const int64_t *t_tick, int prec, float4 *jhi, float4 *jlo,
-                           float4 *jvel, cudaStream_t s) {
+                           float4 *jvel, cudaStream_t s, const int64_t *ctl) {
   const int tb = 256;
   int64_t nb = (n + tb - 1) / tb;
   if (nb > 65535 * 16) nb = 65535 * 16;
   predict_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(n, t_next, x, v, a, jk, m, t_tick,
-                                                          prec, jhi, jlo, jvel);
+                                                          prec, jhi, jlo, jvel, ctl);
   return cudaGetLastError();
 }
 
@@ -394,13 +427,14 @@ cudaError_t launch_correct(int64_t n_act, const int32_t *act, int64_t t_next, do
                            double *v, double *a, double *jk, int64_t *t_tick, int32_t *lev,
                            const double *a1, const double *j1, double eta, int lev_min,
                            int lev_max, int block_steps, unsigned long long *n_clamped,
-                           cudaStream_t s) {
+                           cudaStream_t s, const int64_t *ctl) {
   if (n_act <= 0) return cudaSuccess;
   const int tb = 128;
-  const int64_t nb = (n_act + tb - 1) / tb;
+  int64_t nb = (n_act + tb - 1) / tb;
+  if (ctl && nb > 1216) nb = 1216;  // grid-stride over a bound on the count
   correct_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(
       n_act, act, t_next, x, v, a, jk, t_tick, lev, a1, j1, eta, lev_min, lev_max,
-      block_steps, n_clamped);
+      block_steps, n_clamped, ctl);
   return cudaGetLastError();
 }
 
@@ -429,7 +463,7 @@ cudaError_t launch_next_block(int64_t n, const int64_t *t_tick, const int32_t *l
                                                                           d_scal);
   due_count_kernel<<<static_cast<unsigned>(nblk), kSchedThreads, 0, s>>>(n, t_tick, lev,
                                                                           d_scal, blk_count);
-  count_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, d_scal);
+  count_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, d_scal, n);
   due_scatter_kernel<<<static_cast<unsigned>(nblk), kSchedThreads, 0, s>>>(
       n, t_tick, lev, d_scal, blk_count, act);
   if (launches) *launches += 4;

@@ -35,7 +35,32 @@ struct ForceArgs {
   double *jerk;        // (n_i, 3)
   double *part;        // partial sums of split i-blocks
   int *err;            // device error word
+  // Device-resident mode (block steps replayed from a CUDA graph): when ctl
+  // is set the active count is ctl[kCtlNact]; a launch does nothing unless
+  // it lies in [lo, hi), and the stream-K split is derived on the device.
+  const int64_t *ctl = nullptr;
+  int64_t lo = 0, hi = 0;
 };
+
+// Layout of the context's small device control array (int64 slots).
+constexpr int kCtlTnext = 0;    // t_next of the current block (ticks); -1 = stop
+constexpr int kCtlNact = 1;     // active count of the current block
+constexpr int kCtlErr = 2;      // device error word (low 32 bits)
+constexpr int kCtlClamped = 3;  // step-criterion clamps
+constexpr int kCtlBlocks = 4;   // block steps taken on the device
+constexpr int kCtlTend = 5;     // stop when the next block would pass this tick
+constexpr int kCtlMaxBlk = 6;   // ... or when kCtlBlocks reaches this count
+constexpr int kCtlInter = 7;    // interactions evaluated on the device
+constexpr int kCtlLastT = 8;    // t of the last block taken on the device
+constexpr int kCtlSlots = 16;
+
+// Minimum j-tiles per CTA of the stream-K split (short lists are
+// latency-bound; fewer split segments keep the fix-up short).
+constexpr int64_t kMinUnits = 4;
+
+// Active-list lengths where the built-in force shape changes.
+constexpr int64_t kBucketMid = 64;
+constexpr int64_t kBucketLong = 1024;
 
 // Records the per-thread error message returned by nb_last_error() and
 // returns status unchanged (defined in nb_api.cu, shared by every C-ABI file).
@@ -69,27 +94,38 @@ int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap);
 // Returns the number of kernel launches through *launches.
 cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
                          int *launches);
+// Device-resident form: A.ctl, A.lo, A.hi set; `grid` is the largest
+// persistent grid of the variant and n_max bounds the active count.
+cudaError_t launch_force_dev(int v, const ForceArgs &A, int grid, int64_t n_max,
+                             cudaStream_t s, int *launches);
 
 // --- Hermite and bookkeeping kernels (nb_hermite.cu) ---
+// With ctl set, t_next is read from ctl[kCtlTnext] (negative: no-op).
 cudaError_t launch_predict(int64_t n, int64_t t_next, const double *x,
                            const double *v, const double *a, const double *jk,
                            const double *m, const int64_t *t_tick, int prec,
                            float4 *jhi, float4 *jlo, float4 *jvel,
-                           cudaStream_t s);
+                           cudaStream_t s, const int64_t *ctl = nullptr);
 cudaError_t launch_pad_records(int64_t n, int64_t n_pad, float4 *jhi,
                                float4 *jlo, float4 *jvel, cudaStream_t s);
+// With ctl set, n_act and t_next come from ctl (n_act is then a bound).
 cudaError_t launch_correct(int64_t n_act, const int32_t *act, int64_t t_next,
                            double *x, double *v, double *a, double *jk,
                            int64_t *t_tick, int32_t *lev, const double *a1,
                            const double *j1, double eta, int lev_min,
                            int lev_max, int block_steps,
-                           unsigned long long *n_clamped, cudaStream_t s);
+                           unsigned long long *n_clamped, cudaStream_t s,
+                           const int64_t *ctl = nullptr);
 cudaError_t launch_init_levels(int64_t n, const double *a, const double *jk,
                                double eta_start, int lev_min, int lev_max,
                                int block_steps, int lev_shared, int32_t *lev,
                                int64_t *t_tick, cudaStream_t s);
-// Writes t_next (ticks) and n_act to d_scal[0], d_scal[1] and the active
-// list to act.  Returns the number of launches through *launches.
+// Writes t_next (ticks) and n_act to d_scal[kCtlTnext], d_scal[kCtlNact]
+// and the active list to act.  When the next block would pass
+// d_scal[kCtlTend] or d_scal[kCtlBlocks] has reached d_scal[kCtlMaxBlk],
+// t_next is set to -1 and n_act to 0 (everything after it is a no-op);
+// otherwise kCtlBlocks, kCtlInter (n_act * n) and kCtlLastT advance.
+// Returns the number of launches through *launches.
 cudaError_t launch_next_block(int64_t n, const int64_t *t_tick,
                               const int32_t *lev, int32_t *act,
                               int32_t *blk_count, int64_t *d_scal,

@@ -280,3 +280,50 @@ def test_block_workload_65536_sampled_parity(nb, oracle_mod):
             assert row["cond_jerk"] <= 1e-5 and row["norm_jerk"] <= 1e-5
         else:
             assert row["cond_acc"] <= 1e-3
+
+
+def test_device_resident_blocks_match_host_loop(nb):
+    """nb_run_blocks (CUDA-graph replays, active count kept on the device)
+    takes exactly the block steps of an nb_step loop: same schedule, same
+    bits, with and without a step budget."""
+    n = 4096
+    m, x, v = ics.plummer(n, 31, masses=ics.salpeter_masses(n, 31))
+    kw = dict(eps=1e-4, eta=0.02, lev_min=6, lev_max=20)
+    t_end = 2.0**-6
+    with nb.NBody(m, x, v, **kw) as a:
+        steps = a.run_until(t_end)
+        sa = a.get_state()
+    with nb.NBody(m, x, v, **kw) as b:
+        done, t_last = b.run_blocks(t_end)
+        sb = b.get_state()
+        cnt = b.counters()
+    assert done == steps and t_last == t_end and cnt["blocks"] == steps
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    with nb.NBody(m, x, v, **kw) as c:
+        d1, _ = c.run_blocks(t_end, max_blocks=7)
+        assert d1 == 7
+        d2, t2 = c.run_blocks(t_end)
+        assert d1 + d2 == steps and t2 == t_end
+        sc = c.get_state()
+        # the host path works again after device-resident steps
+        c.step()
+    for k in sa:
+        assert np.array_equal(sa[k], sc[k]), k
+
+
+def test_device_resident_shared_steps_and_fp32(nb):
+    n = 3000
+    m, x, v = ics.plummer(n, 8)
+    for prec in ("ds", "fp32"):
+        kw = dict(eps=1e-3, precision=prec, block_steps=False, lev_shared=8)
+        with nb.NBody(m, x, v, **kw) as a:
+            for _ in range(40):
+                a.step()
+            sa = a.get_state()
+        with nb.NBody(m, x, v, **kw) as b:
+            done, t_last = b.run_blocks(40 * 2.0**-8)
+            sb = b.get_state()
+        assert done == 40 and t_last == 40 * 2.0**-8
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), (prec, k)
