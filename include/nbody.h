@@ -183,6 +183,17 @@ int64_t nb_launch_count(const nb_ctx *ctx);
  * one whose precision differs from the context's. */
 nb_status nb_set_force_variant(nb_ctx *ctx, int32_t variant, int32_t grid_ctas);
 
+/* Data layout helper (host only): a permutation that lists the n particles
+ * (x: (n,3) host array) leaf by leaf of a balanced bisection tree whose
+ * leaves hold `leaf` particles (256 matches the force kernels' tiles):
+ * perm[k] is the particle to store at position k.  Storing particles in
+ * this order makes the kernels' 256-record tiles and i-blocks spatially
+ * compact, which lets the split-precision kernel take its tile-relative
+ * far-field path for most tiles; it changes no result beyond rounding
+ * order.  Deterministic (ties broken by index). */
+nb_status nb_spatial_order(int64_t n, const double *x, int64_t leaf,
+                           int64_t *perm);
+
 /* Install a tuning table for the built-in variant choice: for an active
  * list of n_i particles the first entry k (in order) with n_i >= min_n[k]
  * gives the variant; lists shorter than every min_n fall back to the

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("nb_sync", C.c_int, [_vp]),
     ("nb_launch_count", _i64, [_vp]),
     ("nb_set_force_variant", C.c_int, [_vp, _i32, _i32]),
+    ("nb_spatial_order", C.c_int, [_i64, _vp, _i64, _vp]),
     ("nb_set_force_table", C.c_int, [_vp, _i32, _vp, _vp]),
     ("nb_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     ("nb_debug_inject", C.c_int, [_vp, _i32]),
@@ -155,6 +156,16 @@ def num_variants() -> int:
     while L.nb_variant_info(v, None, None, None, None, None) == NB_OK:
         v += 1
     return v
+
+
+def spatial_order(x, leaf: int = 256) -> np.ndarray:
+    """Permutation (int64) that stores particles leaf by leaf of a balanced
+    bisection tree (see nb_spatial_order in include/nbody.h)."""
+    x = _f64(x, (-1, 3))
+    perm = np.zeros(x.shape[0], dtype=np.int64)
+    _check(load().nb_spatial_order(x.shape[0], x.ctypes.data, int(leaf),
+                                   perm.ctypes.data if x.shape[0] else None))
+    return perm
 
 
 def default_config() -> Config:

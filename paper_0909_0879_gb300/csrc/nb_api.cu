@@ -7,7 +7,9 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <atomic>
+#include <numeric>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -74,6 +76,47 @@ int64_t tick_of(double t, bool *ok) {
 
 }  // namespace
 
+
+namespace {
+
+// Balanced recursive bisection: split [lo, hi) of perm at a multiple of
+// `leaf` particles along the longest side of its bounding box (ties broken
+// by index, so the order is fully determined), recurse on both halves.
+void kd_split(const double *x, int64_t *perm, int64_t lo, int64_t hi, int64_t leaf) {
+  while (hi - lo > leaf) {
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int64_t k = lo; k < hi; ++k)
+      for (int c = 0; c < 3; ++c) {
+        const double v = x[3 * perm[k] + c];
+        mn[c] = v < mn[c] ? v : mn[c];
+        mx[c] = v > mx[c] ? v : mx[c];
+      }
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+      if (mx[c] - mn[c] > mx[ax] - mn[ax]) ax = c;
+    const int64_t leaves = (hi - lo + leaf - 1) / leaf;
+    const int64_t mid = lo + leaf * ((leaves + 1) / 2);
+    std::nth_element(perm + lo, perm + mid, perm + hi, [&](int64_t a, int64_t b) {
+      const double va = x[3 * a + ax], vb = x[3 * b + ax];
+      return va < vb || (va == vb && a < b);
+    });
+    kd_split(x, perm, lo, mid, leaf);
+    lo = mid;  // tail loop on the right half
+  }
+}
+
+}  // namespace
+
+extern "C" nb_status nb_spatial_order(int64_t n, const double *x, int64_t leaf,
+                                      int64_t *perm) {
+  if (n < 0 || !x || !perm || leaf < 1)
+    return fail(NB_ERR_INVALID_ARG, "need n >= 0, leaf >= 1 and non-null arrays");
+  if (!finite_all(x, 3 * n)) return fail(NB_ERR_INVALID_ARG, "non-finite position");
+  std::iota(perm, perm + n, int64_t(0));
+  kd_split(x, perm, 0, n, leaf);
+  return NB_OK;
+}
+
 struct nb_ctx {
   int64_t n = 0, n_pad = 0, n_jt = 0;
   nb_config cfg{};
@@ -85,6 +128,7 @@ struct nb_ctx {
   int64_t *t_tick = nullptr;
   int32_t *lev = nullptr;
   float4 *jhi = nullptr, *jlo = nullptr, *jvel = nullptr;  // j-records
+  float4 *jrel = nullptr, *tinfo = nullptr;  // tile-relative records, tile boxes (DS)
   int32_t *act = nullptr;       // active list
   int32_t *blk = nullptr;       // scheduling scratch
   int64_t *scal = nullptr;      // [0] t_next ticks, [1] n_act
@@ -219,6 +263,8 @@ nb_status queue_force(nb_ctx *c, const int32_t *d_idx, int64_t n_i, double *d_ac
   A.jhi = c->jhi;
   A.jlo = c->jlo;
   A.jvel = c->jvel;
+  A.jrel = c->jrel;
+  A.tinfo = c->tinfo;
   A.n_jt = c->n_jt;
   A.idx = d_idx;
   A.n_i = n_i;
@@ -239,6 +285,10 @@ nb_status queue_predict(nb_ctx *c, int64_t tick) {
   NB_CUDA(launch_predict(c->n, tick, c->x, c->v, c->a, c->jk, c->m, c->t_tick,
                          c->cfg.precision, c->jhi, c->jlo, c->jvel, c->stream));
   c->launches += 1;
+  if (c->jrel) {
+    NB_CUDA(launch_tile_info(c->n, c->n_jt, c->jhi, c->jlo, c->jrel, c->tinfo, c->stream));
+    c->launches += 1;
+  }
   c->t_pred = tick;
   return NB_OK;
 }
@@ -357,7 +407,11 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRY(dev_alloc_t(c, &c->t_tick, n));
   TRY(dev_alloc_t(c, &c->lev, n));
   TRY(dev_alloc_t(c, &c->jhi, c->n_pad));
-  if (cfg->precision == NB_DS) TRY(dev_alloc_t(c, &c->jlo, c->n_pad));
+  if (cfg->precision == NB_DS) {
+    TRY(dev_alloc_t(c, &c->jlo, c->n_pad));
+    TRY(dev_alloc_t(c, &c->jrel, c->n_pad));
+    TRY(dev_alloc_t(c, &c->tinfo, 2 * c->n_jt));
+  }
   TRY(dev_alloc_t(c, &c->jvel, c->n_pad));
   TRY(dev_alloc_t(c, &c->act, n));
   TRY(dev_alloc_t(c, &c->blk, next_block_scratch_ints(n) + 1));
@@ -619,12 +673,16 @@ nb_status queue_device_blocks(nb_ctx *c, cudaStream_t s) {
     NB_CUDA(launch_next_block(c->n, c->t_tick, c->lev, c->act, c->blk, c->scal, s, &nl));
     NB_CUDA(launch_predict(c->n, 0, c->x, c->v, c->a, c->jk, c->m, c->t_tick, prec, c->jhi,
                            c->jlo, c->jvel, s, c->scal));
+    if (c->jrel)
+      NB_CUDA(launch_tile_info(c->n, c->n_jt, c->jhi, c->jlo, c->jrel, c->tinfo, s, c->scal));
     for (int k = 0; k < nbk; ++k) {
       if (b[k].lo > c->n) continue;
       ForceArgs A;
       A.jhi = c->jhi;
       A.jlo = c->jlo;
       A.jvel = c->jvel;
+      A.jrel = c->jrel;
+      A.tinfo = c->tinfo;
       A.n_jt = c->n_jt;
       A.idx = c->act;
       A.n_i = 0;

@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <mutex>
 #include <type_traits>
+#include <utility>
 
 namespace nbi {
 
@@ -188,7 +189,7 @@ __host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) 
   return static_cast<int>(((u + 1) * static_cast<uint64_t>(P) - 1) / U);
 }
 
-template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK, int SACC>
+template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK, int SACC, int REL>
 __global__ void __launch_bounds__(NT, 1)
     force_jerk_kernel(const ForceArgs A, uint64_t U, int P) {
   using V = typename std::conditional<PACK != 0, float2, float>::type;
@@ -198,7 +199,9 @@ __global__ void __launch_bounds__(NT, 1)
   constexpr int NQ = IPT / W;     // packed i-groups per thread
   constexpr int NG = NT / TPI;    // i-slots per CTA (per q)
   constexpr int BI = NG * IPT;    // i-particles per i-block
-  constexpr int NARR = PREC ? 3 : 2;
+  static_assert(!REL || PREC, "tile-relative coordinates only help the split-precision kernel");
+  constexpr int NARR = PREC ? (REL ? 4 : 3) : 2;  // hi, lo, vel, rel
+  constexpr int kOffV = PREC ? 2 : 1;             // velocity array within a stage
   constexpr uint32_t kTileBytes = kJT * 16;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -239,7 +242,8 @@ __global__ void __launch_bounds__(NT, 1)
     mbar_expect_tx(&bars[st], kTileBytes * NARR);
     bulk_g2s(dst, A.jhi + jt * kJT, kTileBytes, &bars[st]);
     if (PREC) bulk_g2s(dst + kJT, A.jlo + jt * kJT, kTileBytes, &bars[st]);
-    bulk_g2s(dst + (NARR - 1) * kJT, A.jvel + jt * kJT, kTileBytes, &bars[st]);
+    bulk_g2s(dst + kOffV * kJT, A.jvel + jt * kJT, kTileBytes, &bars[st]);
+    if (REL) bulk_g2s(dst + 3 * kJT, A.jrel + jt * kJT, kTileBytes, &bars[st]);
   };
   if (tid == 0) {
     const uint64_t pre = nunits < kStages ? nunits : kStages;
@@ -272,6 +276,52 @@ __global__ void __launch_bounds__(NT, 1)
       O::set(nvi[qq][0], wl, -w.x); O::set(nvi[qq][1], wl, -w.y); O::set(nvi[qq][2], wl, -w.z);
     }
     const V veps2 = O::bc(eps2);
+    // bounding box of the i-block (tile-relative far-field test)
+    float bc_i[3] = {0.f, 0.f, 0.f}, bh_i[3] = {0.f, 0.f, 0.f};
+    if (REL) {
+      __shared__ float s_mn[3][NT / 32], s_mx[3][NT / 32];
+      float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        const int64_t k = static_cast<int64_t>(ib) * BI + g + q * NG;
+        if (k < n_i) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float xv = -O::lane(nxh[q / W][c], q % W);
+            mn[c] = fminf(mn[c], xv);
+            mx[c] = fmaxf(mx[c], xv);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+          mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+        }
+      }
+      __syncthreads();  // the previous segment's readers are done
+      if ((tid & 31) == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          s_mn[c][tid >> 5] = mn[c];
+          s_mx[c][tid >> 5] = mx[c];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float a = s_mn[c][0], b = s_mx[c][0];
+        for (int w = 1; w < NT / 32; ++w) {
+          a = fminf(a, s_mn[c][w]);
+          b = fmaxf(b, s_mx[c][w]);
+        }
+        bc_i[c] = 0.5f * a + 0.5f * b;
+        const float big = fmaxf(fabsf(a), fabsf(b));
+        bh_i[c] = fmaxf(bc_i[c] - a, b - bc_i[c]) * (1.0f + 1.0e-6f) + big * 1.2e-7f;
+      }
+    }
     DsAcc<IPT, NT, SACC != 0> D;
     D.init(reinterpret_cast<float *>(sbase + static_cast<size_t>(kStages) * NARR * kJT), tid);
 
@@ -281,7 +331,32 @@ __global__ void __launch_bounds__(NT, 1)
       const bool ok = mbar_wait(&bars[st], ph);
       const float4 *sh = sbase + static_cast<size_t>(st) * NARR * kJT;
       const float4 *sl = sh + kJT;
-      const float4 *sv = sh + (NARR - 1) * kJT;
+      const float4 *sv = sh + kOffV * kJT;
+      const float4 *sr = sh + 3 * kJT;
+      // far tile: pair differences from tile-relative FP32 coordinates
+      bool fast = false;
+      V ndx[NQ][3];
+      if (REL) {
+        const uint64_t jt = (u0 + s_idx) % n_jt;
+        const float4 to = __ldg(&A.tinfo[2 * jt]);
+        const float4 th = __ldg(&A.tinfo[2 * jt + 1]);
+        const float ox[3] = {to.x, to.y, to.z}, hw[3] = {th.x, th.y, th.z};
+        float d2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float d = fmaxf(0.f, fabsf(bc_i[c] - ox[c]) - (bh_i[c] + hw[c]));
+          d2 = fmaf(d, d, d2);
+        }
+        const float lim = kRelKappa * to.w * (1.0f + 1.0e-5f);
+        fast = d2 >= lim * lim;
+        if (fast) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              ndx[q][c] = O::add(O::add(nxh[q][c], O::bc(ox[c])), nxl[q][c]);
+        }
+      }
 
       V p1[NQ][3], p2[NQ][3];
 #pragma unroll
@@ -295,6 +370,8 @@ __global__ void __launch_bounds__(NT, 1)
       // of the few additions that follow it in its chunk), the jerk's once
       // per tile (its tolerance is ten times looser).
       constexpr int CH = (PREC && kFoldChunk < kJT / TPI) ? kFoldChunk : kJT / TPI;
+      auto walk_tile = [&](auto far_tag) {
+        constexpr bool FAR = decltype(far_tag)::value;
 #pragma unroll 1
       for (int c0 = r; c0 < kJT; c0 += CH * TPI) {
         V pa[NQ][3];
@@ -304,16 +381,24 @@ __global__ void __launch_bounds__(NT, 1)
           for (int c = 0; c < 3; ++c) pa[q][c] = O::bc(0.f);
 #pragma unroll 4
         for (int jj = c0; jj < c0 + CH * TPI; jj += TPI) {
-          const float4 hj = sh[jj];
           const float4 wj = sv[jj];
-          float4 lj;
-          if (PREC) lj = sl[jj];
+          float4 hj, lj;
+          if (FAR) {
+            hj = sr[jj];
+          } else {
+            hj = sh[jj];
+            if (PREC) lj = sl[jj];
+          }
           const V xj = O::bc(hj.x), yj = O::bc(hj.y), zj = O::bc(hj.z), mj = O::bc(hj.w);
           const V vxj = O::bc(wj.x), vyj = O::bc(wj.y), vzj = O::bc(wj.z);
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             V dx, dy, dz;
-            if (PREC) {
+            if (FAR) {
+              dx = O::add(xj, ndx[q][0]);
+              dy = O::add(yj, ndx[q][1]);
+              dz = O::add(zj, ndx[q][2]);
+            } else if (PREC) {
               dx = O::add(O::add(xj, nxh[q][0]), O::add(O::bc(lj.x), nxl[q][0]));
               dy = O::add(O::add(yj, nxh[q][1]), O::add(O::bc(lj.y), nxl[q][1]));
               dz = O::add(O::add(zj, nxh[q][2]), O::add(O::bc(lj.z), nxl[q][2]));
@@ -353,6 +438,11 @@ __global__ void __launch_bounds__(NT, 1)
               D.AH(q, c) += x;
           }
       }
+      };
+      if (REL && fast)
+        walk_tile(std::true_type{});
+      else
+        walk_tile(std::false_type{});
       // fold the tile's jerk partial sums (jerk = p1 - 3 p2)
 #pragma unroll
       for (int q = 0; q < IPT; ++q)
@@ -469,11 +559,14 @@ struct Entry {
 };
 
 #define NB_V(PREC, IPT, TPI, NT, MASK, PACK)             \
-  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0},       \
-        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0>}
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 0},    \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 0>}
 #define NB_VS(PREC, IPT, TPI, NT, MASK, PACK)            \
-  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 1},       \
-        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 1>}
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 1, 0},    \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 1, 0>}
+#define NB_VR(PREC, IPT, TPI, NT, MASK, PACK)            \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 1},    \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 1>}
 
 // The compiled shape table.  Index order is part of the tuning interface.
 const Entry kTable[] = {
@@ -503,11 +596,14 @@ const Entry kTable[] = {
     NB_VS(1, 8, 1, 256, 0, 1),  // 23 DS, packed, 8 i-particles per thread
     NB_VS(1, 6, 1, 256, 0, 1),  // 24
     NB_VS(0, 8, 1, 256, 0, 1),  // 25 FP32, packed, 8 i-particles per thread
+    NB_VR(1, 4, 1, 256, 0, 1),  // 26 DS, packed, far tiles tile-relative
+    NB_VR(1, 2, 1, 256, 0, 1),  // 27
+    NB_VR(1, 2, 4, 256, 0, 1),  // 28
 };
 constexpr int kNumVariants = sizeof(kTable) / sizeof(kTable[0]);
 
 size_t smem_bytes(const Variant &V) {
-  return static_cast<size_t>(kStages) * (V.prec ? 3 : 2) * kJT * sizeof(float4) +
+  return static_cast<size_t>(kStages) * (V.prec ? (V.rel ? 4 : 3) : 2) * kJT * sizeof(float4) +
          (V.sacc ? static_cast<size_t>(12) * V.ipt * V.threads * sizeof(float) : 0);
 }
 
@@ -522,13 +618,15 @@ int block_i(const Variant &V) { return V.threads / V.tpi * V.ipt; }
 
 int choose_variant(int prec, int mask, int64_t n_i) {
   // Built-in choice from timings on a GB300 (N = 1M King, every shape):
-  // packed FP32x2 variants for long lists, more threads per i-particle as
-  // the list shortens.  The bucket edges (kBucketMid, kBucketLong) are the
+  // packed FP32x2 variants for long lists (split precision with the
+  // tile-relative far field, which costs ~1% when particles are not stored
+  // in a spatial order and gains ~4-8% when they are), more threads per
+  // i-particle as the list shortens.  The bucket edges (kBucketMid, kBucketLong) are the
   // ones the device-resident block steps use, so both paths run the same
   // shapes.  nb_set_force_table overrides it per workload.
   if (mask) return prec ? 10 : 11;
   if (prec) {
-    if (n_i >= kBucketLong) return 12;
+    if (n_i >= kBucketLong) return 26;
     if (n_i >= kBucketMid) return 16;
     return 4;
   }

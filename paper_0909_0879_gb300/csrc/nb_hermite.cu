@@ -72,6 +72,67 @@ __global__ void pad_kernel(int64_t n, int64_t n_pad, float4 *jhi, float4 *jlo,
   jvel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// One CTA per tile of kJT records.
+__global__ void __launch_bounds__(kJT)
+    tile_info_kernel(int64_t n, const float4 *__restrict__ jhi, const float4 *__restrict__ jlo,
+                     float4 *__restrict__ jrel, float4 *__restrict__ tinfo,
+                     const int64_t *ctl) {
+  if (ctl && ctl[kCtlTnext] < 0) return;
+  __shared__ float smn[3][kJT / 32], smx[3][kJT / 32];
+  __shared__ float4 s_o;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * kJT + tid;
+  const bool real = j < n;
+  const float4 h = jhi[j];
+  float mn[3], mx[3];
+  const float hv[3] = {h.x, h.y, h.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mn[c] = real ? hv[c] : 3.0e38f;
+    mx[c] = real ? hv[c] : -3.0e38f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+      mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+    }
+    if (lane == 0) {
+      smn[c][wid] = mn[c];
+      smx[c][wid] = mx[c];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float o[3], hw[3];
+    float r2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float a = smn[c][0], b = smx[c][0];
+      for (int w = 1; w < kJT / 32; ++w) {
+        a = fminf(a, smn[c][w]);
+        b = fmaxf(b, smx[c][w]);
+      }
+      o[c] = 0.5f * a + 0.5f * b;
+      // half-width covering [a, b] about o, the low words (below half an
+      // ulp of the high word) and the rounding of o
+      const float big = fmaxf(fabsf(a), fabsf(b));
+      hw[c] = fmaxf(o[c] - a, b - o[c]) * (1.0f + 1.0e-6f) + big * 1.2e-7f;
+      r2 = fmaf(hw[c], hw[c], r2);
+    }
+    const float R = sqrtf(r2) * (1.0f + 1.0e-6f);
+    tinfo[2 * blockIdx.x] = make_float4(o[0], o[1], o[2], R);
+    tinfo[2 * blockIdx.x + 1] = make_float4(hw[0], hw[1], hw[2], 0.f);
+    s_o = make_float4(o[0], o[1], o[2], 0.f);
+  }
+  __syncthreads();
+  if (real) {
+    const float4 l = jlo[j];
+    const float4 o = s_o;
+    jrel[j] = make_float4((h.x - o.x) + l.x, (h.y - o.y) + l.y, (h.z - o.z) + l.z, h.w);
+  } else {
+    jrel[j] = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
+  }
+}
+
 __device__ __forceinline__ double norm3(const double u[3]) {
   return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 }
@@ -411,6 +472,12 @@ cudaError_t launch_predict(int64_t n, int64_t t_next, const double *x, const dou
   if (nb > 65535 * 16) nb = 65535 * 16;
   predict_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(n, t_next, x, v, a, jk, m, t_tick,
                                                           prec, jhi, jlo, jvel, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_info(int64_t n, int64_t n_jt, const float4 *jhi, const float4 *jlo,
+                             float4 *jrel, float4 *tinfo, cudaStream_t s, const int64_t *ctl) {
+  tile_info_kernel<<<static_cast<unsigned>(n_jt), kJT, 0, s>>>(n, jhi, jlo, jrel, tinfo, ctl);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ struct ForceArgs {
   const float4 *jhi;   // (x, y, z, m): FP32 values, or the high words (DS)
   const float4 *jlo;   // (x_lo, y_lo, z_lo, 0): low words (DS only)
   const float4 *jvel;  // (vx, vy, vz, 0)
+  const float4 *jrel;  // (x - O_t, m): position relative to its tile's origin
+  const float4 *tinfo; // per tile: (O_t, R_t), (half-widths of the box, 0)
   int64_t n_jt;        // j-tiles; records are padded to n_jt * kJT
   const int32_t *idx;  // i-list (n_i entries); nullptr = 0..n_i-1
   int64_t n_i;
@@ -77,7 +79,14 @@ struct Variant {
   int mask;     // 1: zero the i == j term (eps == 0)
   int pack;     // 1: two i-particles per packed FP32x2 instruction
   int sacc;     // 1: split-precision accumulators in shared memory
+  int rel;      // 1: far tiles in tile-relative FP32 coordinates (DS only)
 };
+
+// A tile is "far" from an i-block when the distance between their bounding
+// boxes is at least kRelKappa times the tile's radius; then positions
+// relative to the tile's origin carry a relative error of at most
+// 2^-23 (1.5 + 2 / kRelKappa) in every pair difference.
+constexpr float kRelKappa = 3.0f;
 
 int num_variants();
 const Variant &variant_at(int v);
@@ -108,6 +117,12 @@ cudaError_t launch_predict(int64_t n, int64_t t_next, const double *x,
                            cudaStream_t s, const int64_t *ctl = nullptr);
 cudaError_t launch_pad_records(int64_t n, int64_t n_pad, float4 *jhi,
                                float4 *jlo, float4 *jvel, cudaStream_t s);
+// Per 256-record tile: bounding box, origin O_t (FP32 box centre), radius
+// R_t, and every record's position relative to O_t.  With ctl set, a
+// negative ctl[kCtlTnext] makes it a no-op.
+cudaError_t launch_tile_info(int64_t n, int64_t n_jt, const float4 *jhi,
+                             const float4 *jlo, float4 *jrel, float4 *tinfo,
+                             cudaStream_t s, const int64_t *ctl = nullptr);
 // With ctl set, n_act and t_next come from ctl (n_act is then a bound).
 cudaError_t launch_correct(int64_t n_act, const int32_t *act, int64_t t_next,
                            double *x, double *v, double *a, double *jk,

@@ -28,6 +28,7 @@ __all__ = [
     "uniform_sphere",
     "random_active_subset",
     "cluster_sizes",
+    "morton_order",
 ]
 
 
@@ -281,3 +282,27 @@ def cluster_sizes(n_clusters: int, seed, lo: int = 16, hi: int = 1024) -> np.nda
     rng = rng_for(seed)
     s = np.round(np.exp(rng.uniform(math.log(lo), math.log(hi), n_clusters)))
     return np.clip(s, lo, hi).astype(np.int64)
+
+
+def morton_order(x: np.ndarray, bits: int = 21) -> np.ndarray:
+    """Permutation that lists particles along a Morton (Z-order) curve of
+    their positions: coordinates are quantised to ``bits`` bits over the
+    bounding cube and interleaved into one integer key.  Spatially close
+    particles get close indices (a data-layout choice; it changes no
+    value)."""
+    x = np.asarray(x, dtype=np.float64)
+    lo = x.min(axis=0)
+    span = float((x.max(axis=0) - lo).max()) or 1.0
+    q = np.minimum(((x - lo) / span * (2**bits - 1)).astype(np.uint64), np.uint64(2**bits - 1))
+
+    def spread(v):
+        v = v & np.uint64(0x1FFFFF)
+        v = (v | (v << np.uint64(32))) & np.uint64(0x1F00000000FFFF)
+        v = (v | (v << np.uint64(16))) & np.uint64(0x1F0000FF0000FF)
+        v = (v | (v << np.uint64(8))) & np.uint64(0x100F00F00F00F00F)
+        v = (v | (v << np.uint64(4))) & np.uint64(0x10C30C30C30C30C3)
+        v = (v | (v << np.uint64(2))) & np.uint64(0x1249249249249249)
+        return v
+
+    key = spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1)) | (spread(q[:, 2]) << np.uint64(2))
+    return np.argsort(key, kind="stable")

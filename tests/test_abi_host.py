@@ -99,3 +99,31 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_spatial_order_is_a_balanced_tree_layout(lib):
+    """Host-only helper: a permutation whose 256-particle leaves are compact
+    and balanced, deterministic for the same input."""
+    from paper_0909_0879_gb300 import _lib, ics
+
+    m, x, v = ics.king(10000, 7.0, 3)
+    p = _lib.spatial_order(x, 256)
+    assert np.array_equal(np.sort(p), np.arange(10000))
+    assert np.array_equal(p, _lib.spatial_order(x, 256))
+    xs = x[p]
+    # leaf boxes are far smaller than those of the unordered particles
+    tiles = [np.ptp(xs[k:k + 256], axis=0).max() for k in range(0, 9984, 256)]
+    raw = [np.ptp(x[k:k + 256], axis=0).max() for k in range(0, 9984, 256)]
+    assert np.median(tiles) < 0.6 * np.median(raw)
+    # uniform points: each leaf's box holds about its share of the volume
+    u = np.random.default_rng(1).uniform(0, 1, (65536, 3))
+    pu = _lib.spatial_order(u, 256)
+    vol = [np.prod(np.ptp(u[pu[k:k + 256]], axis=0)) for k in range(0, 65536, 256)]
+    assert np.mean(vol) < 2.0 * 256 / 65536
+    # a set of the same points in another order gives the same leaf sets
+    q = np.random.default_rng(0).permutation(10000)
+    p2 = _lib.spatial_order(x[q], 256)
+    assert sorted(map(tuple, np.sort(q[p2][: 9984].reshape(-1, 256), axis=1))) == \
+        sorted(map(tuple, np.sort(p[: 9984].reshape(-1, 256), axis=1)))
+    with pytest.raises(_lib.NBodyError):
+        _lib.spatial_order(np.full((3, 3), np.nan), 256)

@@ -75,3 +75,18 @@ def test_random_subsets_and_cluster_sizes():
     assert s.min() >= 16 and s.max() <= 1024
     # log-uniform: the median is near sqrt(16 * 1024) = 128
     assert 110 < np.median(s) < 150
+
+
+def test_morton_order_is_a_spatial_permutation():
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1, 1, (5000, 3))
+    p = ics.morton_order(x)
+    assert np.array_equal(np.sort(p), np.arange(5000))
+    # consecutive particles along the curve are much closer than random pairs
+    d_curve = np.linalg.norm(np.diff(x[p], axis=0), axis=1).mean()
+    d_rand = np.linalg.norm(np.diff(x, axis=0), axis=1).mean()
+    assert d_curve < 0.2 * d_rand
+    # the 8 octants come out in Z order
+    pts = np.array([[-1, -1, -1], [1, -1, -1], [-1, 1, -1], [1, 1, -1],
+                    [-1, -1, 1], [1, -1, 1], [-1, 1, 1], [1, 1, 1]], dtype=float)
+    assert np.array_equal(ics.morton_order(pts[::-1]), np.arange(8)[::-1])
