@@ -416,20 +416,22 @@ __global__ void kinetic_kernel(int64_t n, const double *__restrict__ m,
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// w_i = m_i sum_{j != i} m_j / sqrt(r^2 + eps^2), FP64, j staged in tiles;
-// the block's sum of w_i goes to part[blockIdx.x].
+// w_i = m_i sum_{j > i} m_j / sqrt(r^2 + eps^2), FP64, j staged in tiles
+// from the CTA's own diagonal tile on (each pair once); the block's sum of
+// w_i goes to part[blockIdx.x].
 __global__ void potential_kernel(int64_t n, const double *__restrict__ m,
                                  const double *__restrict__ x, double eps2,
                                  double *__restrict__ part) {
   __shared__ double sx[kEnThreads], sy[kEnThreads], sz[kEnThreads], sm[kEnThreads];
   __shared__ double sh[kEnThreads];
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x;
+  const int64_t i = i0 + threadIdx.x;
   const bool valid = i < n;
   const double xi = valid ? x[3 * i] : 0.0;
   const double yi = valid ? x[3 * i + 1] : 0.0;
   const double zi = valid ? x[3 * i + 2] : 0.0;
   double w = 0.0;
-  for (int64_t j0 = 0; j0 < n; j0 += kEnThreads) {
+  for (int64_t j0 = i0; j0 < n; j0 += kEnThreads) {
     const int64_t jl = j0 + threadIdx.x;
     if (jl < n) {
       sx[threadIdx.x] = x[3 * jl];
@@ -439,10 +441,12 @@ __global__ void potential_kernel(int64_t n, const double *__restrict__ m,
     }
     __syncthreads();
     const int cnt = (n - j0) < kEnThreads ? static_cast<int>(n - j0) : kEnThreads;
-    for (int t = 0; t < cnt; ++t) {
+    // on the diagonal tile only j > i counts
+    const int t0 = (j0 == i0) ? static_cast<int>(threadIdx.x) + 1 : 0;
+    for (int t = t0; t < cnt; ++t) {
       const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
       const double s2 = dx * dx + dy * dy + dz * dz + eps2;
-      if (j0 + t != i) w += sm[t] / sqrt(s2);
+      w += sm[t] * rsqrt(s2);
     }
     __syncthreads();
   }
@@ -548,7 +552,7 @@ cudaError_t launch_energy(int64_t n, const double *m, const double *x, const dou
   kinetic_kernel<<<static_cast<unsigned>(nb), kEnThreads, 0, s>>>(n, m, v, pk);
   potential_kernel<<<static_cast<unsigned>(nb), kEnThreads, 0, s>>>(n, m, x, eps * eps, pw);
   final_sum_kernel<<<1, kEnThreads, 0, s>>>(nb, pk, 1.0, d_out, 0);
-  final_sum_kernel<<<1, kEnThreads, 0, s>>>(nb, pw, -0.5 * G, d_out, 1);
+  final_sum_kernel<<<1, kEnThreads, 0, s>>>(nb, pw, -G, d_out, 1);
   if (launches) *launches += 4;
   return cudaGetLastError();
 }
