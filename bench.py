@@ -478,25 +478,32 @@ def run_block65536(args):
     for prec in args.precisions.split(","):
         with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3, lev_max=20) as s:
             E0 = s.energy()[2]
-            if args.block_steps == 0:
-                # device-resident block steps (CUDA-graph replays); the
-                # host-driven loop below is then timed on the same state
-                e0, e1 = _events(torch)
-                c0 = s.counters()
-                t0 = time.perf_counter()
-                e0.record()
-                nblk, _ = s.run_blocks(t_end * 2.0**-20)
-                e1.record()
-                torch.cuda.synchronize()
-                wall_dev = time.perf_counter() - t0
-                ms_dev = e0.elapsed_time(e1)
-                c1 = s.counters()
-                E_dev = s.energy()[2]
-                dev_res = {"value": (c1["interactions"] - c0["interactions"]) / ms_dev / 1e6,
-                           "ms": ms_dev, "wall_s": wall_dev, "block_steps": nblk,
-                           "dE_over_E": abs(E_dev - E0) / abs(E0)}
-            else:
-                dev_res = None
+            dev_res = None
+        if args.block_steps == 0:
+            # device-resident block steps (CUDA-graph replays): the fused
+            # form and the general scheduler, each from the initial state
+            dev_res = {}
+            for mode in ("auto", "general"):
+                with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3,
+                                lev_max=20) as s:
+                    s.set_block_mode(mode)
+                    e0, e1 = _events(torch)
+                    c0 = s.counters()
+                    l0 = s.launch_count()
+                    t0 = time.perf_counter()
+                    e0.record()
+                    nblk, _ = s.run_blocks(t_end * 2.0**-20)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    wall_dev = time.perf_counter() - t0
+                    ms_dev = e0.elapsed_time(e1)
+                    c1 = s.counters()
+                    E_dev = s.energy()[2]
+                    dev_res[s.last_block_path()] = {
+                        "value": (c1["interactions"] - c0["interactions"]) / ms_dev / 1e6,
+                        "ms": ms_dev, "wall_s": wall_dev, "block_steps": nblk,
+                        "launches_per_block": (s.launch_count() - l0) / max(1, nblk),
+                        "dE_over_E": abs(E_dev - E0) / abs(E0)}
         with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3, lev_max=20) as s:
             hist = {}
             blocks = 0

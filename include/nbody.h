@@ -134,10 +134,32 @@ nb_status nb_step(nb_ctx *ctx, double *t_next, int64_t *n_active);
  * steps are the ones nb_step takes with the built-in force shapes (an
  * installed tuning table or a forced variant is not used here), so the
  * results are bit-identical to an nb_step loop under the built-in choice.
+ *
+ * Two forms of the same steps.  When every particle's next time is the
+ * first multiple of its step 2^-lev after the latest particle time (always
+ * true of states this library integrates from nb_init; block scheduling of
+ * the paper's Sec. 2, strategy (ii)), a fused form runs: the next block
+ * time comes from per-level particle counts kept on the device and the
+ * active list from the levels alone, so a step is three kinds of kernel
+ * (scheduling + predictor, force, fix-up + corrector).  Otherwise (a state
+ * set with nb_set_state that lacks the property) the general scheduler
+ * runs (minimum of t_i + dt_i over all particles).  A check kernel decides
+ * at the start of each call.  NB_ERR_DEVICE if a bounded device-side wait
+ * ran out.
  * Returns the number of block steps taken and the time of the last one.
  * t_end must be a tick multiple; particles due later stay where they are. */
 nb_status nb_run_blocks(nb_ctx *ctx, double t_end, int64_t max_blocks,
                         int64_t *blocks_done, double *t_last);
+
+/* Block-step form of nb_run_blocks: NB_BLOCKS_AUTO (default: fused when
+ * the schedule allows it) or NB_BLOCKS_GENERAL (always the general
+ * scheduler; for comparison).  No counterpart in the paper.
+ * NB_ERR_INVALID_ARG for another value. */
+enum { NB_BLOCKS_AUTO = 0, NB_BLOCKS_GENERAL = 1 };
+nb_status nb_set_block_mode(nb_ctx *ctx, int32_t mode);
+
+/* *fused = 1 if the last nb_run_blocks call ran the fused form, else 0. */
+nb_status nb_last_block_path(nb_ctx *ctx, int32_t *fused);
 
 /* Energy of the current (synchronised) state in FP64 on the GPU:
  * K = 1/2 sum m v^2, W = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)

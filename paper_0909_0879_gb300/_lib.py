@@ -56,6 +56,8 @@ SIGNATURES = [
     ("nb_correct", C.c_int, [_vp, _d]),
     ("nb_step", C.c_int, [_vp, _P(_d), _P(_i64)]),
     ("nb_run_blocks", C.c_int, [_vp, _d, _i64, _P(_i64), _P(_d)]),
+    ("nb_set_block_mode", C.c_int, [_vp, _i32]),
+    ("nb_last_block_path", C.c_int, [_vp, _P(_i32)]),
     ("nb_energy", C.c_int, [_vp, _P(_d), _P(_d), _P(_d)]),
     ("nb_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -274,6 +276,19 @@ class NBody:
         _check(self._L.nb_run_blocks(self._h, float(t_end), int(max_blocks), C.byref(nb),
                                      C.byref(tl)))
         return nb.value, tl.value
+
+    BLOCK_MODES = {"auto": 0, "general": 1}
+
+    def set_block_mode(self, mode: str):
+        """'auto': fused device-resident steps when the schedule allows them;
+        'general': always the general scheduler."""
+        _check(self._L.nb_set_block_mode(self._h, self.BLOCK_MODES[mode]))
+
+    def last_block_path(self) -> str:
+        """'fused' or 'general': the form the last run_blocks call ran."""
+        f = C.c_int32()
+        _check(self._L.nb_last_block_path(self._h, C.byref(f)))
+        return "fused" if f.value else "general"
 
     def run_until(self, t_end: float):
         """Block steps until every particle has reached t_end (a tick multiple

@@ -158,8 +158,14 @@ struct nb_ctx {
   int grid_cap = 0;
   int64_t launches = 0, n_blocks = 0, interactions = 0;
   bool inject_timeout = false;
-  cudaGraphExec_t blk_graph = nullptr;  // device-resident block steps
+  cudaGraphExec_t blk_graph = nullptr;  // device-resident block steps, general scheduler
   double *blk_graph_part = nullptr;
+  cudaGraphExec_t fus_graph = nullptr;  // device-resident block steps, fused kernels
+  double *fus_graph_part = nullptr;
+  unsigned long long *lb_status = nullptr;  // look-back words of the fused compaction
+  int block_mode = 0;                   // 0: fused when the schedule allows, 1: general
+  int last_fused = 0;                   // the last nb_run_blocks ran the fused steps
+  int64_t graph_launches = 0, fus_graph_launches = 0;  // kernels per replay
   std::vector<void *> allocs;
 };
 
@@ -216,8 +222,9 @@ nb_status sync_ctx(nb_ctx *c) {
   }
   const int err = static_cast<int>(c->h_scal[kCtlErr] & 0xffffffff);
   if (err != 0)
-    return fail(NB_ERR_DEVICE, "a force kernel's bounded wait for a shared-memory tile ran out "
-                               "(device error word 0x%x)", err);
+    return fail(NB_ERR_DEVICE, "a bounded device-side wait ran out: %s%s(device error word 0x%x)",
+                (err & kErrWaitTimeout) ? "force kernel shared-memory tile; " : "",
+                (err & kErrScanTimeout) ? "active-list look-back; " : "", err);
   return NB_OK;
 }
 
@@ -358,6 +365,7 @@ void nb_destroy(nb_ctx *c) {
   if (c->h_energy) cudaFreeHost(c->h_energy);
   if (c->ev) cudaEventDestroy(c->ev);
   if (c->blk_graph) cudaGraphExecDestroy(c->blk_graph);
+  if (c->fus_graph) cudaGraphExecDestroy(c->fus_graph);
   delete c;
 }
 
@@ -416,6 +424,7 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRY(dev_alloc_t(c, &c->act, n));
   TRY(dev_alloc_t(c, &c->blk, next_block_scratch_ints(n) + 1));
   TRY(dev_alloc_t(c, &c->scal, kCtlSlots));
+  TRY(dev_alloc_t(c, &c->lb_status, c->n_jt));
   // the device error word and the clamp counter live in scal[2] and scal[3]
   c->err = reinterpret_cast<int *>(c->scal + kCtlErr);
   c->clamped = reinterpret_cast<unsigned long long *>(c->scal + kCtlClamped);
@@ -455,6 +464,7 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRYC(cudaMemsetAsync(c->jk, 0, n3 * sizeof(double), st));
   TRYC(cudaMemsetAsync(c->t_tick, 0, n * sizeof(int64_t), st));
   TRYC(cudaMemsetAsync(c->scal, 0, kCtlSlots * sizeof(int64_t), st));
+  TRYC(cudaMemsetAsync(c->lb_status, 0, c->n_jt * sizeof(unsigned long long), st));
   // no end time and no block budget unless nb_run_blocks sets them
   c->h_scal[kCtlSlots + 0] = INT64_MAX;
   c->h_scal[kCtlSlots + 1] = INT64_MAX;
@@ -652,13 +662,14 @@ namespace {
 
 constexpr int kGraphSteps = 32;  // block steps per graph replay
 
-// Queue kGraphSteps device-resident block steps on stream s.
-nb_status queue_device_blocks(nb_ctx *c, cudaStream_t s) {
-  struct Bucket {
-    int64_t lo, hi;
-    int v;
-  };
-  Bucket b[3];
+// Force shapes of the device-resident steps: the built-in choice per
+// active-count bucket (the same shapes nb_step runs).
+struct Bucket {
+  int64_t lo, hi;
+  int v;
+};
+
+int step_buckets(const nb_ctx *c, Bucket *b) {
   int nbk = 0;
   const int prec = c->cfg.precision;
   if (c->cfg.eps == 0.0) {
@@ -668,40 +679,150 @@ nb_status queue_device_blocks(nb_ctx *c, cudaStream_t s) {
     b[nbk++] = {kBucketMid, kBucketLong, choose_variant(prec, 0, kBucketMid)};
     b[nbk++] = {kBucketLong, INT64_MAX, choose_variant(prec, 0, kBucketLong)};
   }
+  // buckets no active count can reach are left out
+  int k = 0;
+  for (int q = 0; q < nbk; ++q)
+    if (b[q].lo <= c->n) b[k++] = b[q];
+  return k;
+}
+
+ForceArgs device_force_args(const nb_ctx *c, const Bucket &b) {
+  ForceArgs A;
+  A.jhi = c->jhi;
+  A.jlo = c->jlo;
+  A.jvel = c->jvel;
+  A.jrel = c->jrel;
+  A.tinfo = c->tinfo;
+  A.n_jt = c->n_jt;
+  A.idx = c->act;
+  A.n_i = 0;
+  A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
+  A.G = c->cfg.G;
+  A.acc = c->a1;
+  A.jerk = c->j1;
+  A.part = c->part;
+  A.err = c->err;
+  A.ctl = c->scal;
+  A.lo = b.lo;
+  A.hi = b.hi;
+  return A;
+}
+
+// Queue kGraphSteps device-resident block steps on stream s with the
+// general scheduler (any state); *launches counts the kernels.
+nb_status queue_device_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
+  Bucket b[3];
+  const int nbk = step_buckets(c, b);
+  const int prec = c->cfg.precision;
   for (int step = 0; step < kGraphSteps; ++step) {
     int nl = 0;
     NB_CUDA(launch_next_block(c->n, c->t_tick, c->lev, c->act, c->blk, c->scal, s, &nl));
     NB_CUDA(launch_predict(c->n, 0, c->x, c->v, c->a, c->jk, c->m, c->t_tick, prec, c->jhi,
                            c->jlo, c->jvel, s, c->scal));
-    if (c->jrel)
+    ++nl;
+    if (c->jrel) {
       NB_CUDA(launch_tile_info(c->n, c->n_jt, c->jhi, c->jlo, c->jrel, c->tinfo, s, c->scal));
+      ++nl;
+    }
     for (int k = 0; k < nbk; ++k) {
-      if (b[k].lo > c->n) continue;
-      ForceArgs A;
-      A.jhi = c->jhi;
-      A.jlo = c->jlo;
-      A.jvel = c->jvel;
-      A.jrel = c->jrel;
-      A.tinfo = c->tinfo;
-      A.n_jt = c->n_jt;
-      A.idx = c->act;
-      A.n_i = 0;
-      A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
-      A.G = c->cfg.G;
-      A.acc = c->a1;
-      A.jerk = c->j1;
-      A.part = c->part;
-      A.err = c->err;
-      A.ctl = c->scal;
-      A.lo = b[k].lo;
-      A.hi = b[k].hi;
       const int grid = c->num_sms * ctas_per_sm(b[k].v);
-      NB_CUDA(launch_force_dev(b[k].v, A, grid, c->n, s, &nl));
+      NB_CUDA(launch_force_dev(b[k].v, device_force_args(c, b[k]), grid, c->n, s, &nl));
     }
     NB_CUDA(launch_correct(c->n, c->act, 0, c->x, c->v, c->a, c->jk, c->t_tick, c->lev, c->a1,
                            c->j1, c->cfg.eta, c->cfg.lev_min, c->cfg.lev_max,
                            c->cfg.block_steps, c->clamped, s, c->scal));
+    ++nl;
+    *launches += nl;
   }
+  return NB_OK;
+}
+
+// The fused form for a level-structured schedule: block_begin (scheduling
+// from the per-level counts + predictor + tile frames), the force launch of
+// every active-count bucket (the ones outside their range return at once),
+// block_end (fix-up + corrector).
+nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
+  Bucket b[3];
+  const int nbk = step_buckets(c, b);
+  BeginArgs B;
+  B.n = c->n;
+  B.n_jt = c->n_jt;
+  B.x = c->x;
+  B.v = c->v;
+  B.a = c->a;
+  B.jk = c->jk;
+  B.m = c->m;
+  B.t_tick = c->t_tick;
+  B.lev = c->lev;
+  B.prec = c->cfg.precision;
+  B.jhi = c->jhi;
+  B.jlo = c->jlo;
+  B.jvel = c->jvel;
+  B.jrel = c->jrel;
+  B.tinfo = c->tinfo;
+  B.act = c->act;
+  B.ctl = c->scal;
+  B.status = c->lb_status;
+  EndArgs E;
+  E.n = c->n;
+  E.n_jt = c->n_jt;
+  E.nbk = nbk;
+  for (int k = 0; k < nbk; ++k) {
+    E.lo[k] = b[k].lo;
+    E.hi[k] = b[k].hi;
+    E.bi[k] = block_i(variant_at(b[k].v));
+    E.pmax[k] = c->num_sms * ctas_per_sm(b[k].v);
+  }
+  E.part = c->part;
+  E.G = c->cfg.G;
+  E.a1 = c->a1;
+  E.j1 = c->j1;
+  E.act = c->act;
+  E.x = c->x;
+  E.v = c->v;
+  E.a = c->a;
+  E.jk = c->jk;
+  E.t_tick = c->t_tick;
+  E.lev = c->lev;
+  E.eta = c->cfg.eta;
+  E.lev_min = c->cfg.lev_min;
+  E.lev_max = c->cfg.lev_max;
+  E.block_steps = c->cfg.block_steps;
+  E.n_clamped = c->clamped;
+  E.ctl = c->scal;
+  const int end_grid = c->num_sms * 2;
+  for (int step = 0; step < kGraphSteps; ++step) {
+    int nl = 0;
+    NB_CUDA(launch_block_begin(B, s));
+    for (int k = 0; k < nbk; ++k)
+      NB_CUDA(launch_force_dev(b[k].v, device_force_args(c, b[k]), E.pmax[k], c->n, s, &nl,
+                               false));
+    NB_CUDA(launch_block_end(E, end_grid, s));
+    *launches += 2 + nl;
+  }
+  return NB_OK;
+}
+
+// Capture kGraphSteps block steps into an executable graph (on a private
+// stream; the occupancy cache and shared-memory attributes are warm).
+nb_status capture_blocks(nb_ctx *c, bool fused, cudaGraphExec_t *out, int64_t *launches) {
+  cudaStream_t cs;
+  NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  *launches = 0;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  nb_status qs = NB_ERR_CUDA;
+  if (e == cudaSuccess)
+    qs = fused ? queue_fused_blocks(c, cs, launches) : queue_device_blocks(c, cs, launches);
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || e2 != cudaSuccess || qs != NB_OK)
+    return fail(NB_ERR_CUDA, "capture of the block-step graph failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess)
+    return fail(NB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
   return NB_OK;
 }
 
@@ -726,41 +847,40 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
   }
   s = ensure_part(c, pb);
   if (s != NB_OK) return s;
+  if (c->block_mode == 0) {
+    // per-level counts and the level-structure check for the fused steps
+    NB_CUDA(cudaMemsetAsync(c->scal + kCtlTicket, 0,
+                            (kCtlLevCnt + kTicksLog2 + 1 - kCtlTicket) * sizeof(int64_t),
+                            c->stream));
+    int nl = 0;
+    NB_CUDA(launch_schedule_check(c->n, c->t_tick, c->lev, c->scal, c->stream, &nl));
+    c->launches += nl;
+  }
   s = sync_ctx(c);
   if (s != NB_OK) return s;
+  const bool fused = c->block_mode == 0 && c->h_scal[kCtlBad] == 0;
   const int64_t b0 = c->h_scal[kCtlBlocks];
   const int64_t i0 = c->h_scal[kCtlInter];
   c->h_scal[kCtlSlots + 0] = tend;
   c->h_scal[kCtlSlots + 1] = max_blocks > 0 ? b0 + max_blocks : INT64_MAX;
   NB_CUDA(cudaMemcpyAsync(c->scal + kCtlTend, c->h_scal + kCtlSlots, 2 * sizeof(int64_t),
                           cudaMemcpyHostToDevice, c->stream));
-  if (!c->blk_graph || c->blk_graph_part != c->part) {
-    if (c->blk_graph) {
-      cudaGraphExecDestroy(c->blk_graph);
-      c->blk_graph = nullptr;
+  cudaGraphExec_t &graph = fused ? c->fus_graph : c->blk_graph;
+  double *&graph_part = fused ? c->fus_graph_part : c->blk_graph_part;
+  int64_t &per_replay = fused ? c->fus_graph_launches : c->graph_launches;
+  if (!graph || graph_part != c->part) {
+    if (graph) {
+      cudaGraphExecDestroy(graph);
+      graph = nullptr;
     }
-    // warm the occupancy cache and the shared-memory attributes before the
-    // capture, then capture on a private stream
-    cudaStream_t cs;
-    NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    nb_status qs = e == cudaSuccess ? queue_device_blocks(c, cs) : NB_ERR_CUDA;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess || e2 != cudaSuccess || qs != NB_OK)
-      return fail(NB_ERR_CUDA, "capture of the block-step graph failed: %s",
-                  cudaGetErrorString(e != cudaSuccess ? e : e2));
-    e = cudaGraphInstantiate(&c->blk_graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess)
-      return fail(NB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
-    c->blk_graph_part = c->part;
+    s = capture_blocks(c, fused, &graph, &per_replay);
+    if (s != NB_OK) return s;
+    graph_part = c->part;
   }
   int64_t last_blocks = b0;
   for (;;) {
-    NB_CUDA(cudaGraphLaunch(c->blk_graph, c->stream));
-    c->launches += kGraphSteps * 9;
+    NB_CUDA(cudaGraphLaunch(graph, c->stream));
+    c->launches += per_replay;
     s = sync_ctx(c);
     if (s != NB_OK) return s;
     const int64_t nb = c->h_scal[kCtlBlocks];
@@ -779,8 +899,26 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
   c->have_block = false;
   c->force_done = false;
   c->t_pred = -1;
+  c->last_fused = fused ? 1 : 0;
   if (blocks_done) *blocks_done = done;
   if (t_last) *t_last = std::ldexp(static_cast<double>(c->h_scal[kCtlLastT]), -kTicksLog2);
+  return NB_OK;
+}
+
+extern "C" nb_status nb_set_block_mode(nb_ctx *c, int32_t mode) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (mode != NB_BLOCKS_AUTO && mode != NB_BLOCKS_GENERAL)
+    return fail(NB_ERR_INVALID_ARG, "unknown block-step mode %d", mode);
+  c->block_mode = mode;
+  return NB_OK;
+}
+
+extern "C" nb_status nb_last_block_path(nb_ctx *c, int32_t *fused) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (!fused) return fail(NB_ERR_INVALID_ARG, "null output pointer");
+  *fused = c->last_fused;
   return NB_OK;
 }
 

@@ -1,0 +1,402 @@
+// Fused device-resident block steps: one block step of the Hermite-4
+// integrator with individual power-of-two steps (paper Sec. 2, strategy
+// (ii); predictor / corrector after Makino & Aarseth 1992) in three kinds of
+// launch instead of a dozen:
+//
+//   block_begin  scheduling (next block time, ordered active list) and the
+//                FP64 predictor of every particle, with the j-tile frames;
+//   force        the force + jerk kernels of nb_force.cu (unchanged);
+//   block_end    the fix-up of split i-blocks and the FP64 corrector.
+//
+// Scheduling without a pass over the particles.  The integrator keeps every
+// particle's time t_i a multiple of its step dt_i = 2^-lev_i and its next
+// time t_i + dt_i after the current block time t (a step shrinks freely and
+// grows only when t is a multiple of the doubled step).  Then t_i + dt_i is
+// the first multiple of dt_i after t, so the next block time is the first
+// multiple of the smallest occupied step after t, and a particle is due
+// exactly when its step divides that time: the active set is every particle
+// whose level is at least a threshold given by the trailing zeros of t_next.
+// The per-level counts live in the control slots, kept up to date by the
+// corrector; a check kernel rebuilds them, and verifies the property, before
+// device-resident steps start (a state set by the caller that lacks it runs
+// the general scheduler instead).
+//
+// The ordered compaction is a single pass: CTAs take tickets in the order
+// they start, publish their tile's active count, and read the counts before
+// them with a decoupled look-back (bounded waits; a CTA only waits on CTAs
+// that started earlier, so every wait ends).
+#include "nb_device.cuh"
+
+namespace nbi {
+
+namespace {
+
+using dev::kTick;
+
+// Look-back word: epoch (24 bits) | flag (2 bits) | value (38 bits).
+constexpr int kValBits = 38;
+constexpr uint64_t kValMask = (uint64_t(1) << kValBits) - 1;
+constexpr uint64_t kFlagAgg = 1;  // value = this tile's active count
+constexpr uint64_t kFlagPre = 2;  // value = active count of tiles 0..this one
+constexpr int64_t kEpochMod = (int64_t(1) << 24) - 1;
+
+__device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t lb_word(uint64_t epoch, uint64_t flag, uint64_t val) {
+  return (epoch << 40) | (flag << kValBits) | (val & kValMask);
+}
+
+// Exclusive prefix of the active counts of the tiles before `vid`: one warp
+// reads 32 predecessors' words at a time (waiting, bounded, until all 32
+// are published in this epoch), adds them up to the nearest inclusive
+// prefix and stops there, or moves 32 tiles further back.  Returns false if
+// a wait ran out.  Warp-uniform.
+__device__ __forceinline__ bool look_back(const unsigned long long *status, int64_t vid,
+                                          uint64_t epoch, int lane, int64_t *excl_out) {
+  int64_t excl = 0;
+  for (int64_t top = vid - 1; top >= 0; top -= 32) {
+    const int64_t j = top - lane;
+    uint64_t w = 0;
+    uint32_t it = 0;
+    for (;; ++it) {
+      if (j >= 0) w = ld_relaxed(status + j);
+      const bool ready = j < 0 || (w >> 40) == epoch;
+      if (__all_sync(0xffffffffu, ready)) break;
+      if (it >= kWaitLimit) return false;
+    }
+    const bool pre = j >= 0 && ((w >> kValBits) & 3) == kFlagPre;
+    const unsigned pm = __ballot_sync(0xffffffffu, pre);
+    const int last = pm ? __ffs(pm) - 1 : 31;  // nearest inclusive prefix
+    int64_t val = (j >= 0 && lane <= last) ? static_cast<int64_t>(w & kValMask) : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
+    excl += val;
+    if (pm) break;
+  }
+  *excl_out = excl;
+  return true;
+}
+
+__global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) {
+  __shared__ unsigned s_vid;
+  __shared__ int s_lmax;
+  __shared__ int64_t s_ctl[4];  // t_cur, blocks, max blocks, t_end
+  __shared__ int s_wcnt[kJT / 32];
+  __shared__ int64_t s_excl;
+  __shared__ int s_agg, s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int64_t *ctl = B.ctl;
+  // Control values that no CTA of this launch writes, so that every CTA
+  // takes the same decision; the per-level counts are read a lane each.
+  if (wid == 0) {
+    const int64_t c = lane <= kTicksLog2 ? ctl[kCtlLevCnt + lane] : 0;
+    const unsigned occ = __ballot_sync(0xffffffffu, c > 0);
+    if (lane == 0) {
+      s_lmax = occ ? 31 - __clz(occ) : -1;
+      s_vid = static_cast<unsigned>(
+          atomicAdd(reinterpret_cast<unsigned long long *>(ctl + kCtlTicket), 1ull) %
+          gridDim.x);
+      s_ctl[0] = ctl[kCtlLastT];
+      s_ctl[1] = ctl[kCtlBlocks];
+      s_ctl[2] = ctl[kCtlMaxBlk];
+      s_ctl[3] = ctl[kCtlTend];
+    }
+  }
+  __syncthreads();
+  const int lmax = s_lmax;
+  const int64_t blocks = s_ctl[1];
+  int64_t t_next = -1;
+  bool stop = lmax < 0 || blocks >= s_ctl[2];
+  if (!stop) {
+    const int64_t step = int64_t(1) << (kTicksLog2 - lmax);
+    t_next = (s_ctl[0] / step + 1) * step;
+    stop = t_next > s_ctl[3];
+  }
+  const unsigned vid = s_vid;
+  if (stop) {
+    if (vid == 0 && tid == 0) {
+      ctl[kCtlTnext] = -1;
+      ctl[kCtlNact] = 0;
+    }
+    return;
+  }
+  // due <=> dt_i divides t_next <=> lev_i >= l_thr
+  const int tz = __ffsll(static_cast<long long>(t_next)) - 1;
+  const int l_thr = kTicksLog2 - (tz < kTicksLog2 ? tz : kTicksLog2);
+  const int64_t i = static_cast<int64_t>(vid) * kJT + tid;
+  const bool real = i < B.n;
+  const bool due = real && B.lev[i] >= l_thr;
+  const unsigned bal = __ballot_sync(0xffffffffu, due);
+  if (lane == 0) s_wcnt[wid] = __popc(bal);
+  __syncthreads();
+  const uint64_t epoch = static_cast<uint64_t>(blocks % kEpochMod) + 1;
+  if (wid == 0) {
+    // publish this tile's count, then look back while the other warps
+    // start on the predictor
+    int agg = 0;
+    for (int w = 0; w < kJT / 32; ++w) agg += s_wcnt[w];
+    if (lane == 0)
+      st_relaxed(B.status + vid,
+                 lb_word(epoch, vid == 0 ? kFlagPre : kFlagAgg, static_cast<uint64_t>(agg)));
+    int64_t excl = 0;
+    const bool ok = look_back(B.status, vid, epoch, lane, &excl);
+    if (lane == 0) {
+      if (!ok)
+        atomicOr(reinterpret_cast<int *>(ctl + kCtlErr), kErrScanTimeout);
+      else if (vid > 0)
+        st_relaxed(B.status + vid,
+                   lb_word(epoch, kFlagPre, static_cast<uint64_t>(excl + agg)));
+      s_excl = excl;
+      s_agg = agg;
+      s_fail = ok ? 0 : 1;
+    }
+  }
+
+  // FP64 predictor of this tile's particles
+  float4 h = make_float4(0.f, 0.f, 0.f, 0.f), lo = h;
+  if (real) {
+    const double dt = static_cast<double>(t_next - B.t_tick[i]) * kTick;
+    double xp[3], vp[3];
+    dev::predict_pos_vel(B.x, B.v, B.a, B.jk, i, dt, xp, vp);
+    h = dev::store_records(i, xp, vp, B.m[i], B.prec, B.jhi, B.jlo, B.jvel, &lo);
+  }
+  if (B.jrel)
+    dev::tile_frame(vid, i, real, h, lo, B.jrel, B.tinfo);  // synchronises the CTA
+  else
+    __syncthreads();
+  if (!s_fail && due) {
+    int base = 0;
+    for (int w = 0; w < wid; ++w) base += s_wcnt[w];
+    const int64_t pos = s_excl + base + __popc(bal & ((1u << lane) - 1u));
+    if (pos < B.n) B.act[pos] = static_cast<int32_t>(i);
+  }
+  if (tid == 0) {
+    if (vid == gridDim.x - 1) ctl[kCtlNact] = s_fail ? 0 : s_excl + s_agg;
+    if (vid == 0) ctl[kCtlTnext] = t_next;
+  }
+}
+
+// Sum of the split partial segments of NQ entries of one warp at once
+// (entry e of ib[e], kk[e], held by CTAs plo[e]..phi[e]; use[e] false
+// skips it), with the per-entry order of dev::fixup_warp: lanes stride over
+// the CTAs in ascending order, then the same butterfly.  Warp-uniform.
+template <int NQ>
+__device__ __forceinline__ void fixup_warp_n(const double *__restrict__ part,
+                                             const uint64_t *ib, const int *kk,
+                                             const int *plo, const int *phi, const bool *use,
+                                             uint64_t U, int P, uint64_t n_jt, int BI,
+                                             int lane, double s[][6]) {
+  int span = 0;
+#pragma unroll
+  for (int e = 0; e < NQ; ++e) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[e][c] = 0.0;
+    if (use[e] && phi[e] - plo[e] + 1 > span) span = phi[e] - plo[e] + 1;
+  }
+  for (int o = lane; o < span; o += 32) {
+#pragma unroll
+    for (int e = 0; e < NQ; ++e) {
+      const int p = plo[e] + o;
+      if (use[e] && p <= phi[e]) {
+        const uint64_t u0p = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
+        const int slot = (u0p / n_jt == ib[e]) ? 0 : 1;
+        const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s[e][c] += src[static_cast<size_t>(c) * BI + kk[e]];
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int e = 0; e < NQ; ++e)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) s[e][c] += __shfl_xor_sync(0xffffffffu, s[e][c], off);
+}
+
+constexpr int kEndWarps = kEndThreads / 32;
+
+// One round of block_end over the entries k0 .. k0 + NQ * kEndWarps - 1:
+// the warps gather the new force of NQ entries each (the fix-up sum of a
+// split i-block, or the value its only CTA wrote), then warp 0 corrects
+// the round's entries, a lane each.
+template <int NQ>
+__device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t n_act,
+                                          int64_t t_next, int BI, uint64_t U, int P,
+                                          double (*s_f)[6]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint64_t n_jt = static_cast<uint64_t>(E.n_jt);
+  uint64_t ib[NQ];
+  int kk[NQ], plo[NQ], phi[NQ];
+  bool valid[NQ], split[NQ];
+#pragma unroll
+  for (int e = 0; e < NQ; ++e) {
+    const int64_t k = k0 + wid + kEndWarps * e;
+    valid[e] = k < n_act;
+    const uint64_t kc = valid[e] ? static_cast<uint64_t>(k) : 0;
+    ib[e] = kc / BI;
+    kk[e] = static_cast<int>(kc % BI);
+    plo[e] = dev::owner_of(ib[e] * n_jt, U, P);
+    phi[e] = dev::owner_of((ib[e] + 1) * n_jt - 1, U, P);
+    split[e] = valid[e] && plo[e] != phi[e];
+  }
+  double s[NQ][6];
+  fixup_warp_n<NQ>(E.part, ib, kk, plo, phi, split, U, P, n_jt, BI, lane, s);
+  if (lane == 0) {
+#pragma unroll
+    for (int e = 0; e < NQ; ++e) {
+      if (!valid[e]) continue;
+      const int64_t k = k0 + wid + kEndWarps * e;
+      double *f = s_f[wid + kEndWarps * e];
+      if (split[e]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          f[c] = E.G * s[e][c];
+          f[3 + c] = E.G * s[e][3 + c];
+          E.a1[3 * k + c] = f[c];
+          E.j1[3 * k + c] = f[3 + c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          f[c] = E.a1[3 * k + c];
+          f[3 + c] = E.j1[3 * k + c];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (wid == 0 && lane < NQ * kEndWarps && k0 + lane < n_act) {
+    const double *f = s_f[lane];
+    dev::correct_vals(E.act[k0 + lane], f, f + 3, t_next, E.x, E.v, E.a, E.jk, E.t_tick,
+                      E.lev, E.eta, E.lev_min, E.lev_max, E.block_steps, E.n_clamped,
+                      E.ctl + kCtlLevCnt);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kEndThreads) block_end_kernel(const EndArgs E) {
+  __shared__ double s_f[4 * kEndWarps][6];
+  const int64_t t_next = E.ctl[kCtlTnext];
+  if (t_next < 0) return;
+  const int64_t n_act = E.ctl[kCtlNact];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    E.ctl[kCtlBlocks] += 1;
+    E.ctl[kCtlLastT] = t_next;
+    E.ctl[kCtlInter] += n_act * E.n;
+  }
+  int b = -1;
+  for (int q = 0; q < E.nbk; ++q)
+    if (n_act >= E.lo[q] && n_act < E.hi[q]) b = q;
+  if (b < 0) return;
+  // the split the force launch of this bucket derived from the same count
+  const int BI = E.bi[b];
+  const uint64_t U = static_cast<uint64_t>((n_act + BI - 1) / BI) * static_cast<uint64_t>(E.n_jt);
+  const uint64_t pm = (U + kMinUnits - 1) / kMinUnits;
+  const int P = static_cast<int>(pm < static_cast<uint64_t>(E.pmax[b]) ? pm : E.pmax[b]);
+  // short lists: one entry per warp per round (the fix-ups in parallel);
+  // long lists: four, so that the corrector warp runs 32 lanes
+  if (n_act <= static_cast<int64_t>(kEndWarps) * gridDim.x) {
+    for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * kEndWarps; k0 < n_act;
+         k0 += static_cast<int64_t>(gridDim.x) * kEndWarps)
+      end_round<1>(E, k0, n_act, t_next, BI, U, P, s_f);
+  } else {
+    for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * 4 * kEndWarps; k0 < n_act;
+         k0 += static_cast<int64_t>(gridDim.x) * 4 * kEndWarps)
+      end_round<4>(E, k0, n_act, t_next, BI, U, P, s_f);
+  }
+}
+
+// ---- check of the level structure ----------------------------------------
+
+constexpr int kChkThreads = 256;
+
+__global__ void __launch_bounds__(kChkThreads)
+    sched_levels_kernel(int64_t n, const int64_t *__restrict__ t_tick,
+                        const int32_t *__restrict__ lev, int64_t *ctl) {
+  __shared__ int cnt[kTicksLog2 + 1];
+  __shared__ unsigned long long tmax_w[kChkThreads / 32];
+  if (threadIdx.x <= kTicksLog2) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long tmax = 0;
+  int bad = 0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int l = lev[i];
+    const int64_t t = t_tick[i];
+    if (l < 0 || l > kTicksLog2 || t < 0) {
+      bad = 1;
+      continue;
+    }
+    if (t % (int64_t(1) << (kTicksLog2 - l)) != 0) bad = 1;
+    atomicAdd(&cnt[l], 1);
+    const unsigned long long tu = static_cast<unsigned long long>(t);
+    tmax = tu > tmax ? tu : tmax;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, tmax, off);
+    tmax = o > tmax ? o : tmax;
+  }
+  if ((threadIdx.x & 31) == 0) tmax_w[threadIdx.x >> 5] = tmax;
+  if (__syncthreads_or(bad) && threadIdx.x == 0)
+    atomicOr(reinterpret_cast<unsigned long long *>(ctl + kCtlBad), 1ull);
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kChkThreads / 32; ++w) tmax = tmax_w[w] > tmax ? tmax_w[w] : tmax;
+    atomicMax(reinterpret_cast<unsigned long long *>(ctl + kCtlTcur), tmax);
+  }
+  if (threadIdx.x <= kTicksLog2 && cnt[threadIdx.x] > 0)
+    atomicAdd(reinterpret_cast<unsigned long long *>(ctl + kCtlLevCnt + threadIdx.x),
+              static_cast<unsigned long long>(cnt[threadIdx.x]));
+}
+
+// Every particle's next time must lie after the latest particle time.
+__global__ void __launch_bounds__(kChkThreads)
+    sched_due_kernel(int64_t n, const int64_t *__restrict__ t_tick,
+                     const int32_t *__restrict__ lev, int64_t *ctl) {
+  const int64_t t_cur = ctl[kCtlTcur];
+  int bad = 0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int l = lev[i];
+    if (l < 0 || l > kTicksLog2) continue;  // flagged by the level pass
+    if (t_tick[i] + (int64_t(1) << (kTicksLog2 - l)) <= t_cur) bad = 1;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0)
+    atomicOr(reinterpret_cast<unsigned long long *>(ctl + kCtlBad), 2ull);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlLastT] = t_cur;
+}
+
+}  // namespace
+
+cudaError_t launch_schedule_check(int64_t n, const int64_t *t_tick, const int32_t *lev,
+                                  int64_t *ctl, cudaStream_t s, int *launches) {
+  int64_t nb = (n + kChkThreads - 1) / kChkThreads;
+  if (nb > 1024) nb = 1024;
+  sched_levels_kernel<<<static_cast<unsigned>(nb), kChkThreads, 0, s>>>(n, t_tick, lev, ctl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sched_due_kernel<<<static_cast<unsigned>(nb), kChkThreads, 0, s>>>(n, t_tick, lev, ctl);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_begin(const BeginArgs &B, cudaStream_t s) {
+  block_begin_kernel<<<static_cast<unsigned>(B.n_jt), kJT, 0, s>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_end(const EndArgs &E, int grid, cudaStream_t s) {
+  block_end_kernel<<<static_cast<unsigned>(grid), kEndThreads, 0, s>>>(E);
+  return cudaGetLastError();
+}
+
+}  // namespace nbi

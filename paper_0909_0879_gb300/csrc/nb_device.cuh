@@ -1,0 +1,252 @@
+// Device functions shared by the host-driven kernels (one kernel per
+// operation) and the fused device-resident block-step kernels, so that both
+// paths perform the same arithmetic in the same order and give the same bits.
+//
+// Predictor / corrector after Makino & Aarseth (1992); time-step criterion
+// Aarseth (1985), cited in the paper's Sec. 2; block (individual) time steps,
+// paper Sec. 2, strategy (ii).  Not part of the public C ABI.
+#pragma once
+
+#include "nb_internal.cuh"
+
+namespace nbi {
+namespace dev {
+
+constexpr double kTick = 1.0 / static_cast<double>(1 << kTicksLog2);
+
+// Taylor predictor to dt: x + dt (v + dt/2 (a + dt/3 j)),  v + dt (a + dt/2 j).
+__device__ __forceinline__ void predict_pos_vel(const double *x, const double *v,
+                                                const double *a, const double *jk,
+                                                int64_t i, double dt, double xp[3],
+                                                double vp[3]) {
+  const double h2 = 0.5 * dt, h3 = dt * (1.0 / 3.0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double xc = x[3 * i + c], vc = v[3 * i + c];
+    const double ac = a[3 * i + c], jc = jk[3 * i + c];
+    xp[c] = xc + dt * (vc + h2 * (ac + h3 * jc));
+    vp[c] = vc + dt * (ac + h2 * jc);
+  }
+}
+
+// j-records of particle i at the predicted (xp, vp): FP32 position (the
+// high word in DS) + mass, DS low words, FP32 velocity.  Returns the first
+// and the low words through *lo (zero in FP32).
+__device__ __forceinline__ float4 store_records(int64_t i, const double xp[3],
+                                                const double vp[3], double m, int prec,
+                                                float4 *__restrict__ jhi,
+                                                float4 *__restrict__ jlo,
+                                                float4 *__restrict__ jvel, float4 *lo) {
+  const float hx = __double2float_rn(xp[0]);
+  const float hy = __double2float_rn(xp[1]);
+  const float hz = __double2float_rn(xp[2]);
+  const float4 h = make_float4(hx, hy, hz, __double2float_rn(m));
+  jhi[i] = h;
+  float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (prec) {
+    l = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
+                    __double2float_rn(xp[1] - static_cast<double>(hy)),
+                    __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
+    jlo[i] = l;
+  }
+  jvel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
+                        __double2float_rn(vp[2]), 0.f);
+  *lo = l;
+  return h;
+}
+
+// Frame of one tile of kJT records (called by all kJT threads of a CTA,
+// thread t holding record j = tile * kJT + t): the bounding box of the
+// high words, its FP32 centre O_t, half-widths and radius R_t into
+// tinfo[2 tile], tinfo[2 tile + 1], and every record's position relative
+// to O_t into jrel.  The half-widths cover the box about O_t, the low
+// words (below half an ulp of the high word) and the rounding of O_t.
+__device__ __forceinline__ void tile_frame(int64_t tile, int64_t j, bool real, float4 h,
+                                           float4 l, float4 *__restrict__ jrel,
+                                           float4 *__restrict__ tinfo) {
+  __shared__ float smn[3][kJT / 32], smx[3][kJT / 32];
+  __shared__ float4 s_o;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float mn[3], mx[3];
+  const float hv[3] = {h.x, h.y, h.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mn[c] = real ? hv[c] : 3.0e38f;
+    mx[c] = real ? hv[c] : -3.0e38f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+      mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+    }
+    if (lane == 0) {
+      smn[c][wid] = mn[c];
+      smx[c][wid] = mx[c];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float o[3], hw[3];
+    float r2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float a = smn[c][0], b = smx[c][0];
+      for (int w = 1; w < kJT / 32; ++w) {
+        a = fminf(a, smn[c][w]);
+        b = fmaxf(b, smx[c][w]);
+      }
+      o[c] = 0.5f * a + 0.5f * b;
+      const float big = fmaxf(fabsf(a), fabsf(b));
+      hw[c] = fmaxf(o[c] - a, b - o[c]) * (1.0f + 1.0e-6f) + big * 1.2e-7f;
+      r2 = fmaf(hw[c], hw[c], r2);
+    }
+    const float R = sqrtf(r2) * (1.0f + 1.0e-6f);
+    tinfo[2 * tile] = make_float4(o[0], o[1], o[2], R);
+    tinfo[2 * tile + 1] = make_float4(hw[0], hw[1], hw[2], 0.f);
+    s_o = make_float4(o[0], o[1], o[2], 0.f);
+  }
+  __syncthreads();
+  if (real) {
+    const float4 o = s_o;
+    jrel[j] = make_float4((h.x - o.x) + l.x, (h.y - o.y) + l.y, (h.z - o.z) + l.z, h.w);
+  } else {
+    jrel[j] = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
+  }
+}
+
+// CTA owning unit u of U units split over P CTAs (ranges [U p / P, U (p+1) / P)).
+__host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) {
+  return static_cast<int>(((u + 1) * static_cast<uint64_t>(P) - 1) / U);
+}
+
+// Sum of the FP64 partial segments of entry kk of split i-block ib, held by
+// CTAs plo..phi: lanes stride over the CTAs (ascending within a lane) and
+// meet by a butterfly, so every lane returns the same total, in an order
+// fixed by the split.  Called by a full warp.
+__device__ __forceinline__ void fixup_warp(const double *__restrict__ part, uint64_t ib,
+                                           int kk, int plo, int phi, uint64_t U, int P,
+                                           uint64_t n_jt, int BI, int lane, double s[6]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[c] = 0.0;
+  for (int p = plo + lane; p <= phi; p += 32) {
+    const uint64_t u0p = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
+    const int slot = (u0p / n_jt == ib) ? 0 : 1;
+    const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] += src[static_cast<size_t>(c) * BI + kk];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+}
+
+__device__ __forceinline__ double norm3(const double u[3]) {
+  return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+// Largest power of two 2^-lev <= dt (frexp is exact), clamped.
+__device__ __forceinline__ int level_from_dt(double dt, int lev_min, int lev_max,
+                                             int *clamped) {
+  if (!(dt > 0.0)) {
+    *clamped = 1;
+    return lev_max;
+  }
+  if (isinf(dt)) return lev_min;
+  int e;
+  frexp(dt, &e);
+  int lev = 1 - e;
+  if (lev > lev_max) {
+    *clamped = 1;
+    lev = lev_max;
+  }
+  if (lev < lev_min) lev = lev_min;
+  return lev;
+}
+
+// 2^k as a double, for |k| <= 1000, from its exponent bits (exact).
+__device__ __forceinline__ double pow2(int k) {
+  return __longlong_as_double(static_cast<long long>(1023 + k) << 52);
+}
+
+// Hermite corrector, step criterion and new level of particle i with its
+// new force an, jn at t_next.  With lev_cnt set, a change of level moves
+// the particle between the per-level counts.
+__device__ __forceinline__ void correct_vals(
+    int64_t i, const double an3[3], const double jn3[3], int64_t t_next,
+    double *__restrict__ x, double *__restrict__ v, double *__restrict__ a,
+    double *__restrict__ jk, int64_t *__restrict__ t_tick, int32_t *__restrict__ lev,
+    double eta, int lev_min, int lev_max, int block_steps, unsigned long long *n_clamped,
+    int64_t *lev_cnt) {
+  const int64_t dtk = t_next - t_tick[i];
+  const double dt = static_cast<double>(dtk) * kTick;
+  double xp[3], vp[3];
+  predict_pos_vel(x, v, a, jk, i, dt, xp, vp);
+  const double dt2 = dt * dt, dt3 = dt2 * dt;
+  // A due particle's step is a power of two of ticks, so 1/dt^2 and 1/dt^3
+  // are powers of two, built exactly from the exponent (no division), and
+  // the products below equal the quotients bit for bit.
+  double idt2, idt3;
+  if (dtk > 0 && (dtk & (dtk - 1)) == 0) {
+    const int e = (63 - __clzll(dtk)) - kTicksLog2;  // dt = 2^e
+    idt2 = pow2(-2 * e);
+    idt3 = pow2(-3 * e);
+  } else {
+    idt2 = 1.0 / dt2;
+    idt3 = 1.0 / dt3;
+  }
+  double a2e[3], a3e[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double a0 = a[3 * i + c], j0 = jk[3 * i + c];
+    const double an = an3[c], jn = jn3[c];
+    const double da = a0 - an;
+    // second and third derivatives of a at the start of the step
+    const double snap = (-6.0 * da - dt * (4.0 * j0 + 2.0 * jn)) * idt2;
+    const double crackle = (12.0 * da + 6.0 * dt * (j0 + jn)) * idt3;
+    x[3 * i + c] = xp[c] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
+    v[3 * i + c] = vp[c] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
+    a[3 * i + c] = an;
+    jk[3 * i + c] = jn;
+    a2e[c] = snap + crackle * dt;
+    a3e[c] = crackle;
+  }
+  t_tick[i] = t_next;
+  if (block_steps) {
+    const double na = norm3(an3), nj = norm3(jn3), n2 = norm3(a2e), n3 = norm3(a3e);
+    const double dtc = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+    int cl = 0;
+    const int want = level_from_dt(dtc, lev_min, lev_max, &cl);
+    if (cl) atomicAdd(n_clamped, 1ull);
+    const int old = lev[i];
+    int nl = old;
+    if (want >= old) {
+      nl = want;
+    } else if (old - 1 >= lev_min) {
+      const int64_t period = static_cast<int64_t>(1) << (kTicksLog2 - (old - 1));
+      if (t_next % period == 0) nl = old - 1;
+    }
+    lev[i] = nl;
+    if (lev_cnt && nl != old) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(lev_cnt + old),
+                static_cast<unsigned long long>(-1ll));
+      atomicAdd(reinterpret_cast<unsigned long long *>(lev_cnt + nl), 1ull);
+    }
+  }
+}
+
+// The corrector of active entry k (particle act[k]) with its new force in
+// a1, j1 (entry-indexed).
+__device__ __forceinline__ void correct_one(
+    int64_t k, const int32_t *__restrict__ act, int64_t t_next, double *__restrict__ x,
+    double *__restrict__ v, double *__restrict__ a, double *__restrict__ jk,
+    int64_t *__restrict__ t_tick, int32_t *__restrict__ lev, const double *__restrict__ a1,
+    const double *__restrict__ j1, double eta, int lev_min, int lev_max, int block_steps,
+    unsigned long long *n_clamped, int64_t *lev_cnt) {
+  const double an[3] = {a1[3 * k], a1[3 * k + 1], a1[3 * k + 2]};
+  const double jn[3] = {j1[3 * k], j1[3 * k + 1], j1[3 * k + 2]};
+  correct_vals(act[k], an, jn, t_next, x, v, a, jk, t_tick, lev, eta, lev_min, lev_max,
+               block_steps, n_clamped, lev_cnt);
+}
+
+}  // namespace dev
+}  // namespace nbi

@@ -31,7 +31,7 @@
 //  * Several threads per i-particle (TPI > 1) split a tile's j-range inside
 //    the CTA for short active lists; their sums meet by a warp-shuffle
 //    butterfly (commutative pairwise adds, identical on every lane).
-#include "nb_internal.cuh"
+#include "nb_device.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -184,10 +184,7 @@ struct DsAcc<IPT, NT, true> {
   __device__ __forceinline__ float &JL(int q, int c) { return b[(12 * q + 9 + c) * NT]; }
 };
 
-// CTA owning unit u of U units split over P CTAs (ranges [U p / P, U (p+1) / P)).
-__host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) {
-  return static_cast<int>(((u + 1) * static_cast<uint64_t>(P) - 1) / U);
-}
+using dev::owner_of;
 
 template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK, int SACC, int REL>
 __global__ void __launch_bounds__(NT, 1)
@@ -530,18 +527,8 @@ __global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
   const int plo = owner_of(ib * n_jt, U, P);
   const int phi = owner_of((ib + 1) * n_jt - 1, U, P);
   if (plo == phi) return;  // written directly by its only CTA
-  double s[6] = {0, 0, 0, 0, 0, 0};
-  for (int p = plo + lane; p <= phi; p += 32) {
-    const uint64_t u0p = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
-    const int slot = (u0p / n_jt == ib) ? 0 : 1;
-    const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] += src[static_cast<size_t>(c) * BI + kk];
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+  double s[6];
+  dev::fixup_warp(part, ib, kk, plo, phi, U, P, n_jt, BI, lane, s);
   if (lane == 0) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -668,12 +655,16 @@ int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap) {
 }
 
 cudaError_t launch_force_dev(int v, const ForceArgs &A, int grid, int64_t n_max,
-                             cudaStream_t s, int *launches) {
+                             cudaStream_t s, int *launches, bool with_fixup) {
   const Entry &E = kTable[v];
   const int BI = block_i(E.V);
   E.fn<<<grid, E.V.threads, smem_bytes(E.V), s>>>(A, 0, grid);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (!with_fixup) {
+    if (launches) *launches += 1;
+    return cudaSuccess;
+  }
   const int64_t cap = A.hi < n_max ? A.hi : n_max;
   const int64_t nb = (cap + 7) / 8;
   force_fixup_kernel<<<static_cast<unsigned>(nb > 0 ? nb : 1), 256, 0, s>>>(

@@ -8,7 +8,7 @@
 // criterion Aarseth (1985), cited in the paper's Sec. 2; individual (block)
 // time steps, paper Sec. 2, strategy (ii).  None of these formulas is
 // printed in the paper; they are written out from the standard literature.
-#include "nb_internal.cuh"
+#include "nb_device.cuh"
 
 #include <cfloat>
 
@@ -16,22 +16,7 @@ namespace nbi {
 
 namespace {
 
-constexpr double kTick = 1.0 / static_cast<double>(1 << kTicksLog2);
-
-__device__ __forceinline__ void predict_pos_vel(const double *x, const double *v,
-                                                const double *a, const double *jk,
-                                                int64_t i, double dt, double xp[3],
-                                                double vp[3]) {
-  const double h2 = 0.5 * dt, h3 = dt * (1.0 / 3.0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double xc = x[3 * i + c], vc = v[3 * i + c];
-    const double ac = a[3 * i + c], jc = jk[3 * i + c];
-    // x + dt (v + dt/2 (a + dt/3 j)),  v + dt (a + dt/2 j)
-    xp[c] = xc + dt * (vc + h2 * (ac + h3 * jc));
-    vp[c] = vc + dt * (ac + h2 * jc);
-  }
-}
+using dev::kTick;
 
 __global__ void predict_kernel(int64_t n, int64_t t_next, const double *__restrict__ x,
                                const double *__restrict__ v, const double *__restrict__ a,
@@ -47,17 +32,9 @@ __global__ void predict_kernel(int64_t n, int64_t t_next, const double *__restri
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const double dt = static_cast<double>(t_next - t_tick[i]) * kTick;
     double xp[3], vp[3];
-    predict_pos_vel(x, v, a, jk, i, dt, xp, vp);
-    const float hx = __double2float_rn(xp[0]);
-    const float hy = __double2float_rn(xp[1]);
-    const float hz = __double2float_rn(xp[2]);
-    jhi[i] = make_float4(hx, hy, hz, __double2float_rn(m[i]));
-    if (prec)
-      jlo[i] = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
-                           __double2float_rn(xp[1] - static_cast<double>(hy)),
-                           __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
-    jvel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                          __double2float_rn(vp[2]), 0.f);
+    dev::predict_pos_vel(x, v, a, jk, i, dt, xp, vp);
+    float4 lo;
+    dev::store_records(i, xp, vp, m[i], prec, jhi, jlo, jvel, &lo);
   }
 }
 
@@ -78,134 +55,11 @@ __global__ void __launch_bounds__(kJT)
                      float4 *__restrict__ jrel, float4 *__restrict__ tinfo,
                      const int64_t *ctl) {
   if (ctl && ctl[kCtlTnext] < 0) return;
-  __shared__ float smn[3][kJT / 32], smx[3][kJT / 32];
-  __shared__ float4 s_o;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t j = static_cast<int64_t>(blockIdx.x) * kJT + tid;
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * kJT + threadIdx.x;
   const bool real = j < n;
   const float4 h = jhi[j];
-  float mn[3], mx[3];
-  const float hv[3] = {h.x, h.y, h.z};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    mn[c] = real ? hv[c] : 3.0e38f;
-    mx[c] = real ? hv[c] : -3.0e38f;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
-      mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
-    }
-    if (lane == 0) {
-      smn[c][wid] = mn[c];
-      smx[c][wid] = mx[c];
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    float o[3], hw[3];
-    float r2 = 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float a = smn[c][0], b = smx[c][0];
-      for (int w = 1; w < kJT / 32; ++w) {
-        a = fminf(a, smn[c][w]);
-        b = fmaxf(b, smx[c][w]);
-      }
-      o[c] = 0.5f * a + 0.5f * b;
-      // half-width covering [a, b] about o, the low words (below half an
-      // ulp of the high word) and the rounding of o
-      const float big = fmaxf(fabsf(a), fabsf(b));
-      hw[c] = fmaxf(o[c] - a, b - o[c]) * (1.0f + 1.0e-6f) + big * 1.2e-7f;
-      r2 = fmaf(hw[c], hw[c], r2);
-    }
-    const float R = sqrtf(r2) * (1.0f + 1.0e-6f);
-    tinfo[2 * blockIdx.x] = make_float4(o[0], o[1], o[2], R);
-    tinfo[2 * blockIdx.x + 1] = make_float4(hw[0], hw[1], hw[2], 0.f);
-    s_o = make_float4(o[0], o[1], o[2], 0.f);
-  }
-  __syncthreads();
-  if (real) {
-    const float4 l = jlo[j];
-    const float4 o = s_o;
-    jrel[j] = make_float4((h.x - o.x) + l.x, (h.y - o.y) + l.y, (h.z - o.z) + l.z, h.w);
-  } else {
-    jrel[j] = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
-  }
-}
-
-__device__ __forceinline__ double norm3(const double u[3]) {
-  return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-}
-
-// Largest power of two 2^-lev <= dt (frexp is exact), clamped.
-__device__ __forceinline__ int level_from_dt(double dt, int lev_min, int lev_max,
-                                             int *clamped) {
-  if (!(dt > 0.0)) {
-    *clamped = 1;
-    return lev_max;
-  }
-  if (isinf(dt)) return lev_min;
-  int e;
-  frexp(dt, &e);
-  int lev = 1 - e;
-  if (lev > lev_max) {
-    *clamped = 1;
-    lev = lev_max;
-  }
-  if (lev < lev_min) lev = lev_min;
-  return lev;
-}
-
-// Hermite corrector, step criterion and new level of active particle k.
-__device__ __forceinline__ void correct_one(
-    int64_t k, const int32_t *__restrict__ act, int64_t t_next, double *__restrict__ x,
-    double *__restrict__ v, double *__restrict__ a, double *__restrict__ jk,
-    int64_t *__restrict__ t_tick, int32_t *__restrict__ lev, const double *__restrict__ a1,
-    const double *__restrict__ j1, double eta, int lev_min, int lev_max, int block_steps,
-    unsigned long long *n_clamped) {
-  const int64_t i = act[k];
-  const double dt = static_cast<double>(t_next - t_tick[i]) * kTick;
-  double xp[3], vp[3];
-  predict_pos_vel(x, v, a, jk, i, dt, xp, vp);
-  const double dt2 = dt * dt, dt3 = dt2 * dt;
-  // every step is a power of two, so these reciprocals are exact and the
-  // products below equal the quotients bit for bit
-  const double idt2 = 1.0 / dt2, idt3 = 1.0 / dt3;
-  double a1v[3], j1v[3], a2e[3], a3e[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double a0 = a[3 * i + c], j0 = jk[3 * i + c];
-    const double an = a1[3 * k + c], jn = j1[3 * k + c];
-    const double da = a0 - an;
-    // second and third derivatives of a at the start of the step
-    const double snap = (-6.0 * da - dt * (4.0 * j0 + 2.0 * jn)) * idt2;
-    const double crackle = (12.0 * da + 6.0 * dt * (j0 + jn)) * idt3;
-    x[3 * i + c] = xp[c] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
-    v[3 * i + c] = vp[c] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
-    a[3 * i + c] = an;
-    jk[3 * i + c] = jn;
-    a1v[c] = an;
-    j1v[c] = jn;
-    a2e[c] = snap + crackle * dt;
-    a3e[c] = crackle;
-  }
-  t_tick[i] = t_next;
-  if (block_steps) {
-    const double na = norm3(a1v), nj = norm3(j1v), n2 = norm3(a2e), n3 = norm3(a3e);
-    const double dtc = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
-    int cl = 0;
-    const int want = level_from_dt(dtc, lev_min, lev_max, &cl);
-    if (cl) atomicAdd(n_clamped, 1ull);
-    const int old = lev[i];
-    int nl = old;
-    if (want >= old) {
-      nl = want;
-    } else if (old - 1 >= lev_min) {
-      const int64_t period = static_cast<int64_t>(1) << (kTicksLog2 - (old - 1));
-      if (t_next % period == 0) nl = old - 1;
-    }
-    lev[i] = nl;
-  }
+  const float4 l = real ? jlo[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  dev::tile_frame(blockIdx.x, j, real, h, l, jrel, tinfo);
 }
 
 __global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, int64_t t_next,
@@ -222,8 +76,8 @@ __global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, i
   }
   for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n_act;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    correct_one(k, act, t_next, x, v, a, jk, t_tick, lev, a1, j1, eta, lev_min, lev_max,
-                block_steps, n_clamped);
+    dev::correct_one(k, act, t_next, x, v, a, jk, t_tick, lev, a1, j1, eta, lev_min, lev_max,
+                     block_steps, n_clamped, nullptr);
 }
 
 __global__ void init_levels_kernel(int64_t n, const double *__restrict__ a,
@@ -239,9 +93,9 @@ __global__ void init_levels_kernel(int64_t n, const double *__restrict__ a,
   }
   const double av[3] = {a[3 * i], a[3 * i + 1], a[3 * i + 2]};
   const double jv[3] = {jk[3 * i], jk[3 * i + 1], jk[3 * i + 2]};
-  const double dt0 = eta_start * norm3(av) / norm3(jv);
+  const double dt0 = eta_start * dev::norm3(av) / dev::norm3(jv);
   int cl = 0;
-  lev[i] = level_from_dt(dt0, lev_min, lev_max, &cl);
+  lev[i] = dev::level_from_dt(dt0, lev_min, lev_max, &cl);
 }
 
 // ---- block scheduling -----------------------------------------------------

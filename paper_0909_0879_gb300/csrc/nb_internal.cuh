@@ -54,7 +54,14 @@ constexpr int kCtlTend = 5;     // stop when the next block would pass this tick
 constexpr int kCtlMaxBlk = 6;   // ... or when kCtlBlocks reaches this count
 constexpr int kCtlInter = 7;    // interactions evaluated on the device
 constexpr int kCtlLastT = 8;    // t of the last block taken on the device
-constexpr int kCtlSlots = 16;
+constexpr int kCtlTicket = 9;   // CTA tickets of the fused block-begin kernel
+constexpr int kCtlBad = 10;     // nonzero: the schedule is not level-structured
+constexpr int kCtlTcur = 11;    // latest particle time (ticks), from the check
+constexpr int kCtlLevCnt = 16;  // kTicksLog2 + 1 slots: particles per level
+constexpr int kCtlSlots = 40;
+
+// Device error-word bit of a timed-out look-back in the fused compaction.
+constexpr int kErrScanTimeout = 2;
 
 // Minimum j-tiles per CTA of the stream-K split (short lists are
 // latency-bound; fewer split segments keep the fix-up short).
@@ -105,8 +112,10 @@ cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
                          int *launches);
 // Device-resident form: A.ctl, A.lo, A.hi set; `grid` is the largest
 // persistent grid of the variant and n_max bounds the active count.
+// Without with_fixup the split i-blocks' partial sums are left in A.part
+// for the fused block-end kernel.
 cudaError_t launch_force_dev(int v, const ForceArgs &A, int grid, int64_t n_max,
-                             cudaStream_t s, int *launches);
+                             cudaStream_t s, int *launches, bool with_fixup = true);
 
 // --- Hermite and bookkeeping kernels (nb_hermite.cu) ---
 // With ctl set, t_next is read from ctl[kCtlTnext] (negative: no-op).
@@ -151,5 +160,49 @@ cudaError_t launch_energy(int64_t n, const double *m, const double *x,
                           const double *v, double G, double eps, double *red,
                           double *d_out, cudaStream_t s, int *launches);
 int64_t energy_scratch_doubles(int64_t n);
+
+// --- Fused device-resident block steps (nb_blockstep.cu) ---
+// Per-level counts, latest particle time and the level-structure check of
+// the schedule (every particle's next time is the first multiple of its
+// step after the latest particle time) into the control slots; the caller
+// zeroes slots kCtlTicket..kCtlLevCnt + kTicksLog2 first.
+cudaError_t launch_schedule_check(int64_t n, const int64_t *t_tick, const int32_t *lev,
+                                  int64_t *ctl, cudaStream_t s, int *launches);
+
+// Scheduling + prediction of one block step, one CTA per j-tile.
+struct BeginArgs {
+  int64_t n, n_jt;
+  const double *x, *v, *a, *jk, *m;
+  const int64_t *t_tick;
+  const int32_t *lev;
+  int prec;
+  float4 *jhi, *jlo, *jvel;
+  float4 *jrel, *tinfo;              // DS only (tile frames), else null
+  int32_t *act;
+  int64_t *ctl;
+  unsigned long long *status;        // n_jt look-back words
+};
+cudaError_t launch_block_begin(const BeginArgs &B, cudaStream_t s);
+
+// Fix-up of the split i-blocks + corrector of one block step.
+struct EndArgs {
+  int64_t n, n_jt;
+  int nbk;                           // force-shape buckets of the step
+  int64_t lo[3], hi[3];              // active-count range of each bucket
+  int bi[3], pmax[3];                // i-block size and persistent grid
+  const double *part;
+  double G;
+  double *a1, *j1;
+  const int32_t *act;
+  double *x, *v, *a, *jk;
+  int64_t *t_tick;
+  int32_t *lev;
+  double eta;
+  int lev_min, lev_max, block_steps;
+  unsigned long long *n_clamped;
+  int64_t *ctl;
+};
+cudaError_t launch_block_end(const EndArgs &E, int grid, cudaStream_t s);
+constexpr int kEndThreads = 256;
 
 }  // namespace nbi

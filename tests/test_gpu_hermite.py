@@ -295,6 +295,7 @@ def test_device_resident_blocks_match_host_loop(nb):
         sa = a.get_state()
     with nb.NBody(m, x, v, **kw) as b:
         done, t_last = b.run_blocks(t_end)
+        assert b.last_block_path() == "fused"
         sb = b.get_state()
         cnt = b.counters()
     assert done == steps and t_last == t_end and cnt["blocks"] == steps
@@ -327,3 +328,69 @@ def test_device_resident_shared_steps_and_fp32(nb):
         assert done == 40 and t_last == 40 * 2.0**-8
         for k in sa:
             assert np.array_equal(sa[k], sb[k]), (prec, k)
+
+
+def _host_loop(nb, m, x, v, kw, t_end):
+    with nb.NBody(m, x, v, **kw) as a:
+        steps = a.run_until(t_end)
+        return steps, a.get_state(), a.counters()
+
+
+@pytest.mark.parametrize("case", ["ragged_ds", "ragged_fp32", "eps0_ds", "eps0_fp32"])
+def test_fused_block_steps_match_general_and_host(nb, case):
+    """The fused device-resident steps (scheduling from per-level counts,
+    single-pass compaction, fused fix-up + corrector) take the same steps
+    with the same bits as the general scheduler and as the nb_step loop:
+    n not a multiple of the 256-record tile, both precisions, and the
+    masked eps = 0 kernels."""
+    n = 2000 + 77 if case.startswith("ragged") else 300
+    m, x, v = ics.plummer(n, 41, masses=ics.salpeter_masses(n, 41))
+    prec = case.rsplit("_", 1)[1]
+    eps = 0.0 if case.startswith("eps0") else 1e-3
+    kw = dict(eps=eps, eta=0.02, lev_min=5, lev_max=20, precision=prec)
+    t_end = 2.0**-5
+    steps, sa, ca = _host_loop(nb, m, x, v, kw, t_end)
+    for mode in ("auto", "general"):
+        with nb.NBody(m, x, v, **kw) as b:
+            b.set_block_mode(mode)
+            done, t_last = b.run_blocks(t_end)
+            assert b.last_block_path() == ("fused" if mode == "auto" else "general")
+            sb = b.get_state()
+            cb = b.counters()
+        assert done == steps and t_last == t_end, (mode, done, steps)
+        assert cb["interactions"] == ca["interactions"] and cb["clamped"] == ca["clamped"]
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), (case, mode, k)
+
+
+def test_fused_block_steps_need_a_level_structured_schedule(nb):
+    """A state whose schedule lacks the level structure (a particle due
+    before the latest particle time) runs the general scheduler; once the
+    lagging particles catch up the next call runs the fused form again, and
+    every step equals the nb_step loop's."""
+    n = 1500
+    m, x, v = ics.plummer(n, 43)
+    kw = dict(eps=1e-3, eta=0.02, lev_min=4, lev_max=20)
+    with nb.NBody(m, x, v, **kw) as a:
+        st = a.get_state()
+    # half the particles sit at t = 1/16 on level 4, the rest at t = 0 on level 6
+    t_tick = np.zeros(n, np.int64)
+    lev = np.full(n, 6, np.int32)
+    t_tick[::2] = 1 << 16
+    lev[::2] = 4
+    st["t_tick"], st["lev"] = t_tick, lev
+    t_end = 2.0**-3
+    with nb.NBody(m, x, v, **kw) as a:
+        a.set_state(st)
+        steps = a.run_until(t_end)
+        sa = a.get_state()
+    with nb.NBody(m, x, v, **kw) as b:
+        b.set_state(st)
+        d1, _ = b.run_blocks(1 / 16)  # the lagging half catches up to t = 1/16
+        assert b.last_block_path() == "general"
+        d2, t2 = b.run_blocks(t_end)
+        assert b.last_block_path() == "fused"
+        sb = b.get_state()
+    assert d1 + d2 == steps and t2 == t_end
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
