@@ -367,6 +367,9 @@ __global__ void __launch_bounds__(NT, 1)
       // of the few additions that follow it in its chunk), the jerk's once
       // per tile (its tolerance is ten times looser).
       constexpr int CH = (PREC && kFoldChunk < kJT / TPI) ? kFoldChunk : kJT / TPI;
+      // j-loop unroll: 8 for the tile-relative kernel (measured 1 % faster
+      // at N = 1M), 4 elsewhere (8 is 3 % slower for the FP32 IPT = 4 shape)
+      constexpr int UNR = REL ? 8 : 4;
       auto walk_tile = [&](auto far_tag) {
         constexpr bool FAR = decltype(far_tag)::value;
 #pragma unroll 1
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(NT, 1)
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
           for (int c = 0; c < 3; ++c) pa[q][c] = O::bc(0.f);
-#pragma unroll 4
+#pragma unroll(UNR)
         for (int jj = c0; jj < c0 + CH * TPI; jj += TPI) {
           const float4 wj = sv[jj];
           float4 hj, lj;
@@ -607,8 +610,9 @@ int choose_variant(int prec, int mask, int64_t n_i) {
   // Built-in choice from timings on a GB300 (N = 1M King, every shape):
   // packed FP32x2 variants for long lists (split precision with the
   // tile-relative far field, which costs ~1% when particles are not stored
-  // in a spatial order and gains ~4-8% when they are), more threads per
-  // i-particle as the list shortens.  The bucket edges (kBucketMid, kBucketLong) are the
+  // in a spatial order and gains ~4-8% when they are; FP32 with IPT = 4,
+  // 3-4% faster than IPT = 2 at every active fraction from 2^-10 to 1),
+  // more threads per i-particle as the list shortens.  The bucket edges (kBucketMid, kBucketLong) are the
   // ones the device-resident block steps use, so both paths run the same
   // shapes.  nb_set_force_table overrides it per workload.
   if (mask) return prec ? 10 : 11;
@@ -617,7 +621,7 @@ int choose_variant(int prec, int mask, int64_t n_i) {
     if (n_i >= kBucketMid) return 16;
     return 4;
   }
-  if (n_i >= kBucketLong) return 15;
+  if (n_i >= kBucketLong) return 14;
   if (n_i >= kBucketMid) return 8;
   return 9;
 }
