@@ -791,15 +791,38 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   E.n_clamped = c->clamped;
   E.ctl = c->scal;
   const int end_grid = c->num_sms * 2;
-  for (int step = 0; step < kGraphSteps; ++step) {
+  // The bucket launches are independent graph branches (fork after
+  // block_begin, join before block_end), so the ones outside their range
+  // return while the selected one runs instead of after it.
+  cudaStream_t bs[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int k = 0; k < nbk && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&bs[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+  }
+  for (int step = 0; step < kGraphSteps && e == cudaSuccess; ++step) {
     int nl = 0;
-    NB_CUDA(launch_block_begin(B, s));
-    for (int k = 0; k < nbk; ++k)
-      NB_CUDA(launch_force_dev(b[k].v, device_force_args(c, b[k]), E.pmax[k], c->n, s, &nl,
-                               false));
-    NB_CUDA(launch_block_end(E, end_grid, s));
+    e = launch_block_begin(B, s);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+    for (int k = 0; k < nbk && e == cudaSuccess; ++k) {
+      e = cudaStreamWaitEvent(bs[k], fork, 0);
+      if (e == cudaSuccess)
+        e = launch_force_dev(b[k].v, device_force_args(c, b[k]), E.pmax[k], c->n, bs[k], &nl,
+                             false);
+      if (e == cudaSuccess) e = cudaEventRecord(join[k], bs[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join[k], 0);
+    }
+    if (e == cudaSuccess) e = launch_block_end(E, end_grid, s);
     *launches += 2 + nl;
   }
+  for (int k = 0; k < nbk; ++k) {
+    if (bs[k]) cudaStreamDestroy(bs[k]);
+    if (join[k]) cudaEventDestroy(join[k]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (e != cudaSuccess)
+    return fail(NB_ERR_CUDA, "fused block-step capture: %s", cudaGetErrorString(e));
   return NB_OK;
 }
 

@@ -206,8 +206,8 @@ __device__ __forceinline__ void fixup_warp_n(const double *__restrict__ part,
     for (int e = 0; e < NQ; ++e) {
       const int p = plo[e] + o;
       if (use[e] && p <= phi[e]) {
-        const uint64_t u0p = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
-        const int slot = (u0p / n_jt == ib[e]) ? 0 : 1;
+        const uint64_t u0p = dev::udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
+        const int slot = (dev::udiv(u0p, n_jt) == ib[e]) ? 0 : 1;
         const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
 #pragma unroll
         for (int c = 0; c < 6; ++c) s[e][c] += src[static_cast<size_t>(c) * BI + kk[e]];
@@ -242,11 +242,19 @@ __device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t 
     const int64_t k = k0 + wid + kEndWarps * e;
     valid[e] = k < n_act;
     const uint64_t kc = valid[e] ? static_cast<uint64_t>(k) : 0;
-    ib[e] = kc / BI;
-    kk[e] = static_cast<int>(kc % BI);
+    ib[e] = dev::udiv(kc, BI);
+    kk[e] = static_cast<int>(kc - ib[e] * BI);
     plo[e] = dev::owner_of(ib[e] * n_jt, U, P);
     phi[e] = dev::owner_of((ib[e] + 1) * n_jt - 1, U, P);
     split[e] = valid[e] && plo[e] != phi[e];
+  }
+  // warp 0 loads the corrector's inputs of the round's entries while the
+  // warps add the partial sums
+  dev::PState st;
+  int64_t ci = -1;
+  if (wid == 0 && lane < NQ * kEndWarps && k0 + lane < n_act) {
+    ci = E.act[k0 + lane];
+    dev::load_state(ci, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, st);
   }
   double s[NQ][6];
   fixup_warp_n<NQ>(E.part, ib, kk, plo, phi, split, U, P, n_jt, BI, lane, s);
@@ -274,11 +282,10 @@ __device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t 
     }
   }
   __syncthreads();
-  if (wid == 0 && lane < NQ * kEndWarps && k0 + lane < n_act) {
+  if (ci >= 0) {
     const double *f = s_f[lane];
-    dev::correct_vals(E.act[k0 + lane], f, f + 3, t_next, E.x, E.v, E.a, E.jk, E.t_tick,
-                      E.lev, E.eta, E.lev_min, E.lev_max, E.block_steps, E.n_clamped,
-                      E.ctl + kCtlLevCnt);
+    dev::correct_vals(ci, st, f, f + 3, t_next, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, E.eta,
+                      E.lev_min, E.lev_max, E.block_steps, E.n_clamped, E.ctl + kCtlLevCnt);
   }
   __syncthreads();
 }
@@ -299,7 +306,8 @@ __global__ void __launch_bounds__(kEndThreads) block_end_kernel(const EndArgs E)
   if (b < 0) return;
   // the split the force launch of this bucket derived from the same count
   const int BI = E.bi[b];
-  const uint64_t U = static_cast<uint64_t>((n_act + BI - 1) / BI) * static_cast<uint64_t>(E.n_jt);
+  const uint64_t U = dev::udiv(static_cast<uint64_t>(n_act + BI - 1), BI) *
+                     static_cast<uint64_t>(E.n_jt);
   const uint64_t pm = (U + kMinUnits - 1) / kMinUnits;
   const int P = static_cast<int>(pm < static_cast<uint64_t>(E.pmax[b]) ? pm : E.pmax[b]);
   // short lists: one entry per warp per round (the fix-ups in parallel);

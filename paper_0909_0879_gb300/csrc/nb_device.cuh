@@ -113,9 +113,20 @@ __device__ __forceinline__ void tile_frame(int64_t tile, int64_t j, bool real, f
   }
 }
 
+// Unsigned division and remainder, in 32 bits when both operands fit (a
+// 64-bit division is a long instruction sequence; the result is the same).
+__host__ __device__ __forceinline__ uint64_t udiv(uint64_t a, uint64_t b) {
+  if (((a | b) >> 32) == 0) return static_cast<uint32_t>(a) / static_cast<uint32_t>(b);
+  return a / b;
+}
+__host__ __device__ __forceinline__ uint64_t umod(uint64_t a, uint64_t b) {
+  if (((a | b) >> 32) == 0) return static_cast<uint32_t>(a) % static_cast<uint32_t>(b);
+  return a % b;
+}
+
 // CTA owning unit u of U units split over P CTAs (ranges [U p / P, U (p+1) / P)).
 __host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) {
-  return static_cast<int>(((u + 1) * static_cast<uint64_t>(P) - 1) / U);
+  return static_cast<int>(udiv((u + 1) * static_cast<uint64_t>(P) - 1, U));
 }
 
 // Sum of the FP64 partial segments of entry kk of split i-block ib, held by
@@ -128,8 +139,8 @@ __device__ __forceinline__ void fixup_warp(const double *__restrict__ part, uint
 #pragma unroll
   for (int c = 0; c < 6; ++c) s[c] = 0.0;
   for (int p = plo + lane; p <= phi; p += 32) {
-    const uint64_t u0p = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
-    const int slot = (u0p / n_jt == ib) ? 0 : 1;
+    const uint64_t u0p = udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
+    const int slot = (udiv(u0p, n_jt) == ib) ? 0 : 1;
     const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
 #pragma unroll
     for (int c = 0; c < 6; ++c) s[c] += src[static_cast<size_t>(c) * BI + kk];
@@ -168,19 +179,43 @@ __device__ __forceinline__ double pow2(int k) {
   return __longlong_as_double(static_cast<long long>(1023 + k) << 52);
 }
 
-// Hermite corrector, step criterion and new level of particle i with its
-// new force an, jn at t_next.  With lev_cnt set, a change of level moves
-// the particle between the per-level counts.
+// State of one particle as the corrector reads it (loaded ahead of the
+// corrector so that the loads overlap other work).
+struct PState {
+  double x[3], v[3], a[3], j[3];
+  int64_t t;
+  int lev;
+};
+
+__device__ __forceinline__ void load_state(int64_t i, const double *__restrict__ x,
+                                           const double *__restrict__ v,
+                                           const double *__restrict__ a,
+                                           const double *__restrict__ jk,
+                                           const int64_t *__restrict__ t_tick,
+                                           const int32_t *__restrict__ lev, PState &st) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    st.x[c] = x[3 * i + c];
+    st.v[c] = v[3 * i + c];
+    st.a[c] = a[3 * i + c];
+    st.j[c] = jk[3 * i + c];
+  }
+  st.t = t_tick[i];
+  st.lev = lev[i];
+}
+
+// Hermite corrector, step criterion and new level of particle i (state st)
+// with its new force an, jn at t_next.  With lev_cnt set, a change of level
+// moves the particle between the per-level counts.
 __device__ __forceinline__ void correct_vals(
-    int64_t i, const double an3[3], const double jn3[3], int64_t t_next,
+    int64_t i, const PState &st, const double an3[3], const double jn3[3], int64_t t_next,
     double *__restrict__ x, double *__restrict__ v, double *__restrict__ a,
     double *__restrict__ jk, int64_t *__restrict__ t_tick, int32_t *__restrict__ lev,
     double eta, int lev_min, int lev_max, int block_steps, unsigned long long *n_clamped,
     int64_t *lev_cnt) {
-  const int64_t dtk = t_next - t_tick[i];
+  const int64_t dtk = t_next - st.t;
   const double dt = static_cast<double>(dtk) * kTick;
-  double xp[3], vp[3];
-  predict_pos_vel(x, v, a, jk, i, dt, xp, vp);
+  const double h2 = 0.5 * dt, h3 = dt * (1.0 / 3.0);
   const double dt2 = dt * dt, dt3 = dt2 * dt;
   // A due particle's step is a power of two of ticks, so 1/dt^2 and 1/dt^3
   // are powers of two, built exactly from the exponent (no division), and
@@ -197,14 +232,17 @@ __device__ __forceinline__ void correct_vals(
   double a2e[3], a3e[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double a0 = a[3 * i + c], j0 = jk[3 * i + c];
+    const double a0 = st.a[c], j0 = st.j[c];
+    // predictor (the same expression as predict_pos_vel)
+    const double xp = st.x[c] + dt * (st.v[c] + h2 * (a0 + h3 * j0));
+    const double vp = st.v[c] + dt * (a0 + h2 * j0);
     const double an = an3[c], jn = jn3[c];
     const double da = a0 - an;
     // second and third derivatives of a at the start of the step
     const double snap = (-6.0 * da - dt * (4.0 * j0 + 2.0 * jn)) * idt2;
     const double crackle = (12.0 * da + 6.0 * dt * (j0 + jn)) * idt3;
-    x[3 * i + c] = xp[c] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
-    v[3 * i + c] = vp[c] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
+    x[3 * i + c] = xp + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
+    v[3 * i + c] = vp + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
     a[3 * i + c] = an;
     jk[3 * i + c] = jn;
     a2e[c] = snap + crackle * dt;
@@ -217,7 +255,7 @@ __device__ __forceinline__ void correct_vals(
     int cl = 0;
     const int want = level_from_dt(dtc, lev_min, lev_max, &cl);
     if (cl) atomicAdd(n_clamped, 1ull);
-    const int old = lev[i];
+    const int old = st.lev;
     int nl = old;
     if (want >= old) {
       nl = want;
@@ -242,9 +280,12 @@ __device__ __forceinline__ void correct_one(
     int64_t *__restrict__ t_tick, int32_t *__restrict__ lev, const double *__restrict__ a1,
     const double *__restrict__ j1, double eta, int lev_min, int lev_max, int block_steps,
     unsigned long long *n_clamped, int64_t *lev_cnt) {
+  const int64_t i = act[k];
+  PState st;
+  load_state(i, x, v, a, jk, t_tick, lev, st);
   const double an[3] = {a1[3 * k], a1[3 * k + 1], a1[3 * k + 2]};
   const double jn[3] = {j1[3 * k], j1[3 * k + 1], j1[3 * k + 2]};
-  correct_vals(act[k], an, jn, t_next, x, v, a, jk, t_tick, lev, eta, lev_min, lev_max,
+  correct_vals(i, st, an, jn, t_next, x, v, a, jk, t_tick, lev, eta, lev_min, lev_max,
                block_steps, n_clamped, lev_cnt);
 }
 

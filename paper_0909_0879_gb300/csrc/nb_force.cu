@@ -215,13 +215,13 @@ __global__ void __launch_bounds__(NT, 1)
     // device-resident block step: size the split from the device's count
     n_i = A.ctl[kCtlNact];
     if (n_i < A.lo || n_i >= A.hi || n_i <= 0) return;
-    U = static_cast<uint64_t>((n_i + BI - 1) / BI) * n_jt;
+    U = dev::udiv(static_cast<uint64_t>(n_i + BI - 1), BI) * n_jt;
     const uint64_t pmax = (U + kMinUnits - 1) / kMinUnits;
     P = static_cast<int>(pmax < gridDim.x ? pmax : gridDim.x);
     if (p >= P) return;
   }
-  const uint64_t u0 = U * static_cast<uint64_t>(p) / static_cast<uint64_t>(P);
-  const uint64_t u1 = U * static_cast<uint64_t>(p + 1) / static_cast<uint64_t>(P);
+  const uint64_t u0 = dev::udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
+  const uint64_t u1 = dev::udiv(U * static_cast<uint64_t>(p + 1), static_cast<uint64_t>(P));
   if (u0 >= u1) return;  // uniform over the CTA
   const uint64_t nunits = u1 - u0;
   const float eps2 = A.eps2;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NT, 1)
 
   auto issue = [&](uint64_t s_idx) {
     const int st = static_cast<int>(s_idx % kStages);
-    const uint64_t jt = (u0 + s_idx) % n_jt;
+    const uint64_t jt = dev::umod(u0 + s_idx, n_jt);
     float4 *dst = sbase + static_cast<size_t>(st) * NARR * kJT;
     mbar_expect_tx(&bars[st], kTileBytes * NARR);
     bulk_g2s(dst, A.jhi + jt * kJT, kTileBytes, &bars[st]);
@@ -247,12 +247,12 @@ __global__ void __launch_bounds__(NT, 1)
     for (uint64_t s = 0; s < pre; ++s) issue(s);
   }
 
-  const uint64_t ib_first = u0 / n_jt;
+  const uint64_t ib_first = dev::udiv(u0, n_jt);
   uint64_t s_idx = 0;
   uint64_t u = u0;
   while (u < u1) {
-    const uint64_t ib = u / n_jt;
-    const uint64_t jt0 = u % n_jt;
+    const uint64_t ib = dev::udiv(u, n_jt);
+    const uint64_t jt0 = u - ib * n_jt;
     const uint64_t seg = (n_jt - jt0) < (u1 - u) ? (n_jt - jt0) : (u1 - u);
     const bool full = (jt0 == 0) && (seg == n_jt);
 
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(NT, 1)
       bool fast = false;
       V ndx[NQ][3];
       if (REL) {
-        const uint64_t jt = (u0 + s_idx) % n_jt;
+        const uint64_t jt = dev::umod(u0 + s_idx, n_jt);
         const float4 to = __ldg(&A.tinfo[2 * jt]);
         const float4 th = __ldg(&A.tinfo[2 * jt + 1]);
         const float ox[3] = {to.x, to.y, to.z}, hw[3] = {th.x, th.y, th.z};
@@ -520,13 +520,13 @@ __global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
     // P arrives as the force kernel's grid; derive the split as it did
     n_i = ctl[kCtlNact];
     if (n_i < lo || n_i >= hi || n_i <= 0) return;
-    U = static_cast<uint64_t>((n_i + BI - 1) / BI) * n_jt;
+    U = dev::udiv(static_cast<uint64_t>(n_i + BI - 1), BI) * n_jt;
     const uint64_t pmax = (U + kMinUnits - 1) / kMinUnits;
     if (pmax < static_cast<uint64_t>(P)) P = static_cast<int>(pmax);
   }
   if (k >= n_i) return;  // uniform per warp
-  const uint64_t ib = static_cast<uint64_t>(k) / BI;
-  const int kk = static_cast<int>(static_cast<uint64_t>(k) % BI);
+  const uint64_t ib = dev::udiv(static_cast<uint64_t>(k), BI);
+  const int kk = static_cast<int>(static_cast<uint64_t>(k) - ib * BI);
   const int plo = owner_of(ib * n_jt, U, P);
   const int phi = owner_of((ib + 1) * n_jt - 1, U, P);
   if (plo == phi) return;  // written directly by its only CTA
