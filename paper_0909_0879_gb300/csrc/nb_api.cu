@@ -279,7 +279,7 @@ nb_status queue_force(nb_ctx *c, const int32_t *d_idx, int64_t n_i, double *d_ac
   A.G = c->cfg.G;
   A.acc = d_acc;
   A.jerk = d_jerk;
-  A.part = c->part;
+  A.part = reinterpret_cast<float2 *>(c->part);
   A.err = c->err;
   int nl = 0;
   NB_CUDA(launch_force(v, A, grid, c->stream, &nl));
@@ -700,7 +700,7 @@ ForceArgs device_force_args(const nb_ctx *c, const Bucket &b) {
   A.G = c->cfg.G;
   A.acc = c->a1;
   A.jerk = c->j1;
-  A.part = c->part;
+  A.part = reinterpret_cast<float2 *>(c->part);
   A.err = c->err;
   A.ctl = c->scal;
   A.lo = b.lo;
@@ -773,7 +773,7 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
     E.bi[k] = block_i(variant_at(b[k].v));
     E.pmax[k] = c->num_sms * ctas_per_sm(b[k].v);
   }
-  E.part = c->part;
+  E.part = reinterpret_cast<const float2 *>(c->part);
   E.G = c->cfg.G;
   E.a1 = c->a1;
   E.j1 = c->j1;

@@ -189,16 +189,16 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
 // skips it), with the per-entry order of dev::fixup_warp: lanes stride over
 // the CTAs in ascending order, then the same butterfly.  Warp-uniform.
 template <int NQ>
-__device__ __forceinline__ void fixup_warp_n(const double *__restrict__ part,
+__device__ __forceinline__ void fixup_warp_n(const float2 *__restrict__ part,
                                              const uint64_t *ib, const int *kk,
                                              const int *plo, const int *phi, const bool *use,
                                              uint64_t U, int P, uint64_t n_jt, int BI,
-                                             int lane, double s[][6]) {
+                                             int lane, float h[][6], float l[][6]) {
   int span = 0;
 #pragma unroll
   for (int e = 0; e < NQ; ++e) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s[e][c] = 0.0;
+    for (int c = 0; c < 6; ++c) h[e][c] = l[e][c] = 0.f;
     if (use[e] && phi[e] - plo[e] + 1 > span) span = phi[e] - plo[e] + 1;
   }
   for (int o = lane; o < span; o += 32) {
@@ -208,9 +208,12 @@ __device__ __forceinline__ void fixup_warp_n(const double *__restrict__ part,
       if (use[e] && p <= phi[e]) {
         const uint64_t u0p = dev::udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
         const int slot = (dev::udiv(u0p, n_jt) == ib[e]) ? 0 : 1;
-        const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+        const float2 *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s[e][c] += src[static_cast<size_t>(c) * BI + kk[e]];
+        for (int c = 0; c < 6; ++c) {
+          const float2 w = src[static_cast<size_t>(c) * BI + kk[e]];
+          dev::ds_add_pair(h[e][c], l[e][c], w.x, w.y, h[e][c], l[e][c]);
+        }
       }
     }
   }
@@ -219,19 +222,30 @@ __device__ __forceinline__ void fixup_warp_n(const double *__restrict__ part,
 #pragma unroll
     for (int e = 0; e < NQ; ++e)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) s[e][c] += __shfl_xor_sync(0xffffffffu, s[e][c], off);
+      for (int c = 0; c < 6; ++c) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h[e][c], off);
+        const float ol = __shfl_xor_sync(0xffffffffu, l[e][c], off);
+        dev::ds_add_pair(h[e][c], l[e][c], oh, ol, h[e][c], l[e][c]);
+      }
 }
 
 constexpr int kEndWarps = kEndThreads / 32;
 
+// New force of one round's entry as block_end stages it: the fix-up sum of a
+// split i-block (split precision, converted to FP64 by the corrector lane)
+// or nothing (its only CTA wrote the FP64 value to a1, j1).
+struct EndStage {
+  float2 f[4 * kEndWarps][6];
+  int split[4 * kEndWarps];
+};
+
 // One round of block_end over the entries k0 .. k0 + NQ * kEndWarps - 1:
-// the warps gather the new force of NQ entries each (the fix-up sum of a
-// split i-block, or the value its only CTA wrote), then warp 0 corrects
-// the round's entries, a lane each.
+// the warps add the split partial sums of NQ entries each, then warp 0
+// corrects the round's entries, a lane each.
 template <int NQ>
 __device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t n_act,
                                           int64_t t_next, int BI, uint64_t U, int P,
-                                          double (*s_f)[6]) {
+                                          EndStage &sg) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint64_t n_jt = static_cast<uint64_t>(E.n_jt);
   uint64_t ib[NQ];
@@ -256,42 +270,44 @@ __device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t 
     ci = E.act[k0 + lane];
     dev::load_state(ci, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, st);
   }
-  double s[NQ][6];
-  fixup_warp_n<NQ>(E.part, ib, kk, plo, phi, split, U, P, n_jt, BI, lane, s);
+  float h[NQ][6], l[NQ][6];
+  fixup_warp_n<NQ>(E.part, ib, kk, plo, phi, split, U, P, n_jt, BI, lane, h, l);
   if (lane == 0) {
 #pragma unroll
     for (int e = 0; e < NQ; ++e) {
-      if (!valid[e]) continue;
-      const int64_t k = k0 + wid + kEndWarps * e;
-      double *f = s_f[wid + kEndWarps * e];
-      if (split[e]) {
+      const int q = wid + kEndWarps * e;
+      sg.split[q] = split[e] ? 1 : 0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          f[c] = E.G * s[e][c];
-          f[3 + c] = E.G * s[e][3 + c];
-          E.a1[3 * k + c] = f[c];
-          E.j1[3 * k + c] = f[3 + c];
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          f[c] = E.a1[3 * k + c];
-          f[3 + c] = E.j1[3 * k + c];
-        }
-      }
+      for (int c = 0; c < 6; ++c) sg.f[q][c] = make_float2(h[e][c], l[e][c]);
     }
   }
   __syncthreads();
   if (ci >= 0) {
-    const double *f = s_f[lane];
-    dev::correct_vals(ci, st, f, f + 3, t_next, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, E.eta,
+    const int64_t k = k0 + lane;
+    double an[3], jn[3];
+    if (sg.split[lane]) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        an[c] = dev::ds_to_double(sg.f[lane][c].x, sg.f[lane][c].y, E.G);
+        jn[c] = dev::ds_to_double(sg.f[lane][3 + c].x, sg.f[lane][3 + c].y, E.G);
+        E.a1[3 * k + c] = an[c];
+        E.j1[3 * k + c] = jn[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        an[c] = E.a1[3 * k + c];
+        jn[c] = E.j1[3 * k + c];
+      }
+    }
+    dev::correct_vals(ci, st, an, jn, t_next, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, E.eta,
                       E.lev_min, E.lev_max, E.block_steps, E.n_clamped, E.ctl + kCtlLevCnt);
   }
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(kEndThreads) block_end_kernel(const EndArgs E) {
-  __shared__ double s_f[4 * kEndWarps][6];
+  __shared__ EndStage sg;
   const int64_t t_next = E.ctl[kCtlTnext];
   if (t_next < 0) return;
   const int64_t n_act = E.ctl[kCtlNact];
@@ -315,11 +331,11 @@ __global__ void __launch_bounds__(kEndThreads) block_end_kernel(const EndArgs E)
   if (n_act <= static_cast<int64_t>(kEndWarps) * gridDim.x) {
     for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * kEndWarps; k0 < n_act;
          k0 += static_cast<int64_t>(gridDim.x) * kEndWarps)
-      end_round<1>(E, k0, n_act, t_next, BI, U, P, s_f);
+      end_round<1>(E, k0, n_act, t_next, BI, U, P, sg);
   } else {
     for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * 4 * kEndWarps; k0 < n_act;
          k0 += static_cast<int64_t>(gridDim.x) * 4 * kEndWarps)
-      end_round<4>(E, k0, n_act, t_next, BI, U, P, s_f);
+      end_round<4>(E, k0, n_act, t_next, BI, U, P, sg);
   }
 }
 

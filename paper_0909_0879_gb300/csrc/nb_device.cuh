@@ -129,31 +129,70 @@ __host__ __device__ __forceinline__ int owner_of(uint64_t u, uint64_t U, int P) 
   return static_cast<int>(udiv((u + 1) * static_cast<uint64_t>(P) - 1, U));
 }
 
-// Sum of the FP64 partial segments of entry kk of split i-block ib, held by
-// CTAs plo..phi: lanes stride over the CTAs (ascending within a lane) and
-// meet by a butterfly, so every lane returns the same total, in an order
-// fixed by the split.  Called by a full warp.
-__device__ __forceinline__ void fixup_warp(const double *__restrict__ part, uint64_t ib,
+// Split-precision ("double-single") arithmetic on the FP32 pipe: a value
+// is the unevaluated sum hi + lo of two floats.  The partial sums of split
+// i-blocks and their reductions use it instead of FP64, whose pipe retires
+// only ~1.6 lane-operations per SM clock on this part.
+//
+// Exact sum of two floats: s + e == a + b (Knuth's two-sum; the error is the
+// same whichever operand comes first, so the pair sum below is commutative
+// and a butterfly leaves the same total on every lane).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+
+// (ah + al) + (bh + bl) as a normalised pair (h, l).
+__device__ __forceinline__ void ds_add_pair(float ah, float al, float bh, float bl, float &h,
+                                            float &l) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// The pair (h, l) times G in FP64.
+__device__ __forceinline__ double ds_to_double(float h, float l, double G) {
+  return G * (static_cast<double>(h) + static_cast<double>(l));
+}
+
+// Sum of the split-precision partial segments (float2 hi, lo) of entry kk
+// of split i-block ib, held by CTAs plo..phi: lanes stride over the CTAs
+// (ascending within a lane) and meet by a butterfly, so every lane returns
+// the same total, in an order fixed by the split.  Called by a full warp.
+__device__ __forceinline__ void fixup_warp(const float2 *__restrict__ part, uint64_t ib,
                                            int kk, int plo, int phi, uint64_t U, int P,
-                                           uint64_t n_jt, int BI, int lane, double s[6]) {
+                                           uint64_t n_jt, int BI, int lane, float h[6],
+                                           float l[6]) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) s[c] = 0.0;
+  for (int c = 0; c < 6; ++c) h[c] = l[c] = 0.f;
   for (int p = plo + lane; p <= phi; p += 32) {
     const uint64_t u0p = udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
     const int slot = (udiv(u0p, n_jt) == ib) ? 0 : 1;
-    const double *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+    const float2 *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] += src[static_cast<size_t>(c) * BI + kk];
+    for (int c = 0; c < 6; ++c) {
+      const float2 w = src[static_cast<size_t>(c) * BI + kk];
+      ds_add_pair(h[c], l[c], w.x, w.y, h[c], l[c]);
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+    for (int c = 0; c < 6; ++c) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h[c], off);
+      const float ol = __shfl_xor_sync(0xffffffffu, l[c], off);
+      ds_add_pair(h[c], l[c], oh, ol, h[c], l[c]);
+    }
 }
 
-__device__ __forceinline__ double norm3(const double u[3]) {
-  return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+__device__ __forceinline__ double dot3(const double u[3]) {
+  return u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 }
+
+__device__ __forceinline__ double norm3(const double u[3]) { return sqrt(dot3(u)); }
 
 // Largest power of two 2^-lev <= dt (frexp is exact), clamped.
 __device__ __forceinline__ int level_from_dt(double dt, int lev_min, int lev_max,
@@ -166,6 +205,31 @@ __device__ __forceinline__ int level_from_dt(double dt, int lev_min, int lev_max
   int e;
   frexp(dt, &e);
   int lev = 1 - e;
+  if (lev > lev_max) {
+    *clamped = 1;
+    lev = lev_max;
+  }
+  if (lev < lev_min) lev = lev_min;
+  return lev;
+}
+
+// Level of the Aarseth step dt = sqrt(q), q = N / D >= 0, without forming
+// q or dt: floor(log2 q) = e_N - e_D - [f_N < f_D] exactly (N = f_N 2^e_N,
+// D = f_D 2^e_D, f in [0.5, 1)), and the largest 2^-lev <= dt has
+// lev = -floor(floor(log2 q) / 2).  This is the level level_from_dt gives
+// for the exact sqrt(N / D); special values follow it too (q = 0 or NaN:
+// lev_max and a clamp, q = inf: lev_min).
+__device__ __forceinline__ int level_from_ratio(double N, double D, int lev_min, int lev_max,
+                                                int *clamped) {
+  if (isnan(N) || isnan(D) || !(N > 0.0) || isinf(D)) {  // q = 0 or undefined
+    *clamped = 1;
+    return lev_max;
+  }
+  if (isinf(N) || D == 0.0) return lev_min;  // q = inf
+  int eN, eD;
+  const double fN = frexp(N, &eN), fD = frexp(D, &eD);
+  const int F = eN - eD - (fN < fD ? 1 : 0);
+  int lev = -(F >> 1);
   if (lev > lev_max) {
     *clamped = 1;
     lev = lev_max;
@@ -250,10 +314,15 @@ __device__ __forceinline__ void correct_vals(
   }
   t_tick[i] = t_next;
   if (block_steps) {
-    const double na = norm3(an3), nj = norm3(jn3), n2 = norm3(a2e), n3 = norm3(a3e);
-    const double dtc = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+    // Aarseth's criterion dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)
+    // as numerator and denominator; the level comes from their exponents
+    // (no FP64 divide or square root of the quotient: on this part each
+    // costs ~600 cycles of latency in a single warp)
+    const double na2 = dot3(an3), nj2 = dot3(jn3), n22 = dot3(a2e), n32 = dot3(a3e);
+    const double N = eta * (sqrt(na2 * n22) + nj2);
+    const double D = sqrt(nj2 * n32) + n22;
     int cl = 0;
-    const int want = level_from_dt(dtc, lev_min, lev_max, &cl);
+    const int want = level_from_ratio(N, D, lev_min, lev_max, &cl);
     if (cl) atomicAdd(n_clamped, 1ull);
     const int old = st.lev;
     int nl = old;

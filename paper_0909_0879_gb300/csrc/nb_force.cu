@@ -469,20 +469,28 @@ __global__ void __launch_bounds__(NT, 1)
       if (tid == 0 && s_idx + kStages < nunits) issue(s_idx + kStages);
     }
 
-    // epilogue: FP64 results of this segment
+    // epilogue: the segment's sums, reduced over the TPI threads of each
+    // i-particle in split precision on the FP32 pipe; FP64 results for a
+    // whole i-block, split-precision partials otherwise
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
-      double o[6];
+      float oh[6], ol[6];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        o[c] = static_cast<double>(D.AH(q, c)) + static_cast<double>(D.AL(q, c));
-        o[3 + c] = static_cast<double>(D.JH(q, c)) + static_cast<double>(D.JL(q, c));
+        oh[c] = D.AH(q, c);
+        ol[c] = D.AL(q, c);
+        oh[3 + c] = D.JH(q, c);
+        ol[3 + c] = D.JL(q, c);
       }
       if (TPI > 1) {
 #pragma unroll
         for (int off = 1; off < TPI; off <<= 1)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) o[c] += __shfl_xor_sync(0xffffffffu, o[c], off);
+          for (int c = 0; c < 6; ++c) {
+            const float wh = __shfl_xor_sync(0xffffffffu, oh[c], off);
+            const float wl = __shfl_xor_sync(0xffffffffu, ol[c], off);
+            dev::ds_add_pair(oh[c], ol[c], wh, wl, oh[c], ol[c]);
+          }
       }
       const int kk = g + q * NG;
       const int64_t k = static_cast<int64_t>(ib) * BI + kk;
@@ -490,14 +498,15 @@ __global__ void __launch_bounds__(NT, 1)
         if (full) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            A.acc[3 * k + c] = A.G * o[c];
-            A.jerk[3 * k + c] = A.G * o[3 + c];
+            A.acc[3 * k + c] = dev::ds_to_double(oh[c], ol[c], A.G);
+            A.jerk[3 * k + c] = dev::ds_to_double(oh[3 + c], ol[3 + c], A.G);
           }
         } else {
           const int slot = (ib == ib_first) ? 0 : 1;
-          double *dst = A.part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+          float2 *dst = A.part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) dst[static_cast<size_t>(c) * BI + kk] = o[c];
+          for (int c = 0; c < 6; ++c)
+            dst[static_cast<size_t>(c) * BI + kk] = make_float2(oh[c], ol[c]);
         }
       }
     }
@@ -509,7 +518,7 @@ __global__ void __launch_bounds__(NT, 1)
 // i-particle, lanes stride over the CTAs that hold a partial (ascending
 // within a lane) and meet by a butterfly; the order is fixed for a given
 // grid, so results are deterministic.
-__global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
+__global__ void force_fixup_kernel(const float2 *__restrict__ part, int64_t n_i,
                                    uint64_t n_jt, uint64_t U, int P, int BI,
                                    double G, double *__restrict__ acc,
                                    double *__restrict__ jerk, const int64_t *ctl,
@@ -530,13 +539,13 @@ __global__ void force_fixup_kernel(const double *__restrict__ part, int64_t n_i,
   const int plo = owner_of(ib * n_jt, U, P);
   const int phi = owner_of((ib + 1) * n_jt - 1, U, P);
   if (plo == phi) return;  // written directly by its only CTA
-  double s[6];
-  dev::fixup_warp(part, ib, kk, plo, phi, U, P, n_jt, BI, lane, s);
+  float h[6], l[6];
+  dev::fixup_warp(part, ib, kk, plo, phi, U, P, n_jt, BI, lane, h, l);
   if (lane == 0) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      acc[3 * k + c] = G * s[c];
-      jerk[3 * k + c] = G * s[3 + c];
+      acc[3 * k + c] = dev::ds_to_double(h[c], l[c], G);
+      jerk[3 * k + c] = dev::ds_to_double(h[3 + c], l[3 + c], G);
     }
   }
 }
@@ -643,7 +652,7 @@ int ctas_per_sm(int v) {
 }
 
 size_t part_bytes(int v, int grid) {
-  return static_cast<size_t>(grid) * 2 * 6 * block_i(kTable[v].V) * sizeof(double);
+  return static_cast<size_t>(grid) * 2 * 6 * block_i(kTable[v].V) * sizeof(float2);
 }
 
 int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap) {

@@ -35,7 +35,7 @@ struct ForceArgs {
   double G;
   double *acc;         // (n_i, 3)
   double *jerk;        // (n_i, 3)
-  double *part;        // partial sums of split i-blocks
+  float2 *part;        // partial sums of split i-blocks (hi, lo pairs)
   int *err;            // device error word
   // Device-resident mode (block steps replayed from a CUDA graph): when ctl
   // is set the active count is ctl[kCtlNact]; a launch does nothing unless
@@ -193,7 +193,7 @@ struct EndArgs {
   int nbk;                           // force-shape buckets of the step
   int64_t lo[3], hi[3];              // active-count range of each bucket
   int bi[3], pmax[3];                // i-block size and persistent grid
-  const double *part;
+  const float2 *part;                // partial sums of split i-blocks (hi, lo pairs)
   double G;
   double *a1, *j1;
   const int32_t *act;
