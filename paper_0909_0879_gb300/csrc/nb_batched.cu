@@ -15,7 +15,7 @@
 // each i-particle's j-range over up to 32 lanes and meet by a warp-shuffle
 // butterfly, so a 16-body cluster still occupies the whole CTA.
 #include "../../include/nbody.h"
-#include "nb_internal.cuh"
+#include "nb_device.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -36,7 +36,8 @@ struct BatchArgs {
   int *queue;             // work counter (zeroed before the launch)
   double *x, *v, *a, *jk; // FP64 state, (N, 3)
   const double *m;
-  double dt;              // shared step
+  double dt;              // shared step (a power of two)
+  double idt2, idt3;      // 1 / dt^2, 1 / dt^3 (exact)
   float eps2;
   double G;
   int nsteps;             // steps per launch (>= 1)
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
     float4 *s_hi = srec;
     float4 *s_lo = srec + B.cap;
     float4 *s_v = srec + (NARR - 1) * B.cap;
+    float2 *s_f = reinterpret_cast<float2 *>(srec + NARR * B.cap);  // bi x 6 sums
     const double dt = B.init_only ? 0.0 : B.dt;
     const int nsteps = B.init_only ? 1 : B.nsteps;
 
@@ -191,46 +193,69 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
         }
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
-          double o[6];
+          // sums over the tpi threads of an i-particle: split-precision pairs
+          // on the FP32 pipe, one FP64 conversion at the end
+          float oh[6], ol[6];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            o[k] = static_cast<double>(ah[q][k]) + static_cast<double>(al[q][k]);
-            o[3 + k] = static_cast<double>(fmaf(-3.f, p2[q][k], p1[q][k]));
+            oh[k] = ah[q][k];
+            ol[k] = al[q][k];
+            oh[3 + k] = fmaf(-3.f, p2[q][k], p1[q][k]);
+            ol[3 + k] = 0.f;
           }
           for (int off = 1; off < tpi; off <<= 1)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) o[k] += __shfl_xor_sync(0xffffffffu, o[k], off);
-          const int i = i0 + g + q * ng;
-          if (r == 0 && i < n) {
-            const int64_t gi = base + i;
-            if (B.init_only) {
+            for (int k = 0; k < 6; ++k) {
+              const float wh = __shfl_xor_sync(0xffffffffu, oh[k], off);
+              const float wl = __shfl_xor_sync(0xffffffffu, ol[k], off);
+              dev::ds_add_pair(oh[k], ol[k], wh, wl, oh[k], ol[k]);
+            }
+          // hand the sums to consecutive threads so that the FP64
+          // corrector runs on full warps (an FP64 instruction costs the SM
+          // the same whatever the number of active lanes)
+          if (r == 0) {
 #pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                B.a[3 * gi + k] = B.G * o[k];
-                B.jk[3 * gi + k] = B.G * o[3 + k];
-              }
-            } else {
-              double xp[3], vp[3];
-              bpredict(B.x, B.v, B.a, B.jk, gi, dt, xp, vp);
-              const double dt2 = dt * dt, dt3 = dt2 * dt;
-              // dt is a power of two: exact reciprocals, identical results
-              const double idt2 = 1.0 / dt2, idt3 = 1.0 / dt3;
+            for (int k = 0; k < 6; ++k) s_f[(g + q * ng) * 6 + k] = make_float2(oh[k], ol[k]);
+          }
+        }
+        __syncthreads();
+        for (int t = tid; t < bi; t += NT) {
+          const int i = i0 + t;
+          if (i >= n) break;
+          const int64_t gi = base + i;
+          double o[6];
 #pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                const double a0 = B.a[3 * gi + k], j0v = B.jk[3 * gi + k];
-                const double an = B.G * o[k], jn = B.G * o[3 + k];
-                const double da = a0 - an;
-                const double snap = (-6.0 * da - dt * (4.0 * j0v + 2.0 * jn)) * idt2;
-                const double crackle = (12.0 * da + 6.0 * dt * (j0v + jn)) * idt3;
-                B.x[3 * gi + k] =
-                    xp[k] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
-                B.v[3 * gi + k] = vp[k] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
-                B.a[3 * gi + k] = an;
-                B.jk[3 * gi + k] = jn;
-              }
+          for (int k = 0; k < 6; ++k)
+            o[k] = static_cast<double>(s_f[t * 6 + k].x) + static_cast<double>(s_f[t * 6 + k].y);
+          if (B.init_only) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              B.a[3 * gi + k] = B.G * o[k];
+              B.jk[3 * gi + k] = B.G * o[3 + k];
+            }
+          } else {
+            double xp[3], vp[3];
+            bpredict(B.x, B.v, B.a, B.jk, gi, dt, xp, vp);
+            const double dt2 = dt * dt, dt3 = dt2 * dt;
+            // dt is a power of two: the host's exact reciprocals (an FP64
+            // divide costs ~600 cycles of latency on this part)
+            const double idt2 = B.idt2, idt3 = B.idt3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const double a0 = B.a[3 * gi + k], j0v = B.jk[3 * gi + k];
+              const double an = B.G * o[k], jn = B.G * o[3 + k];
+              const double da = a0 - an;
+              const double snap = (-6.0 * da - dt * (4.0 * j0v + 2.0 * jn)) * idt2;
+              const double crackle = (12.0 * da + 6.0 * dt * (j0v + jn)) * idt3;
+              B.x[3 * gi + k] =
+                  xp[k] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
+              B.v[3 * gi + k] = vp[k] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
+              B.a[3 * gi + k] = an;
+              B.jk[3 * gi + k] = jn;
             }
           }
         }
+        __syncthreads();  // s_f is reused by the next i-block
       }
       __syncthreads();
     }
@@ -342,7 +367,8 @@ int pick_bvariant(const nb_batch *b) {
 }
 
 size_t bsmem(const BEntry &E, int cap) {
-  return static_cast<size_t>(E.prec ? 3 : 2) * cap * sizeof(float4);
+  return static_cast<size_t>(E.prec ? 3 : 2) * cap * sizeof(float4) +
+         static_cast<size_t>(E.threads) * E.ipt * 6 * sizeof(float2);
 }
 
 int bgrid(nb_batch *b, int v) {
@@ -372,6 +398,8 @@ nb_status launch_batch(nb_batch *b, int v, int grid, int32_t n_items, const int3
   A.jk = b->jk;
   A.m = b->m;
   A.dt = std::ldexp(1.0, -b->cfg.lev_shared);
+  A.idt2 = std::ldexp(1.0, 2 * b->cfg.lev_shared);
+  A.idt3 = std::ldexp(1.0, 3 * b->cfg.lev_shared);
   A.eps2 = static_cast<float>(b->cfg.eps * b->cfg.eps);
   A.G = b->cfg.G;
   A.nsteps = nsteps;
