@@ -237,7 +237,7 @@ int pick_variant(nb_ctx *c, int64_t n_i) {
   if (c->variant_override >= 0) return c->variant_override;
   for (int k = 0; k < c->table_count; ++k)
     if (n_i >= c->table_min[k]) return c->table_var[k];
-  return choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, n_i);
+  return choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, n_i, c->n_jt, c->num_sms);
 }
 
 nb_status ensure_part(nb_ctx *c, size_t bytes) {
@@ -670,19 +670,14 @@ struct Bucket {
 };
 
 int step_buckets(const nb_ctx *c, Bucket *b) {
-  int nbk = 0;
-  const int prec = c->cfg.precision;
-  if (c->cfg.eps == 0.0) {
-    b[nbk++] = {1, INT64_MAX, choose_variant(prec, 1, 1)};
-  } else {
-    b[nbk++] = {1, kBucketMid, choose_variant(prec, 0, 1)};
-    b[nbk++] = {kBucketMid, kBucketLong, choose_variant(prec, 0, kBucketMid)};
-    b[nbk++] = {kBucketLong, INT64_MAX, choose_variant(prec, 0, kBucketLong)};
-  }
-  // buckets no active count can reach are left out
+  const ShapeBuckets sb = shape_buckets(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, c->n_jt,
+                                        c->num_sms);
+  // buckets no active count can reach (or empty ones) are left out
   int k = 0;
-  for (int q = 0; q < nbk; ++q)
-    if (b[q].lo <= c->n) b[k++] = b[q];
+  for (int q = 0; q < sb.nbk; ++q) {
+    const int64_t hi = q + 1 < sb.nbk ? sb.lo[q + 1] : INT64_MAX;
+    if (sb.lo[q] <= c->n && sb.lo[q] < hi) b[k++] = {sb.lo[q], hi, sb.v[q]};
+  }
   return k;
 }
 
@@ -863,10 +858,13 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
   if (max_blocks < 0) return fail(NB_ERR_INVALID_ARG, "negative block budget");
   // partial-sum scratch for every shape the device-resident steps may run
   size_t pb = 0;
-  for (int64_t n_probe : {int64_t(1), kBucketMid, kBucketLong}) {
-    const int v = choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, n_probe);
-    const size_t bytes = part_bytes(v, c->num_sms * ctas_per_sm(v));
-    pb = bytes > pb ? bytes : pb;
+  {
+    const ShapeBuckets sb = shape_buckets(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0,
+                                          c->n_jt, c->num_sms);
+    for (int q = 0; q < sb.nbk; ++q) {
+      const size_t bytes = part_bytes(sb.v[q], c->num_sms * ctas_per_sm(sb.v[q]));
+      pb = bytes > pb ? bytes : pb;
+    }
   }
   s = ensure_part(c, pb);
   if (s != NB_OK) return s;

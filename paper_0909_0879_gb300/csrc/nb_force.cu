@@ -615,24 +615,45 @@ int num_variants() { return kNumVariants; }
 const Variant &variant_at(int v) { return kTable[v].V; }
 int block_i(const Variant &V) { return V.threads / V.tpi * V.ipt; }
 
-int choose_variant(int prec, int mask, int64_t n_i) {
+ShapeBuckets shape_buckets(int prec, int mask, int64_t n_jt, int num_sms) {
   // Built-in choice from timings on a GB300 (N = 1M King, every shape):
   // packed FP32x2 variants for long lists (split precision with the
   // tile-relative far field, which costs ~1% when particles are not stored
   // in a spatial order and gains ~4-8% when they are; FP32 with IPT = 4,
   // 3-4% faster than IPT = 2 at every active fraction from 2^-10 to 1),
-  // more threads per i-particle as the list shortens.  The bucket edges (kBucketMid, kBucketLong) are the
-  // ones the device-resident block steps use, so both paths run the same
-  // shapes.  nb_set_force_table overrides it per workload.
-  if (mask) return prec ? 10 : 11;
-  if (prec) {
-    if (n_i >= kBucketLong) return 26;
-    if (n_i >= kBucketMid) return 16;
-    return 4;
+  // more threads per i-particle as the list shortens.  The host-driven and
+  // the device-resident steps use the same buckets.  nb_set_force_table
+  // overrides the choice per workload.
+  ShapeBuckets b{};
+  if (mask) {
+    b.nbk = 1;
+    b.lo[0] = 1;
+    b.v[0] = prec ? 10 : 11;
+    return b;
   }
-  if (n_i >= kBucketLong) return 14;
-  if (n_i >= kBucketMid) return 8;
-  return 9;
+  const int vs[3] = {prec ? 4 : 9, prec ? 16 : 8, prec ? 26 : 14};
+  const int64_t base[3] = {1, kBucketMid, kBucketLong};
+  // i-blocks a shape needs so that every SM gets kMinUnits units (a small
+  // N has few j-tiles: N = 1024 is 4, and one 1024-particle i-block would
+  // then run on a single CTA)
+  const int64_t need = kMinUnits * static_cast<int64_t>(num_sms);
+  const int64_t blocks = (need + n_jt - 1) / n_jt;
+  b.nbk = 3;
+  for (int k = 0; k < 3; ++k) {
+    const int64_t fill = (blocks - 1) * block_i(kTable[vs[k]].V) + 1;
+    b.lo[k] = k == 0 ? 1 : std::max(base[k], fill);
+    if (k > 0 && b.lo[k] < b.lo[k - 1]) b.lo[k] = b.lo[k - 1];
+    b.v[k] = vs[k];
+  }
+  return b;
+}
+
+int choose_variant(int prec, int mask, int64_t n_i, int64_t n_jt, int num_sms) {
+  const ShapeBuckets b = shape_buckets(prec, mask, n_jt, num_sms);
+  int v = b.v[0];
+  for (int k = 0; k < b.nbk; ++k)
+    if (n_i >= b.lo[k]) v = b.v[k];
+  return v;
 }
 
 int ctas_per_sm(int v) {

@@ -101,8 +101,18 @@ constexpr float kRelKappa = 1.0f;
 int num_variants();
 const Variant &variant_at(int v);
 int block_i(const Variant &V);  // i-particles per i-block
-// Built-in variant for a precision, mask flag and active-list length.
-int choose_variant(int prec, int mask, int64_t n_i);
+// Built-in force shapes by active-list length: bucket k (lo[k] <= n_i <
+// lo[k+1]) runs variant v[k].  A bucket's lower edge is raised above its
+// nominal length (kBucketMid, kBucketLong) until its shape has enough
+// (i-block, j-tile) units to give every SM kMinUnits of them.
+struct ShapeBuckets {
+  int nbk;
+  int64_t lo[3];
+  int v[3];
+};
+ShapeBuckets shape_buckets(int prec, int mask, int64_t n_jt, int num_sms);
+// The variant of n_i's bucket.
+int choose_variant(int prec, int mask, int64_t n_i, int64_t n_jt, int num_sms);
 // Resident CTAs per SM of a variant (occupancy query, cached).
 int ctas_per_sm(int v);
 // Bytes of partial-sum scratch a launch of variant v on `grid` CTAs needs.
