@@ -5,7 +5,8 @@
 //
 //   block_begin  scheduling (next block time, ordered active list) and the
 //                FP64 predictor of every particle, with the j-tile frames;
-//   force        the force + jerk kernels of nb_force.cu (unchanged);
+//   force        the force + jerk kernels of nb_force.cu, one launch per
+//                active-count bucket (the others return at once);
 //   block_end    the fix-up of split i-blocks and the FP64 corrector.
 //
 // Scheduling without a pass over the particles.  The integrator keeps every
