@@ -226,9 +226,19 @@ __device__ __forceinline__ int level_from_ratio(double N, double D, int lev_min,
     return lev_max;
   }
   if (isinf(N) || D == 0.0) return lev_min;  // q = inf
-  int eN, eD;
-  const double fN = frexp(N, &eN), fD = frexp(D, &eD);
-  const int F = eN - eD - (fN < fD ? 1 : 0);
+  // exponents and mantissas from the bit patterns (frexp costs ~400 cycles
+  // of FP64 latency here); subnormal operands take frexp
+  const long long bN = __double_as_longlong(N), bD = __double_as_longlong(D);
+  const int xN = static_cast<int>((bN >> 52) & 0x7ff), xD = static_cast<int>((bD >> 52) & 0x7ff);
+  int F;
+  if (xN != 0 && xD != 0) {
+    const long long kMant = (1ll << 52) - 1;
+    F = xN - xD - ((bN & kMant) < (bD & kMant) ? 1 : 0);
+  } else {
+    int eN, eD;
+    const double fN = frexp(N, &eN), fD = frexp(D, &eD);
+    F = eN - eD - (fN < fD ? 1 : 0);
+  }
   int lev = -(F >> 1);
   if (lev > lev_max) {
     *clamped = 1;
