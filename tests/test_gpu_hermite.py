@@ -394,3 +394,31 @@ def test_fused_block_steps_need_a_level_structured_schedule(nb):
     assert d1 + d2 == steps and t2 == t_end
     for k in sa:
         assert np.array_equal(sa[k], sb[k]), k
+
+
+@pytest.mark.parametrize("block_steps", [False, True])
+def test_fused_block_steps_large_ragged_n(nb, block_steps):
+    """The fused steps' single-pass compaction over 1,173 tiles (n =
+    300,007, not a multiple of 256): every particle active (shared steps)
+    or a few scattered ones (block steps), bitwise equal to the general
+    scheduler."""
+    n = 300007
+    m, x, v = ics.plummer(n, 47)
+    if block_steps:
+        kw = dict(eps=1e-3, eta=0.02, lev_min=4, lev_max=20)
+        t_end, max_blocks = 2.0**-4, 24
+    else:
+        kw = dict(eps=1e-3, block_steps=False, lev_shared=10)
+        t_end, max_blocks = 3 * 2.0**-10, 0
+    res = {}
+    for mode in ("auto", "general"):
+        with nb.NBody(m, x, v, **kw) as s:
+            s.set_block_mode(mode)
+            done, t_last = s.run_blocks(t_end, max_blocks=max_blocks)
+            assert s.last_block_path() == ("fused" if mode == "auto" else "general")
+            res[mode] = (done, t_last, s.get_state(), s.counters())
+    a, g = res["auto"], res["general"]
+    assert a[0] == g[0] and a[1] == g[1] and a[0] > 0
+    assert a[3]["interactions"] == g[3]["interactions"]
+    for k in a[2]:
+        assert np.array_equal(a[2][k], g[2][k]), k
