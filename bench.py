@@ -63,7 +63,8 @@ def parse():
     p.add_argument("--variant", type=int, default=-1)
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--workload", default="king1m",
-                   choices=["king1m", "shared1024", "block65536", "batched", "adjoint"],
+                   choices=["king1m", "shared1024", "block65536", "batched", "adjoint",
+                            "nsweep"],
                    help="king1m is the headline; the others time the remaining workloads "
                         "and print their own JSON line")
     p.add_argument("--block-steps", type=int, default=0,
@@ -639,11 +640,89 @@ def run_adjoint(args):
     return 0
 
 
+def run_nsweep(args):
+    """Seconds per integration step against N on the paper's own test system
+    (Sec. 3): uniform sphere of radius 1, Salpeter mass spectrum, velocities
+    rescaled to virial ratio Q = 1, G = M = R = 1, eps = 0.1 of the mean
+    interparticle distance (4 pi / 3 N)^(1/3).  The quantity of the paper's
+    Fig. 1 for this GPU: a Hermite step (all particles, shared dt, acc + jerk)
+    in split precision and in FP32, and a KDK leapfrog step (acceleration
+    only, FP32).  CPU baseline: the FP64 oracle's force + jerk on a bounded
+    sample of i-particles against all N, scaled to N, on every host core and
+    on one (the paper's OpenMP and serial versions)."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_0909_0879_gb300 import _lib
+
+    O.build()
+    cores = O.max_threads()
+    dev = torch.device("cuda", 0)
+    k_max = int(np.log2(args.n)) if args.n != N_DEFAULT else 20
+    rows = []
+    for k in range(10, k_max + 1):
+        n = 1 << k
+        m, x, v = ics.uniform_sphere(n, 1006, Q=1.0, masses=ics.salpeter_masses(n, 1006))
+        eps = 0.1 * (4.0 * np.pi / (3.0 * n)) ** (1.0 / 3.0)
+        steps = int(min(20, max(2, 2e10 / (n * n))))
+        row = {"n": n, "eps": eps, "gpu_steps_timed": steps}
+        for prec in ("ds", "fp32"):
+            with _lib.NBody(m, x, v, eps=eps, precision=prec, block_steps=False,
+                            lev_shared=10) as s:
+                s.step()
+                e0, e1 = _events(torch)
+                e0.record()
+                for _ in range(steps):
+                    s.step()
+                e1.record()
+                torch.cuda.synchronize()
+                row[f"hermite_{prec}_s"] = e0.elapsed_time(e1) / 1e3 / steps
+        fm = torch.tensor(m, dtype=torch.float32, device=dev)
+        fx = torch.tensor(x, dtype=torch.float32, device=dev)
+        fv = torch.tensor(v, dtype=torch.float32, device=dev)
+        fa = torch.empty_like(fx)
+        _lib.lf_forward(n, fm, fx, fv, fa, 1, 2.0**-10, None, eps=eps)
+        e0, e1 = _events(torch)
+        e0.record()
+        _lib.lf_forward(n, fm, fx, fv, fa, steps, 2.0**-10, None, eps=eps)
+        e1.record()
+        torch.cuda.synchronize()
+        row["leapfrog_fp32_s"] = e0.elapsed_time(e1) / 1e3 / steps
+        # CPU baseline: oracle force + jerk per i-particle, about 0.5 s a point
+        rng = np.random.default_rng(8)
+        for threads in (cores, 1):
+            O.set_threads(threads)
+            probe = np.sort(rng.choice(n, min(n, 16), replace=False))
+            t0 = time.perf_counter()
+            O.force_jerk(m, x, v, eps, idx=probe)
+            per_i = (time.perf_counter() - t0) / len(probe)
+            ns = int(min(n, max(len(probe), 0.5 / max(per_i, 1e-9))))
+            sample = np.sort(rng.choice(n, ns, replace=False))
+            t0 = time.perf_counter()
+            O.force_jerk(m, x, v, eps, idx=sample)
+            dt = time.perf_counter() - t0
+            key = "oracle_all_cores_s" if threads == cores else "oracle_1_core_s"
+            row[key] = dt * n / ns
+            row[key.replace("_s", "_sample")] = ns
+        O.set_threads(cores)
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"metric": "seconds per integration step vs N (uniform sphere, Salpeter masses, Q = 1)",
+           "unit": "s", "workload": "uniform_sphere_salpeter_q1_eps0.1d", "cores": cores,
+           "rows": rows,
+           "note": "GPU: CUDA events, all particles stepped each step; oracle: FP64 force + jerk "
+                   "on a sample of i-particles against all N, scaled to N (the O(N) part is "
+                   "negligible)"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload != "king1m" and args.impl == "ours":
         return {"shared1024": run_shared1024, "block65536": run_block65536,
-                "batched": run_batched, "adjoint": run_adjoint}[args.workload](args)
+                "batched": run_batched, "adjoint": run_adjoint,
+                "nsweep": run_nsweep}[args.workload](args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

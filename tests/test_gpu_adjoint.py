@@ -55,6 +55,30 @@ def test_acc_and_vjp_kernels_match_oracle(torch_cuda, oracle_mod):
         assert rel_l2(gm.double().cpu().numpy(), rgm) < 1e-4
 
 
+@pytest.mark.parametrize("eps", [1e-3, 0.0])
+def test_wide_acc_shape_large_n(torch_cuda, oracle_mod, eps):
+    """Large N takes the wide acceleration shape (4 particles per thread,
+    packed pairs): n = 262,401 (ragged) against the FP64 oracle on 512
+    sampled particles, same float32-rounded inputs."""
+    torch = torch_cuda
+    from paper_0909_0879_gb300 import _lib
+
+    n = 262401
+    m, x, v = ics.plummer(n, 905)
+    dx = torch.tensor(x, dtype=torch.float32, device="cuda")
+    dm = torch.tensor(m, dtype=torch.float32, device="cuda")
+    acc = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    _lib.lf_acc(n, dx, dm, acc, eps=eps)
+    torch.cuda.synchronize()
+    xr = dx.double().cpu().numpy()
+    mr = dm.double().cpu().numpy()
+    sample = np.sort(np.random.default_rng(6).choice(n, 512, replace=False)).astype(np.int32)
+    ra, _ = oracle_mod.force_jerk(mr, xr, np.zeros_like(xr), eps, idx=sample)
+    got = acc.double().cpu().numpy()[sample]
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ra) < 1e-5
+
+
 def test_leapfrog_adjoint_n4096(torch_cuda, oracle_mod):
     """N = 4096 Plummer, eps = 1e-3, 64 KDK steps of dt = 1/128 in FP32,
     checkpoints every 8 steps; L = sum |x(T) - y|^2 with y = x0 + N(0,0.05^2)
