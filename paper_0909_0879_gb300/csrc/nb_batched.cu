@@ -98,16 +98,16 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
       for (int p = tid; p < n; p += NT) {
         double xp[3], vp[3];
         bpredict(B.x, B.v, B.a, B.jk, base + p, dt, xp, vp);
-        const float hx = __double2float_rn(xp[0]);
-        const float hy = __double2float_rn(xp[1]);
-        const float hz = __double2float_rn(xp[2]);
-        s_hi[p] = make_float4(hx, hy, hz, __double2float_rn(B.m[base + p]));
+        // conversions on the integer pipe (bit-identical to the hardware ones)
+        const float hx = dev::d2f_rn(xp[0]);
+        const float hy = dev::d2f_rn(xp[1]);
+        const float hz = dev::d2f_rn(xp[2]);
+        s_hi[p] = make_float4(hx, hy, hz, dev::d2f_rn(B.m[base + p]));
         if (PREC)
-          s_lo[p] = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
-                                __double2float_rn(xp[1] - static_cast<double>(hy)),
-                                __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
-        s_v[p] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                             __double2float_rn(vp[2]), 0.f);
+          s_lo[p] = make_float4(dev::d2f_rn(xp[0] - dev::f2d(hx)),
+                                dev::d2f_rn(xp[1] - dev::f2d(hy)),
+                                dev::d2f_rn(xp[2] - dev::f2d(hz)), 0.f);
+        s_v[p] = make_float4(dev::d2f_rn(vp[0]), dev::d2f_rn(vp[1]), dev::d2f_rn(vp[2]), 0.f);
       }
       __syncthreads();
       for (int i0 = 0; i0 < n; i0 += bi) {
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
           double o[6];
 #pragma unroll
           for (int k = 0; k < 6; ++k)
-            o[k] = static_cast<double>(s_f[t * 6 + k].x) + static_cast<double>(s_f[t * 6 + k].y);
+            o[k] = dev::f2d(s_f[t * 6 + k].x) + dev::f2d(s_f[t * 6 + k].y);
           if (B.init_only) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {

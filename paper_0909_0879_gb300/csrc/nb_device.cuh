@@ -29,6 +29,38 @@ __device__ __forceinline__ void predict_pos_vel(const double *x, const double *v
   }
 }
 
+// FP64 <-> FP32 conversions on the integer pipe.  This part's FP64 pipe
+// retires one warp instruction per ~68 cycles per scheduler and a
+// conversion occupies it like an FMA, while these are a dozen integer
+// operations.  Both are bit-identical to the hardware conversions; values
+// whose result would not be a normal number take the hardware path.
+//
+// Round-to-nearest-even double -> float (IEEE 754 binary64 -> binary32).
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const int e = static_cast<int>((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e < 1 || e > 254) return __double2float_rn(d);  // zero, subnormal, out of range
+  const unsigned long long m = b & ((1ull << 52) - 1);
+  const unsigned long long rem = m & ((1ull << 29) - 1);  // the 29 dropped bits
+  unsigned int bits = (static_cast<unsigned int>(e) << 23) | static_cast<unsigned int>(m >> 29);
+  // round half to even; a carry out of the mantissa steps the exponent,
+  // as it should (up to infinity past the largest float)
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (bits & 1u))) bits += 1u;
+  bits |= static_cast<unsigned int>(b >> 32) & 0x80000000u;
+  return __uint_as_float(bits);
+}
+
+// Exact float -> double.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return static_cast<double>(f);  // zero, subnormal, inf, NaN
+  const unsigned long long b = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
+                               (static_cast<unsigned long long>(e - 127u + 1023u) << 52) |
+                               (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
 // j-records of particle i at the predicted (xp, vp): FP32 position (the
 // high word in DS) + mass, DS low words, FP32 velocity.  Returns the first
 // and the low words through *lo (zero in FP32).
@@ -37,20 +69,18 @@ __device__ __forceinline__ float4 store_records(int64_t i, const double xp[3],
                                                 float4 *__restrict__ jhi,
                                                 float4 *__restrict__ jlo,
                                                 float4 *__restrict__ jvel, float4 *lo) {
-  const float hx = __double2float_rn(xp[0]);
-  const float hy = __double2float_rn(xp[1]);
-  const float hz = __double2float_rn(xp[2]);
-  const float4 h = make_float4(hx, hy, hz, __double2float_rn(m));
+  const float hx = d2f_rn(xp[0]);
+  const float hy = d2f_rn(xp[1]);
+  const float hz = d2f_rn(xp[2]);
+  const float4 h = make_float4(hx, hy, hz, d2f_rn(m));
   jhi[i] = h;
   float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
   if (prec) {
-    l = make_float4(__double2float_rn(xp[0] - static_cast<double>(hx)),
-                    __double2float_rn(xp[1] - static_cast<double>(hy)),
-                    __double2float_rn(xp[2] - static_cast<double>(hz)), 0.f);
+    l = make_float4(d2f_rn(xp[0] - f2d(hx)), d2f_rn(xp[1] - f2d(hy)), d2f_rn(xp[2] - f2d(hz)),
+                    0.f);
     jlo[i] = l;
   }
-  jvel[i] = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]),
-                        __double2float_rn(vp[2]), 0.f);
+  jvel[i] = make_float4(d2f_rn(vp[0]), d2f_rn(vp[1]), d2f_rn(vp[2]), 0.f);
   *lo = l;
   return h;
 }
@@ -155,7 +185,7 @@ __device__ __forceinline__ void ds_add_pair(float ah, float al, float bh, float 
 
 // The pair (h, l) times G in FP64.
 __device__ __forceinline__ double ds_to_double(float h, float l, double G) {
-  return G * (static_cast<double>(h) + static_cast<double>(l));
+  return G * (f2d(h) + f2d(l));
 }
 
 // Sum of the split-precision partial segments (float2 hi, lo) of entry kk
@@ -303,6 +333,14 @@ __device__ __forceinline__ void correct_vals(
     idt2 = 1.0 / dt2;
     idt3 = 1.0 / dt3;
   }
+  // per-particle coefficients, shared by the three components (each FP64
+  // instruction counts on this part: a single warp retires one every ~70
+  // cycles on a dependent chain)
+  const double idt = dt * idt2;  // 1/dt, exact for a power-of-two step
+  const double s_da = -6.0 * idt2, s_j0 = -4.0 * idt, s_jn = -2.0 * idt;
+  const double c_da = 12.0 * idt3, c_j = 6.0 * idt2;
+  const double x_s = dt2 * dt2 * (1.0 / 24.0), x_c = dt3 * dt2 * (1.0 / 120.0);
+  const double v_s = dt3 * (1.0 / 6.0), v_c = dt2 * dt2 * (1.0 / 24.0);
   double a2e[3], a3e[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -312,11 +350,13 @@ __device__ __forceinline__ void correct_vals(
     const double vp = st.v[c] + dt * (a0 + h2 * j0);
     const double an = an3[c], jn = jn3[c];
     const double da = a0 - an;
-    // second and third derivatives of a at the start of the step
-    const double snap = (-6.0 * da - dt * (4.0 * j0 + 2.0 * jn)) * idt2;
-    const double crackle = (12.0 * da + 6.0 * dt * (j0 + jn)) * idt3;
-    x[3 * i + c] = xp + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
-    v[3 * i + c] = vp + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
+    // second and third derivatives of a at the start of the step:
+    // snap = (-6 da - dt (4 j0 + 2 jn)) / dt^2, crackle = (12 da + 6 dt (j0 + jn)) / dt^3
+    const double snap = s_da * da + (s_j0 * j0 + s_jn * jn);
+    const double crackle = c_da * da + c_j * (j0 + jn);
+    // x += dt^4 snap / 24 + dt^5 crackle / 120, v += dt^3 snap / 6 + dt^4 crackle / 24
+    x[3 * i + c] = xp + (x_s * snap + x_c * crackle);
+    v[3 * i + c] = vp + (v_s * snap + v_c * crackle);
     a[3 * i + c] = an;
     jk[3 * i + c] = jn;
     a2e[c] = snap + crackle * dt;
