@@ -93,6 +93,10 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
     float2 *s_f = reinterpret_cast<float2 *>(srec + NARR * B.cap);  // bi x 6 sums
     const double dt = B.init_only ? 0.0 : B.dt;
     const int nsteps = B.init_only ? 1 : B.nsteps;
+    // corrector coefficients of the shared step (dt a power of two: exact;
+    // the host gives 1/dt^2, 1/dt^3)
+    const dev::HermCoef K =
+        dev::herm_coef(dt, 0.5 * dt, dt * (1.0 / 3.0), dt * dt, dt * dt * dt, B.idt2, B.idt3);
 
     for (int step = 0; step < nsteps; ++step) {
       for (int p = tid; p < n; p += NT) {
@@ -234,24 +238,15 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
               B.jk[3 * gi + k] = B.G * o[3 + k];
             }
           } else {
-            double xp[3], vp[3];
-            bpredict(B.x, B.v, B.a, B.jk, gi, dt, xp, vp);
-            const double dt2 = dt * dt, dt3 = dt2 * dt;
-            // dt is a power of two: the host's exact reciprocals (an FP64
-            // divide costs ~600 cycles of latency on this part)
-            const double idt2 = B.idt2, idt3 = B.idt3;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-              const double a0 = B.a[3 * gi + k], j0v = B.jk[3 * gi + k];
-              const double an = B.G * o[k], jn = B.G * o[3 + k];
-              const double da = a0 - an;
-              const double snap = (-6.0 * da - dt * (4.0 * j0v + 2.0 * jn)) * idt2;
-              const double crackle = (12.0 * da + 6.0 * dt * (j0v + jn)) * idt3;
-              B.x[3 * gi + k] =
-                  xp[k] + dt2 * dt2 * (snap * (1.0 / 24.0) + dt * crackle * (1.0 / 120.0));
-              B.v[3 * gi + k] = vp[k] + dt3 * (snap * (1.0 / 6.0) + dt * crackle * (1.0 / 24.0));
-              B.a[3 * gi + k] = an;
-              B.jk[3 * gi + k] = jn;
+              double x1, v1, a2, a3;
+              dev::herm_component(K, B.x[3 * gi + k], B.v[3 * gi + k], B.a[3 * gi + k],
+                                  B.jk[3 * gi + k], B.G * o[k], B.G * o[3 + k], x1, v1, a2, a3);
+              B.x[3 * gi + k] = x1;
+              B.v[3 * gi + k] = v1;
+              B.a[3 * gi + k] = B.G * o[k];
+              B.jk[3 * gi + k] = B.G * o[3 + k];
             }
           }
         }

@@ -283,6 +283,59 @@ __device__ __forceinline__ double pow2(int k) {
   return __longlong_as_double(static_cast<long long>(1023 + k) << 52);
 }
 
+// Coefficients of the Hermite corrector for one step dt, shared by the three
+// components (each FP64 instruction counts on this part: a scheduler
+// retires one FP64 warp instruction per ~68 cycles, whatever the number of
+// active lanes).  For a power-of-two dt every coefficient is exact.
+struct HermCoef {
+  double dt, h2, h3;            // dt, dt/2, dt/3 (predictor)
+  double s_da, s_j0, s_jn;      // snap = s_da da + s_j0 j0 + s_jn jn
+  double c_da, c_j;             // crackle = c_da da + c_j (j0 + jn)
+  double x_s, x_c, v_s, v_c;    // dt^4/24, dt^5/120, dt^3/6, dt^4/24
+};
+
+__device__ __forceinline__ HermCoef herm_coef(double dt, double h2, double h3, double dt2,
+                                              double dt3, double idt2, double idt3) {
+  HermCoef K;
+  const double idt = dt * idt2;  // 1/dt
+  K.dt = dt;
+  K.h2 = h2;
+  K.h3 = h3;
+  K.s_da = -6.0 * idt2;
+  K.s_j0 = -4.0 * idt;
+  K.s_jn = -2.0 * idt;
+  K.c_da = 12.0 * idt3;
+  K.c_j = 6.0 * idt2;
+  K.x_s = dt2 * dt2 * (1.0 / 24.0);
+  K.x_c = dt3 * dt2 * (1.0 / 120.0);
+  K.v_s = dt3 * (1.0 / 6.0);
+  K.v_c = dt2 * dt2 * (1.0 / 24.0);
+  return K;
+}
+
+// One component of the Hermite-4 step from (x0, v0, a0, j0) with the new
+// force (an, jn): the predictor (the expression of predict_pos_vel), the
+// second and third derivatives of a at the start of the step,
+//   snap = (-6 da - dt (4 j0 + 2 jn)) / dt^2,
+//   crackle = (12 da + 6 dt (j0 + jn)) / dt^3,   da = a0 - an,
+// the corrected x1 = x_p + dt^4 snap / 24 + dt^5 crackle / 120 and
+// v1 = v_p + dt^3 snap / 6 + dt^4 crackle / 24, and the derivatives at the
+// end of the step for the step criterion, a2 = snap + dt crackle, a3 = crackle.
+__device__ __forceinline__ void herm_component(const HermCoef &K, double x0, double v0,
+                                               double a0, double j0, double an, double jn,
+                                               double &x1, double &v1, double &a2,
+                                               double &a3) {
+  const double xp = x0 + K.dt * (v0 + K.h2 * (a0 + K.h3 * j0));
+  const double vp = v0 + K.dt * (a0 + K.h2 * j0);
+  const double da = a0 - an;
+  const double snap = K.s_da * da + (K.s_j0 * j0 + K.s_jn * jn);
+  const double crackle = K.c_da * da + K.c_j * (j0 + jn);
+  x1 = xp + (K.x_s * snap + K.x_c * crackle);
+  v1 = vp + (K.v_s * snap + K.v_c * crackle);
+  a2 = snap + crackle * K.dt;
+  a3 = crackle;
+}
+
 // State of one particle as the corrector reads it (loaded ahead of the
 // corrector so that the loads overlap other work).
 struct PState {
@@ -333,34 +386,17 @@ __device__ __forceinline__ void correct_vals(
     idt2 = 1.0 / dt2;
     idt3 = 1.0 / dt3;
   }
-  // per-particle coefficients, shared by the three components (each FP64
-  // instruction counts on this part: a single warp retires one every ~70
-  // cycles on a dependent chain)
-  const double idt = dt * idt2;  // 1/dt, exact for a power-of-two step
-  const double s_da = -6.0 * idt2, s_j0 = -4.0 * idt, s_jn = -2.0 * idt;
-  const double c_da = 12.0 * idt3, c_j = 6.0 * idt2;
-  const double x_s = dt2 * dt2 * (1.0 / 24.0), x_c = dt3 * dt2 * (1.0 / 120.0);
-  const double v_s = dt3 * (1.0 / 6.0), v_c = dt2 * dt2 * (1.0 / 24.0);
+  const HermCoef K = herm_coef(dt, h2, h3, dt2, dt3, idt2, idt3);
   double a2e[3], a3e[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double a0 = st.a[c], j0 = st.j[c];
-    // predictor (the same expression as predict_pos_vel)
-    const double xp = st.x[c] + dt * (st.v[c] + h2 * (a0 + h3 * j0));
-    const double vp = st.v[c] + dt * (a0 + h2 * j0);
-    const double an = an3[c], jn = jn3[c];
-    const double da = a0 - an;
-    // second and third derivatives of a at the start of the step:
-    // snap = (-6 da - dt (4 j0 + 2 jn)) / dt^2, crackle = (12 da + 6 dt (j0 + jn)) / dt^3
-    const double snap = s_da * da + (s_j0 * j0 + s_jn * jn);
-    const double crackle = c_da * da + c_j * (j0 + jn);
-    // x += dt^4 snap / 24 + dt^5 crackle / 120, v += dt^3 snap / 6 + dt^4 crackle / 24
-    x[3 * i + c] = xp + (x_s * snap + x_c * crackle);
-    v[3 * i + c] = vp + (v_s * snap + v_c * crackle);
-    a[3 * i + c] = an;
-    jk[3 * i + c] = jn;
-    a2e[c] = snap + crackle * dt;
-    a3e[c] = crackle;
+    double x1, v1;
+    herm_component(K, st.x[c], st.v[c], st.a[c], st.j[c], an3[c], jn3[c], x1, v1, a2e[c],
+                   a3e[c]);
+    x[3 * i + c] = x1;
+    v[3 * i + c] = v1;
+    a[3 * i + c] = an3[c];
+    jk[3 * i + c] = jn3[c];
   }
   t_tick[i] = t_next;
   if (block_steps) {
