@@ -275,8 +275,11 @@ nb_status nb_batched_run_per_cluster(nb_batch *b, int64_t nsteps);
 nb_status nb_batched_set_tuning(nb_batch *b, int32_t variant,
                                 int32_t steps_per_launch, int32_t grid_ctas,
                                 int32_t use_graph);
+/* Shape of batched variant v: precision, i-particles per thread, threads
+ * per CTA, and 1 if two i-particles share each packed FP32x2 instruction.
+ * Any output may be NULL; NB_ERR_INVALID_ARG past the last variant. */
 nb_status nb_batched_variant_info(int32_t v, int32_t *precision, int32_t *ipt,
-                                  int32_t *threads);
+                                  int32_t *threads, int32_t *packed);
 
 /* Per-cluster FP64 kinetic and softened potential energy into host arrays
  * of n_clusters entries (either may be NULL).  Synchronises. */

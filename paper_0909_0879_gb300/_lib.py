@@ -75,7 +75,7 @@ SIGNATURES = [
     ("nb_batched_run", C.c_int, [_vp, _i64]),
     ("nb_batched_run_per_cluster", C.c_int, [_vp, _i64]),
     ("nb_batched_set_tuning", C.c_int, [_vp, _i32, _i32, _i32, _i32]),
-    ("nb_batched_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32)]),
+    ("nb_batched_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     ("nb_batched_energy", C.c_int, [_vp, _vp, _vp]),
     ("nb_batched_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("nb_batched_sync", C.c_int, [_vp]),
@@ -376,15 +376,15 @@ class NBody:
 
 def batched_variant_info(v: int):
     L = load()
-    p, i, t = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(L.nb_batched_variant_info(v, C.byref(p), C.byref(i), C.byref(t)))
-    return {"precision": p.value, "ipt": i.value, "threads": t.value}
+    p, i, t, k = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(L.nb_batched_variant_info(v, C.byref(p), C.byref(i), C.byref(t), C.byref(k)))
+    return {"precision": p.value, "ipt": i.value, "threads": t.value, "packed": k.value}
 
 
 def num_batched_variants() -> int:
     v = 0
     L = load()
-    while L.nb_batched_variant_info(v, None, None, None) == NB_OK:
+    while L.nb_batched_variant_info(v, None, None, None, None) == NB_OK:
         v += 1
     return v
 

@@ -66,8 +66,13 @@ __device__ __forceinline__ void bpredict(const double *x, const double *v, const
   }
 }
 
-template <int PREC, int IPT, int NT, int MASK>
+template <int PREC, int IPT, int NT, int MASK, int PACK>
 __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs B) {
+  using V = typename std::conditional<PACK != 0, float2, float>::type;
+  using O = dev::VOps<V>;
+  constexpr int W = O::W;
+  static_assert(IPT % W == 0, "packed kernels need an even IPT");
+  constexpr int NQ = IPT / W;
   constexpr int NARR = PREC ? 3 : 2;
   extern __shared__ __align__(16) float4 srec[];
   __shared__ int s_item;
@@ -115,84 +120,89 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
       }
       __syncthreads();
       for (int i0 = 0; i0 < n; i0 += bi) {
-        float xh[IPT][3], xl[IPT][3], vi[IPT][3];
+        // i-data negated, so that every difference is an addition (a - b and
+        // a + (-b) round alike); two i-particles per packed FP32x2 lane
+        // pair when PACK (per-lane IEEE rounding: the same bits as scalar)
+        V nxh[NQ][3], nxl[NQ][3], nvi[NQ][3];
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
           const int i = i0 + g + q * ng;
           const int ii = i < n ? i : 0;
           const float4 h = s_hi[ii];
           const float4 w = s_v[ii];
-          xh[q][0] = h.x; xh[q][1] = h.y; xh[q][2] = h.z;
-          vi[q][0] = w.x; vi[q][1] = w.y; vi[q][2] = w.z;
-          if (PREC) {
-            const float4 l = s_lo[ii];
-            xl[q][0] = l.x; xl[q][1] = l.y; xl[q][2] = l.z;
-          } else {
-            xl[q][0] = xl[q][1] = xl[q][2] = 0.f;
-          }
+          const float4 l = PREC ? s_lo[ii] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const int qq = q / W, wl = q % W;
+          O::set(nxh[qq][0], wl, -h.x); O::set(nxh[qq][1], wl, -h.y); O::set(nxh[qq][2], wl, -h.z);
+          O::set(nxl[qq][0], wl, -l.x); O::set(nxl[qq][1], wl, -l.y); O::set(nxl[qq][2], wl, -l.z);
+          O::set(nvi[qq][0], wl, -w.x); O::set(nvi[qq][1], wl, -w.y); O::set(nvi[qq][2], wl, -w.z);
         }
-        float ah[IPT][3], al[IPT][3], p1[IPT][3], p2[IPT][3];
+        float ah[IPT][3], al[IPT][3];
+        V p1[NQ][3], p2[NQ][3];
 #pragma unroll
         for (int q = 0; q < IPT; ++q)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) ah[q][k] = al[q][k] = p1[q][k] = p2[q][k] = 0.f;
+          for (int k = 0; k < 3; ++k) ah[q][k] = al[q][k] = 0.f;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) p1[q][k] = p2[q][k] = O::bc(0.f);
+        const V veps2 = O::bc(eps2);
         for (int j0 = r; j0 < n; j0 += kBatchFold * tpi) {
           const int jend = min(n, j0 + kBatchFold * tpi);
-          float pa[IPT][3];
+          V pa[NQ][3];
 #pragma unroll
-          for (int q = 0; q < IPT; ++q)
+          for (int q = 0; q < NQ; ++q)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) pa[q][k] = 0.f;
+            for (int k = 0; k < 3; ++k) pa[q][k] = O::bc(0.f);
 #pragma unroll 4
           for (int j = j0; j < jend; j += tpi) {
             const float4 hj = s_hi[j];
             const float4 wj = s_v[j];
-            float4 lj;
+            float4 lj = make_float4(0.f, 0.f, 0.f, 0.f);
             if (PREC) lj = s_lo[j];
+            const V xj = O::bc(hj.x), yj = O::bc(hj.y), zj = O::bc(hj.z), mj = O::bc(hj.w);
+            const V vxj = O::bc(wj.x), vyj = O::bc(wj.y), vzj = O::bc(wj.z);
 #pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-              float dx, dy, dz;
+            for (int q = 0; q < NQ; ++q) {
+              V dx, dy, dz;
               if (PREC) {
-                dx = (hj.x - xh[q][0]) + (lj.x - xl[q][0]);
-                dy = (hj.y - xh[q][1]) + (lj.y - xl[q][1]);
-                dz = (hj.z - xh[q][2]) + (lj.z - xl[q][2]);
+                dx = O::add(O::add(xj, nxh[q][0]), O::add(O::bc(lj.x), nxl[q][0]));
+                dy = O::add(O::add(yj, nxh[q][1]), O::add(O::bc(lj.y), nxl[q][1]));
+                dz = O::add(O::add(zj, nxh[q][2]), O::add(O::bc(lj.z), nxl[q][2]));
               } else {
-                dx = hj.x - xh[q][0];
-                dy = hj.y - xh[q][1];
-                dz = hj.z - xh[q][2];
+                dx = O::add(xj, nxh[q][0]);
+                dy = O::add(yj, nxh[q][1]);
+                dz = O::add(zj, nxh[q][2]);
               }
-              const float ux = wj.x - vi[q][0];
-              const float uy = wj.y - vi[q][1];
-              const float uz = wj.z - vi[q][2];
-              const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-              float rinv;
-              if (MASK)
-                rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-              else
-                rinv = rsqrtf(r2);
-              const float rinv2 = rinv * rinv;
-              const float mr3 = (hj.w * rinv) * rinv2;
-              const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-              const float cc = (rv * rinv2) * mr3;
-              pa[q][0] = fmaf(mr3, dx, pa[q][0]);
-              pa[q][1] = fmaf(mr3, dy, pa[q][1]);
-              pa[q][2] = fmaf(mr3, dz, pa[q][2]);
-              p1[q][0] = fmaf(mr3, ux, p1[q][0]);
-              p1[q][1] = fmaf(mr3, uy, p1[q][1]);
-              p1[q][2] = fmaf(mr3, uz, p1[q][2]);
-              p2[q][0] = fmaf(cc, dx, p2[q][0]);
-              p2[q][1] = fmaf(cc, dy, p2[q][1]);
-              p2[q][2] = fmaf(cc, dz, p2[q][2]);
+              const V ux = O::add(vxj, nvi[q][0]);
+              const V uy = O::add(vyj, nvi[q][1]);
+              const V uz = O::add(vzj, nvi[q][2]);
+              const V r2 = O::fma(dx, dx, O::fma(dy, dy, O::fma(dz, dz, veps2)));
+              const V rinv = O::template rsq<MASK>(r2);
+              const V rinv2 = O::mul(rinv, rinv);
+              const V mr3 = O::mul(O::mul(mj, rinv), rinv2);
+              const V rv = O::fma(dx, ux, O::fma(dy, uy, O::mul(dz, uz)));
+              const V cc = O::mul(O::mul(rv, rinv2), mr3);
+              pa[q][0] = O::fma(mr3, dx, pa[q][0]);
+              pa[q][1] = O::fma(mr3, dy, pa[q][1]);
+              pa[q][2] = O::fma(mr3, dz, pa[q][2]);
+              p1[q][0] = O::fma(mr3, ux, p1[q][0]);
+              p1[q][1] = O::fma(mr3, uy, p1[q][1]);
+              p1[q][2] = O::fma(mr3, uz, p1[q][2]);
+              p2[q][0] = O::fma(cc, dx, p2[q][0]);
+              p2[q][1] = O::fma(cc, dy, p2[q][1]);
+              p2[q][2] = O::fma(cc, dz, p2[q][2]);
             }
           }
 #pragma unroll
           for (int q = 0; q < IPT; ++q)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
+              const float x = O::lane(pa[q / W][k], q % W);
               if (PREC)
-                bds_add(ah[q][k], al[q][k], pa[q][k]);
+                bds_add(ah[q][k], al[q][k], x);
               else
-                ah[q][k] += pa[q][k];
+                ah[q][k] += x;
             }
         }
 #pragma unroll
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
           for (int k = 0; k < 3; ++k) {
             oh[k] = ah[q][k];
             ol[k] = al[q][k];
-            oh[3 + k] = fmaf(-3.f, p2[q][k], p1[q][k]);
+            oh[3 + k] = fmaf(-3.f, O::lane(p2[q / W][k], q % W), O::lane(p1[q / W][k], q % W));
             ol[3 + k] = 0.f;
           }
           for (int off = 1; off < tpi; off <<= 1)
@@ -299,14 +309,20 @@ __global__ void batched_energy_kernel(int32_t n_clusters, const int64_t *__restr
 
 using BKernel = void (*)(const BatchArgs);
 struct BEntry {
-  int prec, ipt, threads, mask;
+  int prec, ipt, threads, mask, pack;
   BKernel fn;
 };
-#define NB_BV(P, I, T, M) BEntry{P, I, T, M, &batched_hermite_kernel<P, I, T, M>}
+#define NB_BV(P, I, T, M) BEntry{P, I, T, M, 0, &batched_hermite_kernel<P, I, T, M, 0>}
+#define NB_BVP(P, I, T, M) BEntry{P, I, T, M, 1, &batched_hermite_kernel<P, I, T, M, 1>}
+// Index order is part of the tuning interface.
 const BEntry kBTable[] = {
     NB_BV(1, 2, 256, 0), NB_BV(1, 1, 256, 0), NB_BV(1, 2, 128, 0), NB_BV(1, 1, 128, 0),
     NB_BV(0, 2, 256, 0), NB_BV(0, 1, 256, 0), NB_BV(0, 2, 128, 0), NB_BV(0, 1, 128, 0),
     NB_BV(1, 2, 256, 1), NB_BV(0, 2, 256, 1),
+    // two i-particles per packed FP32x2 instruction (bit-identical to the
+    // scalar shape of the same IPT and threads)
+    NB_BVP(1, 2, 128, 0), NB_BVP(1, 2, 256, 0), NB_BVP(1, 4, 128, 0),
+    NB_BVP(0, 2, 128, 0), NB_BVP(0, 2, 256, 0), NB_BVP(0, 4, 128, 0),
 };
 constexpr int kNumBVariants = sizeof(kBTable) / sizeof(kBTable[0]);
 
@@ -556,11 +572,13 @@ nb_status nb_batched_set_tuning(nb_batch *b, int32_t variant, int32_t steps_per_
   return NB_OK;
 }
 
-nb_status nb_batched_variant_info(int32_t v, int32_t *precision, int32_t *ipt, int32_t *threads) {
+nb_status nb_batched_variant_info(int32_t v, int32_t *precision, int32_t *ipt, int32_t *threads,
+                                  int32_t *packed) {
   if (v < 0 || v >= kNumBVariants) return bfail(NB_ERR_INVALID_ARG, "unknown batched variant");
   if (precision) *precision = kBTable[v].prec;
   if (ipt) *ipt = kBTable[v].ipt;
   if (threads) *threads = kBTable[v].threads;
+  if (packed) *packed = kBTable[v].pack;
   return NB_OK;
 }
 

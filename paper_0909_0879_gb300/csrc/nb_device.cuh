@@ -29,6 +29,48 @@ __device__ __forceinline__ void predict_pos_vel(const double *x, const double *v
   }
 }
 
+// Scalar and packed (two lanes per instruction, sm_100+ f32x2) FP32 ops
+// with identical per-lane IEEE round-to-nearest results, so the scalar and
+// packed kernels give bit-identical sums.
+template <class V>
+struct VOps;
+template <>
+struct VOps<float> {
+  static constexpr int W = 1;
+  static __device__ __forceinline__ float bc(float s) { return s; }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+  template <int MASK>
+  static __device__ __forceinline__ float rsq(float r2) {
+    if (MASK) return r2 > 0.f ? rsqrtf(r2) : 0.f;
+    return rsqrtf(r2);
+  }
+  static __device__ __forceinline__ float lane(float a, int) { return a; }
+  static __device__ __forceinline__ void set(float &a, int, float s) { a = s; }
+};
+template <>
+struct VOps<float2> {
+  static constexpr int W = 2;
+  static __device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+  }
+  template <int MASK>
+  static __device__ __forceinline__ float2 rsq(float2 r2) {
+    return make_float2(VOps<float>::rsq<MASK>(r2.x), VOps<float>::rsq<MASK>(r2.y));
+  }
+  static __device__ __forceinline__ float lane(float2 a, int w) { return w ? a.y : a.x; }
+  static __device__ __forceinline__ void set(float2 &a, int w, float s) {
+    if (w)
+      a.y = s;
+    else
+      a.x = s;
+  }
+};
+
 // FP64 <-> FP32 conversions on the integer pipe.  This part's FP64 pipe
 // retires one warp instruction per ~68 cycles per scheduler and a
 // conversion occupies it like an FMA, while these are a dozen integer

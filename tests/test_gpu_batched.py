@@ -154,3 +154,38 @@ def test_batched_every_variant(nb, oracle_mod):
             xo, ao = ref[c]
             tol = rel * np.linalg.norm(ao, axis=1) * (10 * 2.0**-8) ** 2 / 2 + 1e-12
             assert np.all(np.linalg.norm(st["x"][s] - xo, axis=1) <= tol), (var, c)
+
+
+def test_batched_packed_variants_bitwise_equal_scalar(nb):
+    """Two i-particles per packed FP32x2 instruction round lane by lane as
+    the scalar instructions do: each packed shape gives the bits of the
+    scalar shape with the same precision, IPT and threads."""
+    off, m, x, v = make_clusters(12, 11)
+    infos = [nb.batched_variant_info(k) for k in range(nb.num_batched_variants())]
+    pairs = []
+    for k, a in enumerate(infos):
+        if not a["packed"]:
+            continue
+        for j, b in enumerate(infos):
+            if (not b["packed"] and b["precision"] == a["precision"] and b["ipt"] == a["ipt"]
+                    and b["threads"] == a["threads"]):
+                pairs.append((k, j, a["precision"]))
+    assert pairs
+    compared = 0
+    for k, j, p in pairs:
+        res = []
+        for var in (k, j):
+            with nb.Batch(off, m, x, v, eps=1e-3, lev_shared=8,
+                          precision="ds" if p else "fp32") as b:
+                try:
+                    b.set_tuning(var, 5, 0, True)
+                except nb.NBodyError:
+                    break  # an eps == 0 (masked) shape: not for this batch
+                b.run(10)
+                res.append(b.get_state())
+        if len(res) < 2:
+            continue
+        compared += 1
+        for key in res[0]:
+            assert np.array_equal(res[0][key], res[1][key]), (k, j, key)
+    assert compared >= 4
