@@ -308,17 +308,30 @@ class NBody:
         _check(self._L.nb_energy(self._h, C.byref(k), C.byref(w), C.byref(e)))
         return k.value, w.value, e.value
 
-    def get_state(self, want=("x", "v", "a", "jerk", "t_tick", "lev")):
+    _STATE_SPEC = {"x": (3, np.float64), "v": (3, np.float64), "a": (3, np.float64),
+                   "jerk": (3, np.float64), "t_tick": (0, np.int64), "lev": (0, np.int32)}
+
+    def get_state(self, want=("x", "v", "a", "jerk", "t_tick", "lev"), out=None):
+        """Copy the state to host arrays.  With out (a dict of C-contiguous
+        arrays of the right shapes and dtypes, e.g. in pinned memory, as a
+        previous get_state returned) the copies land in those arrays and no
+        host memory is allocated or first touched."""
         n = self.n
-        out = {}
         bufs = {}
-        for key in ("x", "v", "a", "jerk"):
-            if key in want:
-                bufs[key] = out[key] = np.zeros((n, 3))
-        if "t_tick" in want:
-            bufs["t_tick"] = out["t_tick"] = np.zeros(n, dtype=np.int64)
-        if "lev" in want:
-            bufs["lev"] = out["lev"] = np.zeros(n, dtype=np.int32)
+        res = {}
+        for key, (w, dt) in self._STATE_SPEC.items():
+            if key not in want:
+                continue
+            shape = (n, w) if w else (n,)
+            if out is not None and key in out:
+                a = out[key]
+                if a.shape != shape or a.dtype != dt or not a.flags.c_contiguous:
+                    raise ValueError(f"out[{key!r}] must be a C-contiguous {dt.__name__} "
+                                     f"array of shape {shape}")
+            else:
+                a = np.zeros(shape, dtype=dt)
+            bufs[key] = res[key] = a
+        out = res
         p = {k: (bufs[k].ctypes.data if k in bufs else None)
              for k in ("x", "v", "a", "jerk", "t_tick", "lev")}
         _check(self._L.nb_get_state(self._h, p["x"], p["v"], p["a"], p["jerk"], p["t_tick"],

@@ -62,9 +62,20 @@ namespace {
                   __LINE__);                                                 \
   } while (0)
 
+// True when no value is an infinity or a NaN (exponent field all ones),
+// checked on the bit patterns in blocks so that the loop vectorises.
 bool finite_all(const double *p, int64_t cnt) {
-  for (int64_t i = 0; i < cnt; ++i)
-    if (!std::isfinite(p[i])) return false;
+  constexpr uint64_t kExp = 0x7ff0000000000000ull;
+  for (int64_t b = 0; b < cnt; b += 4096) {
+    const int64_t e = b + 4096 < cnt ? b + 4096 : cnt;
+    uint64_t bad = 0;
+    for (int64_t i = b; i < e; ++i) {
+      uint64_t u;
+      std::memcpy(&u, p + i, sizeof u);
+      bad |= static_cast<uint64_t>((u & kExp) == kExp);
+    }
+    if (bad) return false;
+  }
   return true;
 }
 
@@ -996,7 +1007,7 @@ nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double
     return fail(NB_ERR_INVALID_ARG, "non-finite state");
   for (int64_t i = 0; i < n; ++i) {
     if (lev[i] < 0 || lev[i] > kTicksLog2 || t_tick[i] < 0 ||
-        t_tick[i] % (int64_t(1) << (kTicksLog2 - lev[i])) != 0)
+        (t_tick[i] & ((int64_t(1) << (kTicksLog2 - lev[i])) - 1)) != 0)
       return fail(NB_ERR_INVALID_ARG, "particle %lld: level or tick invalid", (long long)i);
   }
   const size_t n3 = 3 * static_cast<size_t>(n) * sizeof(double);
