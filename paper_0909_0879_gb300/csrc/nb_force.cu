@@ -26,11 +26,14 @@
 //  * Work decomposition: the (i-block, j-tile) space is cut into equal
 //    contiguous ranges, one per persistent CTA (a "stream-K" split), so every
 //    active-list length fills the GPU evenly.  An i-block whose j-range spans
-//    several CTAs gets FP64 partial sums that a fix-up kernel adds in
-//    ascending CTA order: results are deterministic.
+//    several CTAs gets split-precision (hi, lo) partial sums that a fix-up
+//    adds in a fixed order on the FP32 pipe: results are deterministic.
 //  * Several threads per i-particle (TPI > 1) split a tile's j-range inside
-//    the CTA for short active lists; their sums meet by a warp-shuffle
-//    butterfly (commutative pairwise adds, identical on every lane).
+//    the CTA for short active lists; their split-precision sums meet by a
+//    warp-shuffle butterfly (commutative pair additions, identical on every
+//    lane).
+//  * FP64 only where a value leaves the kernel (the FP64 pipe of this part
+//    retires one warp instruction per ~68 cycles per scheduler).
 #include "nb_device.cuh"
 
 #include <algorithm>
