@@ -9,9 +9,9 @@
  *   w_ij = v_j - v_i, s^2 = |d_ij|^2 + eps^2
  * for a list of active i-particles against all j-particles, on one GPU, and
  * advances the system with the 4th-order Hermite predictor-corrector and
- * power-of-two block time steps (the paper's "individual time steps",
- * Sec. 2, strategy (ii); the Hermite scheme itself is Makino & Aarseth 1992
- * and is not printed in the paper).
+ * power-of-two block time steps (the paper's individual per-particle time
+ * steps, Sec. 2, strategy (ii); the Hermite scheme itself is Makino &
+ * Aarseth 1992 and is not printed in the paper).
  *
  * Conventions (every entry point):
  *  - Every call returns nb_status; NB_OK is 0.  On error a message is kept
