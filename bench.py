@@ -689,12 +689,18 @@ def run_nsweep(args):
         fv = torch.tensor(v, dtype=torch.float32, device=dev)
         fa = torch.empty_like(fx)
         _lib.lf_forward(n, fm, fx, fv, fa, 1, 2.0**-10, None, eps=eps)
-        e0, e1 = _events(torch)
-        e0.record()
-        _lib.lf_forward(n, fm, fx, fv, fa, steps, 2.0**-10, None, eps=eps)
-        e1.record()
-        torch.cuda.synchronize()
-        row["leapfrog_fp32_s"] = e0.elapsed_time(e1) / 1e3 / steps
+        # a forward call starts with one force evaluation before its first
+        # step: time a call of 0 steps and one of `steps`, and divide the
+        # difference, so each step carries exactly its one evaluation
+        ms = []
+        for k in (0, steps):
+            e0, e1 = _events(torch)
+            e0.record()
+            _lib.lf_forward(n, fm, fx, fv, fa, k, 2.0**-10, None, eps=eps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        row["leapfrog_fp32_s"] = (ms[1] - ms[0]) / 1e3 / steps
         # CPU baseline: oracle force + jerk per i-particle, about 0.5 s a point
         rng = np.random.default_rng(8)
         for threads in (cores, 1):

@@ -81,13 +81,13 @@ __global__ void __launch_bounds__(kLfT) lf_acc_kernel(int64_t n, const float *__
 }
 
 // Wide shape for large N: each thread holds 4 i-particles, two per packed
-// FP32x2 instruction (per-lane IEEE rounding), and walks every j of a
-// shared-memory tile (1,024 i-particles per CTA); the next tile is read into
-// registers while the current one is summed, and each tile's sum is added to
-// the running total so that no FP32 sum runs over more than 256 terms plus
-// one term per tile.
+// FP32x2 instruction (per-lane IEEE rounding), and TPI threads share an
+// i-particle group, splitting every shared-memory tile's j-range (their sums
+// meet by a warp-shuffle butterfly); 1,024 / TPI i-particles per CTA.  The
+// next tile is read into registers while the current one is summed, and each
+// tile's sum is added to the running total, so no FP32 sum runs over more
+// than 256 / TPI terms plus one term per tile.
 constexpr int kLfWideIpt = 4;
-constexpr int kLfWideI = kLfT * kLfWideIpt;  // i-particles per CTA
 
 template <int MASK>
 __device__ __forceinline__ float2 lf_rsq2(float2 s2) {
@@ -97,19 +97,21 @@ __device__ __forceinline__ float2 lf_rsq2(float2 s2) {
   return r;
 }
 
-template <int MASK>
+template <int MASK, int TPI>
 __global__ void __launch_bounds__(kLfT) lf_acc_wide_kernel(int64_t n, const float *__restrict__ x,
                                                            const float *__restrict__ m,
                                                            float eps2, float G,
                                                            float *__restrict__ acc) {
   __shared__ float4 sj[kLfJT];
   constexpr int NQ = kLfWideIpt / 2;
-  const int tid = threadIdx.x;
+  constexpr int NG = kLfT / TPI;            // i-particle groups per CTA
+  constexpr int BI = NG * kLfWideIpt;       // i-particles per CTA
+  const int tid = threadIdx.x, g = tid / TPI, r = tid % TPI;
   float2 nx[NQ], ny[NQ], nz[NQ];  // negated i-positions, two particles per pair
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kLfWideI + tid + (2 * q) * kLfT;
-    const int64_t i1 = i0 + kLfT;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * BI + g + (2 * q) * NG;
+    const int64_t i1 = i0 + NG;
     const int64_t a0 = i0 < n ? i0 : 0, a1 = i1 < n ? i1 : 0;
     nx[q] = make_float2(-x[3 * a0], -x[3 * a1]);
     ny[q] = make_float2(-x[3 * a0 + 1], -x[3 * a1 + 1]);
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kLfT) lf_acc_wide_kernel(int64_t n, const floa
 #pragma unroll
     for (int q = 0; q < NQ; ++q) px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
 #pragma unroll 8
-    for (int t = 0; t < kLfJT; ++t) {
+    for (int t = r; t < kLfJT; t += TPI) {
       const float4 qj = sj[t];
       const float2 xj = make_float2(qj.x, qj.x), yj = make_float2(qj.y, qj.y);
       const float2 zj = make_float2(qj.z, qj.z), mj = make_float2(qj.w, qj.w);
@@ -156,10 +158,24 @@ __global__ void __launch_bounds__(kLfT) lf_acc_wide_kernel(int64_t n, const floa
       tz[q] = __fadd2_rn(tz[q], pz[q]);
     }
   }
+  if (TPI > 1) {
+#pragma unroll
+    for (int off = 1; off < TPI; off <<= 1)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        tx[q].x += __shfl_xor_sync(0xffffffffu, tx[q].x, off);
+        tx[q].y += __shfl_xor_sync(0xffffffffu, tx[q].y, off);
+        ty[q].x += __shfl_xor_sync(0xffffffffu, ty[q].x, off);
+        ty[q].y += __shfl_xor_sync(0xffffffffu, ty[q].y, off);
+        tz[q].x += __shfl_xor_sync(0xffffffffu, tz[q].x, off);
+        tz[q].y += __shfl_xor_sync(0xffffffffu, tz[q].y, off);
+      }
+  }
+  if (r != 0) return;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kLfWideI + tid + (2 * q) * kLfT;
-    const int64_t i1 = i0 + kLfT;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * BI + g + (2 * q) * NG;
+    const int64_t i1 = i0 + NG;
     if (i0 < n) {
       acc[3 * i0] = G * tx[q].x;
       acc[3 * i0 + 1] = G * ty[q].x;
@@ -264,23 +280,46 @@ struct LfCtx {
   const float *m;
   float eps2, G;
   int mask;
+  int sms;
   cudaStream_t s;
   int64_t launches;
 };
 
-// Large N (>= kLfWideMin) takes the wide shape; below it, the 8-threads-per-
-// particle shape keeps enough CTAs to fill the GPU (N = 4096: 128 CTAs).
-// Measured per evaluation (uniform sphere): N = 65536: 5.1 ms wide, 2.6 ms
-// narrow; 131072: 12.1 / 11.8; 262144: 45.4 / 46.8; 1048576: 614 / 742.
-constexpr int64_t kLfWideMin = 262144;
+// N >= kLfWideMin takes the wide shape; below it, the 8-threads-per-particle
+// shape keeps enough CTAs to fill the GPU (N = 4096: 128 CTAs).
+constexpr int64_t kLfWideMin = 65536;
+
+// Threads per i-particle group of the wide shape, 4 or 8.  CTAs take the
+// same time, so an SM's share is ceil(grid / SMs) CTAs run one after
+// another; 8 threads halve the i-particles per CTA, and are taken where the
+// grid then divides more evenly over the SMs (N = 131072 on 152 SMs: 3.4
+// against 6.7 CTAs per SM).
+int lf_wide_tpi(int64_t n, int sms) {
+  auto balance = [&](int tpi) {
+    const int64_t bi = kLfT / tpi * kLfWideIpt;
+    const int64_t grid = (n + bi - 1) / bi;
+    const int64_t rounds = (grid + sms - 1) / sms;
+    return static_cast<double>(grid) / static_cast<double>(rounds * sms);
+  };
+  return balance(8) > balance(4) + 0.01 ? 8 : 4;
+}
+
+template <int TPI>
+void launch_lf_wide(const LfCtx &C, const float *x, float *acc) {
+  constexpr int bi = kLfT / TPI * kLfWideIpt;
+  const unsigned grid = static_cast<unsigned>((C.n + bi - 1) / bi);
+  if (C.mask)
+    lf_acc_wide_kernel<1, TPI><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, C.eps2, C.G, acc);
+  else
+    lf_acc_wide_kernel<0, TPI><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, C.eps2, C.G, acc);
+}
 
 cudaError_t lf_acc(LfCtx &C, const float *x, float *acc) {
   if (C.n >= kLfWideMin) {
-    const unsigned grid = static_cast<unsigned>((C.n + kLfWideI - 1) / kLfWideI);
-    if (C.mask)
-      lf_acc_wide_kernel<1><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, C.eps2, C.G, acc);
+    if (lf_wide_tpi(C.n, C.sms) == 8)
+      launch_lf_wide<8>(C, x, acc);
     else
-      lf_acc_wide_kernel<0><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, C.eps2, C.G, acc);
+      launch_lf_wide<4>(C, x, acc);
   } else {
     const unsigned grid = static_cast<unsigned>((C.n + kLfI - 1) / kLfI);
     if (C.mask)
@@ -346,6 +385,12 @@ LfCtx make_ctx(int64_t n, const float *m, float eps, float G, void *stream) {
   C.eps2 = eps * eps;
   C.G = G;
   C.mask = eps == 0.f ? 1 : 0;
+  // A failed query leaves its error for the launch's error check to report.
+  int dev = 0;
+  C.sms = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&C.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (C.sms < 1) C.sms = 1;
   C.s = static_cast<cudaStream_t>(stream);
   C.launches = 0;
   return C;

@@ -55,15 +55,17 @@ def test_acc_and_vjp_kernels_match_oracle(torch_cuda, oracle_mod):
         assert rel_l2(gm.double().cpu().numpy(), rgm) < 1e-4
 
 
+@pytest.mark.parametrize("n", [65536, 131101, 262401])
 @pytest.mark.parametrize("eps", [1e-3, 0.0])
-def test_wide_acc_shape_large_n(torch_cuda, oracle_mod, eps):
-    """Large N takes the wide acceleration shape (4 particles per thread,
-    packed pairs): n = 262,401 (ragged) against the FP64 oracle on 512
-    sampled particles, same float32-rounded inputs."""
+def test_wide_acc_shape_large_n(torch_cuda, oracle_mod, eps, n):
+    """N >= 65,536 takes the wide acceleration shape (4 particles per
+    thread, packed pairs, 4 or 8 threads per particle group): the smallest
+    such N, and two ragged ones, n = 131,101 (8 threads per group on 152
+    SMs) and 262,401 (4 threads), against the FP64 oracle on 512 sampled
+    particles, same float32-rounded inputs."""
     torch = torch_cuda
     from paper_0909_0879_gb300 import _lib
 
-    n = 262401
     m, x, v = ics.plummer(n, 905)
     dx = torch.tensor(x, dtype=torch.float32, device="cuda")
     dm = torch.tensor(m, dtype=torch.float32, device="cuda")
