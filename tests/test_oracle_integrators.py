@@ -269,3 +269,63 @@ def test_leapfrog_adjoint_short_step_limit(oracle_mod):
     L, gx, gv, gm = oracle_mod.leapfrog_loss_grad(m, x, v, y, 1e-2, 1e-9, 1)
     assert np.abs(gx - 2 * (x - y)).max() < 1e-7
     assert np.abs(gm).max() < 1e-12
+
+
+# ------------------------------------------------ sixth-order symplectic
+
+
+def test_symplectic6_weights_order_conditions(oracle_mod):
+    """The seven weights of a symmetric composition of a symmetric
+    second-order step reach order 6 only if they sum to 1 (consistency)
+    and their third and fifth powers sum to 0 (the h^3 and h^5 error terms
+    of the base step cancel); the symmetry w_k = w_{6-k} removes the even
+    orders."""
+    w = np.array(oracle_mod.SYMPLECTIC6_WEIGHTS)
+    assert w.shape == (7,)
+    assert np.array_equal(w, w[::-1])
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert abs(np.sum(w**3)) < 1e-13
+    assert abs(np.sum(w**5)) < 1e-13
+
+
+def _kepler_errors(oracle_mod, order, ks, t_end=2.0, weights=None):
+    m, x, v = kepler_ic()
+    errs = []
+    for k in ks:
+        xf, _ = oracle_mod.symplectic(m, x, v, 0.0, t_end / k, k, order, weights=weights)
+        errs.append(np.linalg.norm((xf[1] - xf[0]) - kepler_relative_position(t_end)))
+    return errs
+
+
+def test_symplectic_convergence_orders_kepler(oracle_mod):
+    """eps = 0 two-body problem (e = 0.5) from pericentre to t = 2 against
+    Kepler's equation: halving dt divides the position error by ~2^2 for
+    the leapfrog and by ~2^6 for the seven-stage composition."""
+    e2 = _kepler_errors(oracle_mod, 2, (256, 512, 1024))
+    e6 = _kepler_errors(oracle_mod, 6, (32, 64, 128))
+    for errs, lo, hi in ((e2, 3.6, 4.4), (e6, 48.0, 80.0)):
+        r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+        assert lo < r1 < hi and lo < r2 < hi, (errs, r1, r2)
+    # with fewer force evaluations (64 steps x 7 against 512) the
+    # composition is far more accurate
+    assert e6[1] < 1e-2 * e2[1]
+
+
+def test_symplectic6_time_reversible(oracle_mod):
+    m, x, v = ics.plummer(32, 4)
+    x1, v1 = oracle_mod.symplectic(m, x, v, 1e-2, 1 / 64, 6, 6)
+    x2, v2 = oracle_mod.symplectic(m, x1, -v1, 1e-2, 1 / 64, 6, 6)
+    assert np.abs(x2 - x).max() < 1e-11 and np.abs(-v2 - v).max() < 1e-11
+
+
+def test_symplectic6_order_pin_catches_a_wrong_weight(oracle_mod):
+    """A weight off by one part in a thousand (the others renormalised so
+    the sum stays 1) leaves a second-order error term, which the
+    convergence pin above detects."""
+    w = list(oracle_mod.SYMPLECTIC6_WEIGHTS)
+    w[2] *= 1.001
+    w[4] = w[2]
+    w[3] = 1.0 - 2.0 * (w[0] + w[1] + w[2])
+    errs = _kepler_errors(oracle_mod, 6, (32, 64, 128), weights=w)
+    r = errs[1] / errs[2]
+    assert r < 8.0, (errs, r)
