@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--workload", default="king1m",
                    choices=["king1m", "shared1024", "block65536", "batched", "adjoint",
-                            "nsweep"],
+                            "nsweep", "symplectic"],
                    help="king1m is the headline; the others time the remaining workloads "
                         "and print their own JSON line")
     p.add_argument("--block-steps", type=int, default=0,
@@ -647,14 +647,90 @@ def run_adjoint(args):
     return 0
 
 
+def _time_symplectic(torch, s, order, dt, steps):
+    """Seconds per step of s.symplectic: the difference of a 0-step call
+    (which only evaluates the acceleration at the start) and a `steps`
+    call, so each step carries exactly its own force evaluations.  The
+    step's graph is captured by a 1-step call first."""
+    s.symplectic(order, dt, 1)
+    ms = []
+    for k in (0, steps):
+        e0, e1 = _events(torch)
+        e0.record()
+        s.symplectic(order, dt, k)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return (ms[1] - ms[0]) / 1e3 / steps
+
+
+def run_symplectic(args):
+    """The paper's symplectic integrators (Sec. 2.2) on its own test system
+    (Sec. 3): N = 65536 uniform sphere of radius 1, Salpeter masses, virial
+    ratio Q = 1, G = M = 1, eps = 0.1 (4 pi / 3 N)^(1/3).
+    Speed: per precision, particle layout and order, seconds per step and
+    interactions/s over 16 steps (CUDA events; the force evaluation a call
+    makes at its start is excluded); layouts are generation order (as the
+    paper's particles come) and nb_spatial_order (balanced bisection, which
+    lets the split-precision kernel take its tile-relative far field).
+    Accuracy (split precision, generation order): relative energy error at
+    t = 1/8 at equal force evaluations, sixth order with dt = 2^-7..2^-10
+    against the leapfrog with dt / 7."""
+    import torch
+
+    from paper_0909_0879_gb300 import _lib, metrics
+
+    n = args.n if args.n != N_DEFAULT else 65536
+    m, x, v = ics.uniform_sphere(n, 1006, Q=1.0, masses=ics.salpeter_masses(n, 1006))
+    eps = 0.1 * (4.0 * np.pi / (3.0 * n)) ** (1.0 / 3.0)
+    perm = _lib.spatial_order(x, 256)
+    layouts = {"generation": (m, x, v), "spatial": (m[perm], x[perm], v[perm])}
+    props = torch.cuda.get_device_properties(0)
+    peak = metrics.fp32_peak_tflops(props.multi_processor_count, 2070.0) * 1e12
+    speed = []
+    for prec in args.precisions.split(","):
+        for lay in ("generation", "spatial") if prec == "ds" else ("generation",):
+            mm, xx, vv = layouts[lay]
+            for order in (6, 2):
+                with _lib.NBody(mm, xx, vv, eps=eps, precision=prec) as s:
+                    per_step = _time_symplectic(torch, s, order, 2.0**-8, 16)
+                stages = 7 if order == 6 else 1
+                ips = stages * n * n / per_step
+                speed.append({"precision": prec, "layout": lay, "order": order,
+                              "s_per_step": per_step,
+                              "ms_per_force_evaluation": per_step / stages * 1e3,
+                              "interactions_per_s": ips,
+                              "frac_of_fp32_peak": ips * metrics.FLOPS_PER_ACC_INTERACTION / peak})
+                print(json.dumps(speed[-1]), file=sys.stderr, flush=True)
+    accuracy = []
+    for k in (7, 8, 9, 10):
+        row = {"dt_order6": 2.0**-k, "dt_order2": 2.0**-k / 7,
+               "force_evaluations": 7 * 2 ** (k - 3)}
+        for order, dt, steps in ((6, 2.0**-k, 2 ** (k - 3)), (2, 2.0**-k / 7, 7 * 2 ** (k - 3))):
+            with _lib.NBody(m, x, v, eps=eps, precision="ds") as s:
+                E0 = s.energy()[2]
+                s.symplectic(order, dt, steps)
+                row[f"dE_over_E_order{order}"] = abs(s.energy()[2] / E0 - 1.0)
+        accuracy.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"metric": "interactions/s and energy error of the symplectic integrators",
+           "unit": "interactions/s", "workload": f"uniform_sphere_salpeter_q1_n{n}_eps0.1d",
+           "flops_per_interaction": metrics.FLOPS_PER_ACC_INTERACTION,
+           "peak_basis": "FP32 lanes x 2 x 2070 MHz", "speed": speed,
+           "energy_at_t_1/8": accuracy}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_nsweep(args):
     """Seconds per integration step against N on the paper's own test system
     (Sec. 3): uniform sphere of radius 1, Salpeter mass spectrum, velocities
     rescaled to virial ratio Q = 1, G = M = R = 1, eps = 0.1 of the mean
     interparticle distance (4 pi / 3 N)^(1/3).  The quantity of the paper's
     Fig. 1 for this GPU: a Hermite step (all particles, shared dt, acc + jerk)
-    in split precision and in FP32, and a KDK leapfrog step (acceleration
-    only, FP32).  CPU baseline: the FP64 oracle's force + jerk on a bounded
+    in split precision and in FP32, a sixth-order symplectic step (seven
+    acceleration-only evaluations, split precision) and a KDK leapfrog step
+    of the differentiable FP32 path (acceleration only).  CPU baseline: the FP64 oracle's force + jerk on a bounded
     sample of i-particles against all N, scaled to N, on every host core and
     on one (the paper's OpenMP and serial versions)."""
     import torch
@@ -684,6 +760,8 @@ def run_nsweep(args):
                 e1.record()
                 torch.cuda.synchronize()
                 row[f"hermite_{prec}_s"] = e0.elapsed_time(e1) / 1e3 / steps
+        with _lib.NBody(m, x, v, eps=eps, precision="ds") as s:
+            row["symplectic6_ds_s"] = _time_symplectic(torch, s, 6, 2.0**-10, steps)
         fm = torch.tensor(m, dtype=torch.float32, device=dev)
         fx = torch.tensor(x, dtype=torch.float32, device=dev)
         fv = torch.tensor(v, dtype=torch.float32, device=dev)
@@ -735,7 +813,7 @@ def main():
     if args.workload != "king1m" and args.impl == "ours":
         return {"shared1024": run_shared1024, "block65536": run_block65536,
                 "batched": run_batched, "adjoint": run_adjoint,
-                "nsweep": run_nsweep}[args.workload](args)
+                "nsweep": run_nsweep, "symplectic": run_symplectic}[args.workload](args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -161,6 +161,30 @@ nb_status nb_set_block_mode(nb_ctx *ctx, int32_t mode);
 /* *fused = 1 if the last nb_run_blocks call ran the fused form, else 0. */
 nb_status nb_last_block_path(nb_ctx *ctx, int32_t *fused);
 
+/* Fixed-step symplectic integration of every particle (paper Sec. 2.2):
+ * nsteps steps of length dt (any finite value; a negative dt integrates
+ * backwards) of the scheme of the given order, on the context's FP64
+ * state with forces in its precision (FP32 or split precision, softening
+ * eps, no jerk).
+ *   order 2: kick-drift-kick leapfrog, one force evaluation per step;
+ *   order 6: the symmetric composition of seven leapfrog steps of lengths
+ *            w_k dt with the sixth-order weights of Kinoshita, Yoshida &
+ *            Nakai (1991), Table 1, first column (Yoshida's 1990 solution
+ *            A: w1 = -1.17767998417887, w2 = 0.235573213359358,
+ *            w3 = 0.784513610477557, w0 = 1 - 2 (w1 + w2 + w3), stages
+ *            w3 w2 w1 w0 w1 w2 w3), seven force evaluations per step.
+ * The call first evaluates the acceleration at the current positions (so
+ * nsteps = 0 only refreshes it); the kicks between two drifts of a step
+ * are merged, and each step ends with its closing half kick, so x and v
+ * are synchronous after every step.  One step is captured as a CUDA graph
+ * (cached for the last order and dt) and replayed.  On return x, v hold
+ * the new state and a the acceleration at x (nb_get_state); t_tick, lev
+ * and jerk are not advanced, so Hermite calls (nb_next_block, nb_predict,
+ * nb_step, nb_run_blocks) answer NB_ERR_STATE until nb_set_state gives a
+ * Hermite state.  Synchronises.  NB_ERR_INVALID_ARG: order not 2 or 6,
+ * non-finite dt, nsteps < 0. */
+nb_status nb_symplectic(nb_ctx *ctx, int32_t order, double dt, int64_t nsteps);
+
 /* Energy of the current (synchronised) state in FP64 on the GPU:
  * K = 1/2 sum m v^2, W = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)
  * (the softened pair potential consistent with the force).  Uses the

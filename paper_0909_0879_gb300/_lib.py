@@ -58,6 +58,7 @@ SIGNATURES = [
     ("nb_run_blocks", C.c_int, [_vp, _d, _i64, _P(_i64), _P(_d)]),
     ("nb_set_block_mode", C.c_int, [_vp, _i32]),
     ("nb_last_block_path", C.c_int, [_vp, _P(_i32)]),
+    ("nb_symplectic", C.c_int, [_vp, _i32, _d, _i64]),
     ("nb_energy", C.c_int, [_vp, _P(_d), _P(_d), _P(_d)]),
     ("nb_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -289,6 +290,13 @@ class NBody:
         f = C.c_int32()
         _check(self._L.nb_last_block_path(self._h, C.byref(f)))
         return "fused" if f.value else "general"
+
+    def symplectic(self, order: int, dt: float, nsteps: int):
+        """Fixed-step symplectic integration of every particle: order 2
+        (kick-drift-kick leapfrog) or 6 (seven-stage composition), nsteps
+        steps of dt.  Afterwards x, v and a (= A(x)) are current; Hermite
+        calls need set_state first."""
+        _check(self._L.nb_symplectic(self._h, int(order), float(dt), int(nsteps)))
 
     def run_until(self, t_end: float):
         """Block steps until every particle has reached t_end (a tick multiple

@@ -177,6 +177,15 @@ struct nb_ctx {
   int block_mode = 0;                   // 0: fused when the schedule allows, 1: general
   int last_fused = 0;                   // the last nb_run_blocks ran the fused steps
   int64_t graph_launches = 0, fus_graph_launches = 0;  // kernels per replay
+  // fixed-step symplectic integration: one step's graph for (order, dt)
+  cudaGraphExec_t sym_graph = nullptr;
+  double *sym_graph_part = nullptr;
+  int sym_order = 0;
+  double sym_dt = 0.0;
+  int64_t sym_graph_launches = 0;
+  // nb_symplectic moved x and v: the Hermite fields (jerk, times, levels)
+  // no longer belong to them until nb_set_state
+  bool sym_moved = false;
   std::vector<void *> allocs;
 };
 
@@ -241,6 +250,16 @@ nb_status sync_ctx(nb_ctx *c) {
 
 nb_status check_ctx(nb_ctx *c) {
   if (!c) return fail(NB_ERR_INVALID_ARG, "null context");
+  return NB_OK;
+}
+
+// Hermite calls need the jerk, times and levels of the current x and v.
+nb_status check_hermite(nb_ctx *c) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (c->sym_moved)
+    return fail(NB_ERR_STATE, "nb_symplectic moved the particles; nb_set_state must give the "
+                              "Hermite state (jerk, times, levels) before Hermite steps");
   return NB_OK;
 }
 
@@ -377,6 +396,7 @@ void nb_destroy(nb_ctx *c) {
   if (c->ev) cudaEventDestroy(c->ev);
   if (c->blk_graph) cudaGraphExecDestroy(c->blk_graph);
   if (c->fus_graph) cudaGraphExecDestroy(c->fus_graph);
+  if (c->sym_graph) cudaGraphExecDestroy(c->sym_graph);
   delete c;
 }
 
@@ -508,7 +528,7 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
 
 nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
   Range r("nb_next_block");
-  nb_status s = check_ctx(c);
+  nb_status s = check_hermite(c);
   if (s != NB_OK) return s;
   int nl = 0;
   NB_CUDA(launch_next_block(c->n, c->t_tick, c->lev, c->act, c->blk, c->scal, c->stream, &nl));
@@ -527,7 +547,7 @@ nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
 
 nb_status nb_predict(nb_ctx *c, double t) {
   Range r("nb_predict");
-  nb_status s = check_ctx(c);
+  nb_status s = check_hermite(c);
   if (s != NB_OK) return s;
   bool ok;
   const int64_t tick = tick_of(t, &ok);
@@ -855,12 +875,131 @@ nb_status capture_blocks(nb_ctx *c, bool fused, cudaGraphExec_t *out, int64_t *l
   return NB_OK;
 }
 
+// ---- fixed-step symplectic integration
+
+// Acceleration of every particle into c->a (acceleration-only kernel of the
+// built-in shape for n, which every built-in shape has).
+nb_status queue_acc_all(nb_ctx *c, cudaStream_t s, int64_t *launches) {
+  const int v = choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, c->n, c->n_jt,
+                               c->num_sms);
+  if (!has_acc_only(v)) return fail(NB_ERR_STATE, "force shape %d has no acceleration-only kernel", v);
+  const int grid = force_grid(v, c->n, c->n_jt, c->num_sms, 0);
+  if (part_bytes(v, grid) > c->part_cap)
+    return fail(NB_ERR_STATE, "partial-sum scratch too small for shape %d", v);
+  ForceArgs A;
+  A.jhi = c->jhi;
+  A.jlo = c->jlo;
+  A.jvel = c->jvel;
+  A.jrel = c->jrel;
+  A.tinfo = c->tinfo;
+  A.n_jt = c->n_jt;
+  A.idx = nullptr;
+  A.n_i = c->n;
+  A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
+  A.G = c->cfg.G;
+  A.acc = c->a;
+  A.jerk = nullptr;
+  A.part = reinterpret_cast<float2 *>(c->part);
+  A.err = c->err;
+  int nl = 0;
+  NB_CUDA(launch_force(v, A, grid, s, &nl));
+  *launches += nl;
+  return NB_OK;
+}
+
+nb_status queue_kick_drift(nb_ctx *c, cudaStream_t s, double h, double d, bool rec,
+                           int64_t *launches) {
+  NB_CUDA(launch_kick_drift(c->n, c->n_jt, h, d, rec, c->a, c->v, c->x, c->m,
+                            c->cfg.precision, c->jhi, c->jlo, c->jvel, c->jrel, c->tinfo, s));
+  *launches += 1;
+  return NB_OK;
+}
+
+// One step: the stages' kick-drift + force with the kicks between two
+// drifts merged, then the closing half kick.
+nb_status queue_symplectic_step(nb_ctx *c, cudaStream_t s, const double *w, int S, double dt,
+                                int64_t *launches) {
+  for (int k = 0; k < S; ++k) {
+    const double h = 0.5 * dt * ((k > 0 ? w[k - 1] : 0.0) + w[k]);
+    nb_status st = queue_kick_drift(c, s, h, w[k] * dt, true, launches);
+    if (st == NB_OK) st = queue_acc_all(c, s, launches);
+    if (st != NB_OK) return st;
+  }
+  return queue_kick_drift(c, s, 0.5 * dt * w[S - 1], 0.0, false, launches);
+}
+
+nb_status capture_symplectic(nb_ctx *c, const double *w, int S, double dt) {
+  if (c->sym_graph) {
+    cudaGraphExecDestroy(c->sym_graph);
+    c->sym_graph = nullptr;
+  }
+  cudaStream_t cs;
+  NB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  int64_t nl = 0;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  nb_status qs = NB_ERR_CUDA;
+  if (e == cudaSuccess) qs = queue_symplectic_step(c, cs, w, S, dt, &nl);
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (qs != NB_OK && qs != NB_ERR_CUDA) {
+    if (e2 == cudaSuccess) cudaGraphDestroy(g);
+    return qs;
+  }
+  if (e != cudaSuccess || e2 != cudaSuccess || qs != NB_OK)
+    return fail(NB_ERR_CUDA, "capture of the symplectic step failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  e = cudaGraphInstantiate(&c->sym_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess)
+    return fail(NB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  c->sym_graph_launches = nl;
+  return NB_OK;
+}
+
 }  // namespace
+
+extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t nsteps) {
+  Range r("nb_symplectic");
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  double w[7];
+  const int S = symplectic_stages(order, w);
+  if (S == 0) return fail(NB_ERR_INVALID_ARG, "symplectic order %d is not 2 or 6", order);
+  if (!std::isfinite(dt)) return fail(NB_ERR_INVALID_ARG, "non-finite time step");
+  if (nsteps < 0) return fail(NB_ERR_INVALID_ARG, "negative step count");
+  // the acceleration at the current positions, then nsteps replays of one
+  // step's graph
+  int64_t nl = 0;
+  s = queue_kick_drift(c, c->stream, 0.0, 0.0, true, &nl);
+  if (s == NB_OK) s = queue_acc_all(c, c->stream, &nl);
+  if (s != NB_OK) return s;
+  c->launches += nl;
+  c->interactions += c->n * c->n;
+  c->sym_moved = true;
+  c->have_block = false;
+  c->force_done = false;
+  c->t_pred = -1;
+  if (nsteps > 0) {
+    if (!c->sym_graph || c->sym_order != order || c->sym_dt != dt ||
+        c->sym_graph_part != c->part) {
+      s = capture_symplectic(c, w, S, dt);
+      if (s != NB_OK) return s;
+      c->sym_order = order;
+      c->sym_dt = dt;
+      c->sym_graph_part = c->part;
+    }
+    for (int64_t k = 0; k < nsteps; ++k) NB_CUDA(cudaGraphLaunch(c->sym_graph, c->stream));
+    c->launches += nsteps * c->sym_graph_launches;
+    c->interactions += nsteps * S * c->n * c->n;
+  }
+  return sync_ctx(c);
+}
 
 extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
                                    int64_t *blocks_done, double *t_last) {
   Range r("nb_run_blocks");
-  nb_status s = check_ctx(c);
+  nb_status s = check_hermite(c);
   if (s != NB_OK) return s;
   bool ok;
   const int64_t tend = tick_of(t_end, &ok);
@@ -1021,6 +1160,7 @@ nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double
   c->have_block = false;
   c->force_done = false;
   c->t_pred = -1;
+  c->sym_moved = false;
   return sync_ctx(c);
 }
 

@@ -149,7 +149,8 @@ struct DsAcc<IPT, NT, true> {
 
 using dev::owner_of;
 
-template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK, int SACC, int REL>
+// JRK = 0: acceleration only (no velocity records, no jerk sums).
+template <int PREC, int IPT, int TPI, int NT, int MASK, int PACK, int SACC, int REL, int JRK>
 __global__ void __launch_bounds__(NT, 1)
     force_jerk_kernel(const ForceArgs A, uint64_t U, int P) {
   using V = typename std::conditional<PACK != 0, float2, float>::type;
@@ -199,10 +200,10 @@ __global__ void __launch_bounds__(NT, 1)
     const int st = static_cast<int>(s_idx % kStages);
     const uint64_t jt = dev::umod(u0 + s_idx, n_jt);
     float4 *dst = sbase + static_cast<size_t>(st) * NARR * kJT;
-    mbar_expect_tx(&bars[st], kTileBytes * NARR);
+    mbar_expect_tx(&bars[st], kTileBytes * (JRK ? NARR : NARR - 1));
     bulk_g2s(dst, A.jhi + jt * kJT, kTileBytes, &bars[st]);
     if (PREC) bulk_g2s(dst + kJT, A.jlo + jt * kJT, kTileBytes, &bars[st]);
-    bulk_g2s(dst + kOffV * kJT, A.jvel + jt * kJT, kTileBytes, &bars[st]);
+    if (JRK) bulk_g2s(dst + kOffV * kJT, A.jvel + jt * kJT, kTileBytes, &bars[st]);
     if (REL) bulk_g2s(dst + 3 * kJT, A.jrel + jt * kJT, kTileBytes, &bars[st]);
   };
   if (tid == 0) {
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(NT, 1)
       int64_t i = 0;
       if (k < n_i) i = A.idx ? A.idx[k] : k;
       const float4 h = A.jhi[i];
-      const float4 w = A.jvel[i];
+      const float4 w = JRK ? A.jvel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
       if (PREC) l = A.jlo[i];
       const int qq = q / W, wl = q % W;
@@ -344,8 +345,14 @@ __global__ void __launch_bounds__(NT, 1)
           for (int c = 0; c < 3; ++c) pa[q][c] = O::bc(0.f);
 #pragma unroll(UNR)
         for (int jj = c0; jj < c0 + CH * TPI; jj += TPI) {
-          const float4 wj = sv[jj];
           float4 hj, lj;
+          V vxj, vyj, vzj;
+          if (JRK) {
+            const float4 wj = sv[jj];
+            vxj = O::bc(wj.x);
+            vyj = O::bc(wj.y);
+            vzj = O::bc(wj.z);
+          }
           if (FAR) {
             hj = sr[jj];
           } else {
@@ -353,7 +360,6 @@ __global__ void __launch_bounds__(NT, 1)
             if (PREC) lj = sl[jj];
           }
           const V xj = O::bc(hj.x), yj = O::bc(hj.y), zj = O::bc(hj.z), mj = O::bc(hj.w);
-          const V vxj = O::bc(wj.x), vyj = O::bc(wj.y), vzj = O::bc(wj.z);
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             V dx, dy, dz;
@@ -370,24 +376,32 @@ __global__ void __launch_bounds__(NT, 1)
               dy = O::add(yj, nxh[q][1]);
               dz = O::add(zj, nxh[q][2]);
             }
-            const V ux = O::add(vxj, nvi[q][0]);
-            const V uy = O::add(vyj, nvi[q][1]);
-            const V uz = O::add(vzj, nvi[q][2]);
+            V ux, uy, uz;
+            if (JRK) {
+              ux = O::add(vxj, nvi[q][0]);
+              uy = O::add(vyj, nvi[q][1]);
+              uz = O::add(vzj, nvi[q][2]);
+            }
             const V r2 = O::fma(dx, dx, O::fma(dy, dy, O::fma(dz, dz, veps2)));
             const V rinv = O::template rsq<MASK>(r2);
             const V rinv2 = O::mul(rinv, rinv);
             const V mr3 = O::mul(O::mul(mj, rinv), rinv2);
-            const V rv = O::fma(dx, ux, O::fma(dy, uy, O::mul(dz, uz)));
-            const V cc = O::mul(O::mul(rv, rinv2), mr3);
+            V cc;
+            if (JRK) {
+              const V rv = O::fma(dx, ux, O::fma(dy, uy, O::mul(dz, uz)));
+              cc = O::mul(O::mul(rv, rinv2), mr3);
+            }
             pa[q][0] = O::fma(mr3, dx, pa[q][0]);
             pa[q][1] = O::fma(mr3, dy, pa[q][1]);
             pa[q][2] = O::fma(mr3, dz, pa[q][2]);
-            p1[q][0] = O::fma(mr3, ux, p1[q][0]);
-            p1[q][1] = O::fma(mr3, uy, p1[q][1]);
-            p1[q][2] = O::fma(mr3, uz, p1[q][2]);
-            p2[q][0] = O::fma(cc, dx, p2[q][0]);
-            p2[q][1] = O::fma(cc, dy, p2[q][1]);
-            p2[q][2] = O::fma(cc, dz, p2[q][2]);
+            if (JRK) {
+              p1[q][0] = O::fma(mr3, ux, p1[q][0]);
+              p1[q][1] = O::fma(mr3, uy, p1[q][1]);
+              p1[q][2] = O::fma(mr3, uz, p1[q][2]);
+              p2[q][0] = O::fma(cc, dx, p2[q][0]);
+              p2[q][1] = O::fma(cc, dy, p2[q][1]);
+              p2[q][2] = O::fma(cc, dz, p2[q][2]);
+            }
           }
         }
 #pragma unroll
@@ -408,7 +422,7 @@ __global__ void __launch_bounds__(NT, 1)
         walk_tile(std::false_type{});
       // fold the tile's jerk partial sums (jerk = p1 - 3 p2)
 #pragma unroll
-      for (int q = 0; q < IPT; ++q)
+      for (int q = 0; q < (JRK ? IPT : 0); ++q)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float jt =
@@ -442,8 +456,8 @@ __global__ void __launch_bounds__(NT, 1)
       for (int c = 0; c < 3; ++c) {
         oh[c] = D.AH(q, c);
         ol[c] = D.AL(q, c);
-        oh[3 + c] = D.JH(q, c);
-        ol[3 + c] = D.JL(q, c);
+        oh[3 + c] = JRK ? D.JH(q, c) : 0.f;
+        ol[3 + c] = JRK ? D.JL(q, c) : 0.f;
       }
       if (TPI > 1) {
 #pragma unroll
@@ -462,7 +476,7 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             A.acc[3 * k + c] = dev::ds_to_double(oh[c], ol[c], A.G);
-            A.jerk[3 * k + c] = dev::ds_to_double(oh[3 + c], ol[3 + c], A.G);
+            if (JRK) A.jerk[3 * k + c] = dev::ds_to_double(oh[3 + c], ol[3 + c], A.G);
           }
         } else {
           const int slot = (ib == ib_first) ? 0 : 1;
@@ -480,7 +494,7 @@ __global__ void __launch_bounds__(NT, 1)
 // Sum the partial segments of every split i-block: one warp per
 // i-particle, lanes stride over the CTAs that hold a partial (ascending
 // within a lane) and meet by a butterfly; the order is fixed for a given
-// grid, so results are deterministic.
+// grid, so results are deterministic.  jerk may be null (acceleration only).
 __global__ void force_fixup_kernel(const float2 *__restrict__ part, int64_t n_i,
                                    uint64_t n_jt, uint64_t U, int P, int BI,
                                    double G, double *__restrict__ acc,
@@ -508,27 +522,38 @@ __global__ void force_fixup_kernel(const float2 *__restrict__ part, int64_t n_i,
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       acc[3 * k + c] = dev::ds_to_double(h[c], l[c], G);
-      jerk[3 * k + c] = dev::ds_to_double(h[3 + c], l[3 + c], G);
+      if (jerk) jerk[3 * k + c] = dev::ds_to_double(h[3 + c], l[3 + c], G);
     }
   }
 }
 
 using KernelFn = void (*)(const ForceArgs, uint64_t, int);
 
+// fn: acceleration + jerk; acc_fn: acceleration only (compiled for the
+// built-in shapes, null elsewhere).
 struct Entry {
   Variant V;
   KernelFn fn;
+  KernelFn acc_fn;
 };
 
-#define NB_V(PREC, IPT, TPI, NT, MASK, PACK)             \
-  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 0},    \
-        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 0>}
-#define NB_VS(PREC, IPT, TPI, NT, MASK, PACK)            \
-  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 1, 0},    \
-        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 1, 0>}
-#define NB_VR(PREC, IPT, TPI, NT, MASK, PACK)            \
-  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 1},    \
-        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 1>}
+#define NB_V(PREC, IPT, TPI, NT, MASK, PACK)                 \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 0},        \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 0, 1>, nullptr}
+#define NB_VA(PREC, IPT, TPI, NT, MASK, PACK)                \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 0},        \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 0, 1>, \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 0, 0>}
+#define NB_VS(PREC, IPT, TPI, NT, MASK, PACK)                \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 1, 0},        \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 1, 0, 1>, nullptr}
+#define NB_VR(PREC, IPT, TPI, NT, MASK, PACK)                \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 1},        \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 1, 1>, nullptr}
+#define NB_VRA(PREC, IPT, TPI, NT, MASK, PACK)               \
+  Entry{Variant{PREC, IPT, TPI, NT, MASK, PACK, 0, 1},        \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 1, 1>, \
+        &force_jerk_kernel<PREC, IPT, TPI, NT, MASK, PACK, 0, 1, 0>}
 
 // The compiled shape table.  Index order is part of the tuning interface.
 const Entry kTable[] = {
@@ -536,19 +561,19 @@ const Entry kTable[] = {
     NB_V(1, 2, 1, 256, 0, 0),   // 1
     NB_V(1, 1, 1, 256, 0, 0),   // 2
     NB_V(1, 1, 4, 256, 0, 0),   // 3  DS, short lists
-    NB_V(1, 1, 16, 256, 0, 0),  // 4
+    NB_VA(1, 1, 16, 256, 0, 0), // 4
     NB_V(0, 4, 1, 256, 0, 0),   // 5  FP32, long lists
     NB_V(0, 2, 1, 256, 0, 0),   // 6
     NB_V(0, 1, 1, 256, 0, 0),   // 7
-    NB_V(0, 1, 4, 256, 0, 0),   // 8  FP32, short lists
-    NB_V(0, 1, 16, 256, 0, 0),  // 9
-    NB_V(1, 1, 1, 256, 1, 0),   // 10 DS, eps == 0
-    NB_V(0, 1, 1, 256, 1, 0),   // 11 FP32, eps == 0
+    NB_VA(0, 1, 4, 256, 0, 0),  // 8  FP32, short lists
+    NB_VA(0, 1, 16, 256, 0, 0), // 9
+    NB_VA(1, 1, 1, 256, 1, 0),  // 10 DS, eps == 0
+    NB_VA(0, 1, 1, 256, 1, 0),  // 11 FP32, eps == 0
     NB_V(1, 4, 1, 256, 0, 1),   // 12 DS, packed pairs of i
     NB_V(1, 2, 1, 256, 0, 1),   // 13
-    NB_V(0, 4, 1, 256, 0, 1),   // 14 FP32, packed pairs of i
+    NB_VA(0, 4, 1, 256, 0, 1),  // 14 FP32, packed pairs of i
     NB_V(0, 2, 1, 256, 0, 1),   // 15
-    NB_V(1, 2, 4, 256, 0, 1),   // 16 DS, packed, short lists
+    NB_VA(1, 2, 4, 256, 0, 1),  // 16 DS, packed, short lists
     NB_V(1, 2, 1, 128, 0, 1),   // 17 DS, packed, 128 threads
     NB_V(1, 4, 1, 384, 0, 1),   // 18 DS, packed, 12 warps per CTA
     NB_V(1, 4, 2, 384, 0, 1),   // 19
@@ -558,7 +583,7 @@ const Entry kTable[] = {
     NB_VS(1, 8, 1, 256, 0, 1),  // 23 DS, packed, 8 i-particles per thread
     NB_VS(1, 6, 1, 256, 0, 1),  // 24
     NB_VS(0, 8, 1, 256, 0, 1),  // 25 FP32, packed, 8 i-particles per thread
-    NB_VR(1, 4, 1, 256, 0, 1),  // 26 DS, packed, far tiles tile-relative
+    NB_VRA(1, 4, 1, 256, 0, 1), // 26 DS, packed, far tiles tile-relative
     NB_VR(1, 2, 1, 256, 0, 1),  // 27
     NB_VR(1, 2, 4, 256, 0, 1),  // 28
 };
@@ -571,6 +596,7 @@ size_t smem_bytes(const Variant &V) {
 
 std::mutex g_occ_mu;
 int g_occ[kNumVariants] = {0};
+bool g_acc_attr[kNumVariants] = {false};
 
 }  // namespace
 
@@ -671,13 +697,28 @@ cudaError_t launch_force_dev(int v, const ForceArgs &A, int grid, int64_t n_max,
   return cudaGetLastError();
 }
 
+bool has_acc_only(int v) { return kTable[v].acc_fn != nullptr; }
+
 cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
                          int *launches) {
   const Entry &E = kTable[v];
+  const KernelFn fn = A.jerk ? E.fn : E.acc_fn;
+  if (!fn) return cudaErrorInvalidValue;
   const int BI = block_i(E.V);
   const uint64_t n_ib = static_cast<uint64_t>((A.n_i + BI - 1) / BI);
   const uint64_t U = n_ib * static_cast<uint64_t>(A.n_jt);
-  E.fn<<<grid, E.V.threads, smem_bytes(E.V), s>>>(A, U, grid);
+  if (!A.jerk) {
+    // same shared-memory layout as the jerk kernel (the velocity stage is
+    // left unused); the attribute is set once, at the first launch
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    if (!g_acc_attr[v]) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem_bytes(E.V)));
+      if (e != cudaSuccess) return e;
+      g_acc_attr[v] = true;
+    }
+  }
+  fn<<<grid, E.V.threads, smem_bytes(E.V), s>>>(A, U, grid);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int nl = 1;

@@ -34,7 +34,7 @@ struct ForceArgs {
   float eps2;
   double G;
   double *acc;         // (n_i, 3)
-  double *jerk;        // (n_i, 3)
+  double *jerk;        // (n_i, 3); null: acceleration only (launch_force)
   float2 *part;        // partial sums of split i-blocks (hi, lo pairs)
   int *err;            // device error word
   // Device-resident mode (block steps replayed from a CUDA graph): when ctl
@@ -119,8 +119,12 @@ int ctas_per_sm(int v);
 size_t part_bytes(int v, int grid);
 // Persistent grid for a variant, an active-list length and an optional cap.
 int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap);
+// The variant has an acceleration-only kernel (the built-in shapes).
+bool has_acc_only(int v);
 // Queue the force kernel (and its fix-up when i-blocks are split) on `s`.
-// Returns the number of kernel launches through *launches.
+// With A.jerk null the acceleration-only kernel runs (cudaErrorInvalidValue
+// when the variant has none).  Returns the number of kernel launches
+// through *launches.
 cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
                          int *launches);
 // Device-resident form: A.ctl, A.lo, A.hi set; `grid` is the largest
@@ -218,4 +222,14 @@ struct EndArgs {
 cudaError_t launch_block_end(const EndArgs &E, int grid, cudaStream_t s);
 constexpr int kEndThreads = 256;
 
+// --- Fixed-step symplectic integration (nb_symplectic.cu) ---
+// Stage weights of the scheme of the given order into w (at most 7);
+// returns the stage count (1 for order 2, 7 for order 6, 0 otherwise).
+int symplectic_stages(int order, double *w);
+// v += h a, x += d v for every particle (a factor of 0 skips its update);
+// with rec set also the j-records and, when jrel is set, the tile frames.
+cudaError_t launch_kick_drift(int64_t n, int64_t n_jt, double h, double d, bool rec,
+                              const double *a, double *v, double *x, const double *m, int prec,
+                              float4 *jhi, float4 *jlo, float4 *jvel, float4 *jrel,
+                              float4 *tinfo, cudaStream_t s);
 }  // namespace nbi

@@ -1,0 +1,94 @@
+// Fixed-step symplectic integration (Sec. 2.2) of every particle on the
+// device-resident FP64 state: the kick-drift-kick leapfrog (second order)
+// and the sixth-order scheme, a symmetric composition of seven leapfrog
+// steps of lengths w_k dt.  The forces come from the acceleration-only form
+// of the force kernel (nb_force.cu) in the context's precision.
+//
+// One step of S stages with weights w_0..w_{S-1} runs, with the kicks
+// between two drifts merged into one:
+//   for k: v += (w_{k-1} + w_k) dt/2 a   (w_{-1} = 0)
+//          x += w_k dt v, j-records, tile frames
+//          a = A(x)
+//   v += w_{S-1} dt/2 a
+// so a step takes S force evaluations and leaves x, v at the same instant.
+#include "nb_device.cuh"
+
+namespace nbi {
+namespace {
+
+// Yoshida (1990, Phys. Lett. A 150, 262), solution A: the first of the
+// three sixth-order weight sets of Kinoshita, Yoshida & Nakai (1991,
+// Table 1), the one Sec. 2.2 takes.  w0 = 1 - 2 (w1 + w2 + w3); the stages
+// run w3 w2 w1 w0 w1 w2 w3.
+constexpr double kY6W1 = -1.17767998417887100695;
+constexpr double kY6W2 = 0.235573213359358133684;
+constexpr double kY6W3 = 0.784513610477557263820;
+
+// One CTA per 256-record tile, thread t on record j = tile * kJT + t:
+// v += h a and x += d v in FP64 (each skipped when its factor is 0), then,
+// with rec set, the particle's j-records and (split precision) the tile's
+// frame for the far-field test of the force kernel.
+__global__ void __launch_bounds__(kJT)
+    kick_drift_kernel(int64_t n, double h, double d, int rec, const double *__restrict__ a,
+                      double *__restrict__ v, double *__restrict__ x,
+                      const double *__restrict__ m, int prec, float4 *__restrict__ jhi,
+                      float4 *__restrict__ jlo, float4 *__restrict__ jvel,
+                      float4 *__restrict__ jrel, float4 *__restrict__ tinfo) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * kJT + threadIdx.x;
+  const bool real = j < n;
+  float4 hr = make_float4(0.f, 0.f, 0.f, 0.f), lr = hr;
+  if (real) {
+    double xv[3], vv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      vv[c] = v[3 * j + c];
+      xv[c] = x[3 * j + c];
+    }
+    if (h != 0.0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        vv[c] = fma(h, a[3 * j + c], vv[c]);
+        v[3 * j + c] = vv[c];
+      }
+    }
+    if (d != 0.0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xv[c] = fma(d, vv[c], xv[c]);
+        x[3 * j + c] = xv[c];
+      }
+    }
+    if (rec) hr = dev::store_records(j, xv, vv, m[j], prec, jhi, jlo, jvel, &lr);
+  } else if (rec) {
+    hr = jhi[j];  // padding record (zero mass, far away)
+  }
+  if (rec && jrel) dev::tile_frame(blockIdx.x, j, real, hr, lr, jrel, tinfo);
+}
+
+}  // namespace
+
+int symplectic_stages(int order, double *w) {
+  if (order == 2) {
+    w[0] = 1.0;
+    return 1;
+  }
+  if (order == 6) {
+    const double w0 = 1.0 - 2.0 * (kY6W1 + kY6W2 + kY6W3);
+    const double s[7] = {kY6W3, kY6W2, kY6W1, w0, kY6W1, kY6W2, kY6W3};
+    for (int k = 0; k < 7; ++k) w[k] = s[k];
+    return 7;
+  }
+  return 0;
+}
+
+cudaError_t launch_kick_drift(int64_t n, int64_t n_jt, double h, double d, bool rec,
+                              const double *a, double *v, double *x, const double *m, int prec,
+                              float4 *jhi, float4 *jlo, float4 *jvel, float4 *jrel,
+                              float4 *tinfo, cudaStream_t s) {
+  if (n_jt <= 0) return cudaSuccess;
+  kick_drift_kernel<<<static_cast<unsigned>(n_jt), kJT, 0, s>>>(
+      n, h, d, rec ? 1 : 0, a, v, x, m, prec, jhi, jlo, jvel, jrel, tinfo);
+  return cudaGetLastError();
+}
+
+}  // namespace nbi

@@ -20,6 +20,10 @@ symmetric acceleration-only pair, n_f = 30 N (N - 1) / 2.
 from __future__ import annotations
 
 FLOPS_PER_INTERACTION = 44
+# Acceleration only (the symplectic integrators): 3 FADD (differences),
+# 3 FFMA (s^2), 1 reciprocal square root, 3 FMUL (1/s^2, m/s, m/s^3) and
+# 3 FFMA (acceleration), a fused multiply-add counted as 2 flops.
+FLOPS_PER_ACC_INTERACTION = 19
 FLOPS_PER_INTERACTION_CONVENTION = 60  # common acc+jerk convention in the literature
 PAPER_FLOPS_PER_PAIR = 30
 FP32_LANES_PER_SM = 128

@@ -1,0 +1,165 @@
+"""GPU parity of the fixed-step symplectic integrators (the kick-drift-kick
+leapfrog and the seven-stage sixth-order composition, Sec. 2.2) against the
+FP64 oracle.
+
+Bar.  The GPU integrates the same FP64 state as the oracle; only its forces
+differ, by at most tol * sum_j |f_ij| per particle (tol = 1e-6 for split
+precision, the force bar; 2e-5 for FP32: about 10 ulps per pair term plus
+one per term of the 256-term tile sums and of the per-tile total).  Over a
+time T a force error da moves a particle by at most T^2/2 max|da| and
+changes its velocity by at most T max|da| (the feedback of the position
+error on the force is second order at eps = 0.05, where the largest tidal
+rate, m / eps^3 = 8, gives a time scale of 0.35 >> T = 1/8).  The tests
+take twice those bounds per particle, and check that the order-2 and
+order-6 results differ by far more, so a wrong weight or stage order
+cannot pass.
+"""
+import numpy as np
+import pytest
+
+from paper_0909_0879_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"ds": 1e-6, "fp32": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0909_0879_gb300 import _lib
+
+    _lib.load()
+    return _lib
+
+
+def _aabs_max(oracle_mod, m, xs, eps):
+    """Per-particle max over the given positions of sum_j |f_ij|."""
+    out = None
+    for x in xs:
+        aabs, _ = oracle_mod.force_jerk_abs(m, x, np.zeros_like(x), eps)
+        out = aabs if out is None else np.maximum(out, aabs)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+def test_symplectic_matches_oracle(nb, oracle_mod, prec):
+    """N = 1000 (ragged: 3 tiles + 232) Plummer, eps = 0.05, 4 steps of
+    dt = 1/32, orders 2 and 6."""
+    n, eps, dt, ns = 1000, 0.05, 1.0 / 32, 4
+    T = dt * ns
+    m, x, v = ics.plummer(n, 11)
+    res = {}
+    for order in (2, 6):
+        with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+            s.symplectic(order, dt, ns)
+            st = s.get_state(want=("x", "v", "a"))
+        xo, vo = oracle_mod.symplectic(m, x, v, eps, dt, ns, order)
+        aabs = _aabs_max(oracle_mod, m, (x, xo), eps)
+        ex = np.linalg.norm(st["x"] - xo, axis=1)
+        ev = np.linalg.norm(st["v"] - vo, axis=1)
+        bx = T * T * TOL[prec] * aabs
+        bv = 2 * T * TOL[prec] * aabs
+        print(prec, order, "max dx / bound %.3g, max dv / bound %.3g"
+              % ((ex / bx).max(), (ev / bv).max()))
+        assert np.all(ex <= bx) and np.all(ev <= bv)
+        # the acceleration left in the state is A(x) at the final positions
+        ao, _ = oracle_mod.force_jerk(m, st["x"], np.zeros_like(xo), eps)
+        cond = np.linalg.norm(st["a"] - ao, axis=1) / _aabs_max(oracle_mod, m, (st["x"],), eps)
+        assert cond.max() <= TOL[prec]
+        res[order] = (st["x"], bx)
+    # the two orders differ by far more than the bound
+    d26 = np.linalg.norm(res[2][0] - res[6][0], axis=1)
+    assert np.median(d26 / res[6][1]) > 10.0
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+@pytest.mark.parametrize("n", [1000, 70001])
+def test_acceleration_only_kernel_equals_jerk_kernel(nb, prec, n):
+    """nsteps = 0 only evaluates A(x) with the acceleration-only kernel; the
+    acceleration sums are the same operations in the same order as those
+    of the acceleration + jerk kernel that nb_init ran at the same
+    positions with the same shape and grid: bit-identical."""
+    m, x, v = ics.plummer(n, 12)
+    with nb.NBody(m, x, v, eps=1e-3, precision=prec) as s:
+        a0 = s.get_state(want=("a",))["a"]
+        s.symplectic(6, 1.0 / 64, 0)
+        a1 = s.get_state(want=("a", "x"))
+    assert np.array_equal(a1["x"], x)
+    assert np.array_equal(a1["a"], a0)
+
+
+def test_symplectic6_reversible_on_gpu(nb, oracle_mod):
+    """Six steps forward, velocities negated, six steps again: back to the
+    start within the force-error bound (a kick merged across the wrong
+    stages or a missing closing half kick breaks this by orders of
+    magnitude)."""
+    n, eps, dt, ns = 1000, 0.05, 1.0 / 32, 6
+    T = dt * ns
+    m, x, v = ics.plummer(n, 13)
+    with nb.NBody(m, x, v, eps=eps, precision="ds") as s:
+        s.symplectic(6, dt, ns)
+        st = s.get_state()
+        st["v"] = -st["v"]
+        s.set_state(st)
+        s.symplectic(6, dt, ns)
+        back = s.get_state(want=("x", "v"))
+    aabs = _aabs_max(oracle_mod, m, (x, st["x"]), eps)
+    ex = np.linalg.norm(back["x"] - x, axis=1)
+    ev = np.linalg.norm(-back["v"] - v, axis=1)
+    assert np.all(ex <= 2 * T * T * TOL["ds"] * aabs)
+    assert np.all(ev <= 4 * T * TOL["ds"] * aabs)
+
+
+def test_symplectic_protocol(nb):
+    """Bad order / non-finite dt / negative count are rejected; after a
+    symplectic run the Hermite calls answer NB_ERR_STATE until set_state;
+    a negative dt integrates backwards."""
+    m, x, v = ics.plummer(300, 14)
+    with nb.NBody(m, x, v, eps=1e-2, precision="ds") as s:
+        for args in ((4, 0.01, 1), (6, float("nan"), 1), (2, 0.01, -1)):
+            with pytest.raises(nb.NBodyError) as ei:
+                s.symplectic(*args)
+            assert ei.value.status == 1
+        s.symplectic(2, 1.0 / 64, 3)
+        with pytest.raises(nb.NBodyError) as ei:
+            s.step()
+        assert ei.value.status == 2
+        with pytest.raises(nb.NBodyError):
+            s.run_blocks(1.0)
+        st = s.get_state()
+        s.symplectic(2, -1.0 / 64, 3)
+        back = s.get_state(want=("x",))
+        assert np.abs(back["x"] - x).max() < 1e-9
+        s.set_state(st)
+        s.step()
+
+
+def test_symplectic6_energy_at_bench_size(nb, oracle_mod):
+    """The bench's workload: N = 65536 uniform sphere, Salpeter masses,
+    Q = 1, eps = 0.1 of the mean interparticle distance, split precision.
+    Properties that hold at any size: the final acceleration matches the
+    oracle on 256 sampled particles within the force bar, and at dt = 2^-7
+    the sixth-order energy error over 8 steps is below the leapfrog's."""
+    n = 65536
+    m, x, v = ics.uniform_sphere(n, 1006, Q=1.0, masses=ics.salpeter_masses(n, 1006))
+    eps = 0.1 * (4.0 * np.pi / (3.0 * n)) ** (1.0 / 3.0)
+    dE = {}
+    for order in (2, 6):
+        with nb.NBody(m, x, v, eps=eps, precision="ds") as s:
+            E0 = s.energy()[2]
+            s.symplectic(order, 2.0**-7, 8)
+            dE[order] = abs(s.energy()[2] / E0 - 1.0)
+            st = s.get_state(want=("x", "a"))
+        if order == 6:
+            idx = np.sort(np.random.default_rng(3).choice(n, 256, replace=False)).astype(np.int32)
+            zv = np.zeros_like(st["x"])
+            ao, _ = oracle_mod.force_jerk(m, st["x"], zv, eps, idx=idx)
+            aabs, _ = oracle_mod.force_jerk_abs(m, st["x"], zv, eps, idx=idx)
+            cond = np.linalg.norm(st["a"][idx] - ao, axis=1) / aabs
+            assert cond.max() <= TOL["ds"]
+    print("dE/E order 2 %.3e, order 6 %.3e" % (dE[2], dE[6]))
+    assert dE[6] < dE[2]
