@@ -28,6 +28,10 @@
  *                        the standard block scheme (reading, see DESIGN)
  *   leapfrog             paper Sec. 3.1 (the classic second-order scheme),
  *                        kick-drift-kick form (reading)
+ *   external field       paper Sec. 2.1: the Galactic potential of Allen &
+ *                        Santillan (1991), a Plummer bulge, a Miyamoto-Nagai
+ *                        disk and a spherical halo (forms and parameters
+ *                        from that paper; not printed in this one)
  *
  * Parity status: every function below is pinned by -m "not gpu" tests
  * (brute force in 50-digit arithmetic, conservation laws, closed forms,
@@ -517,4 +521,84 @@ double orc_leapfrog_loss_grad(int64_t n, const double *m, const double *x0,
   orc_leapfrog_adjoint_path(n, m, xs, G, eps, dt, nsteps, gx0, gv0, gmass);
   free(xs); free(x); free(v); free(acc);
   return L;
+}
+
+/* External Galactic field (Allen & Santillan 1991).  p holds 13 doubles:
+ *   G, centre (cx, cy, cz), bulge (M_b, b_b), disk (M_d, a_d, b_d),
+ *   halo (M_h, a_h, gamma, r_cut).
+ * With d = x - centre, r = |d|, R^2 = d_x^2 + d_y^2, z = d_z:
+ *   bulge  Phi_b = -G M_b / sqrt(r^2 + b_b^2)
+ *   disk   Phi_d = -G M_d / sqrt(R^2 + (a_d + sqrt(z^2 + b_d^2))^2)
+ *   halo   mass inside r: M(r) = M_h (r/a_h)^gamma / (1 + (r/a_h)^(gamma-1)),
+ *          M(r_cut) beyond r_cut; force -G M(r) / r^2 along d / r;
+ *          Phi_h(r) = -G M(r)/r - G M_h / ((gamma-1) a_h) [F(q_cut) - F(q)]
+ *          for r < r_cut with q = r / a_h and
+ *          F(q) = -(gamma-1) / (1 + q^(gamma-1)) + ln(1 + q^(gamma-1)),
+ *          and -G M(r_cut) / r beyond (so that dPhi_h/dr = G M(r) / r^2).
+ * acc (3) and phi (1) may be NULL. */
+static void ext_one(const double *p, const double *xi, double *acc, double *phi) {
+  const double G = p[0];
+  const double dx = xi[0] - p[1], dy = xi[1] - p[2], dz = xi[2] - p[3];
+  const double mb = p[4], bb = p[5], md = p[6], ad = p[7], bd = p[8];
+  const double mh = p[9], ah = p[10], gam = p[11], rcut = p[12];
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double r = sqrt(r2);
+  double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+  /* bulge: -grad of -G M_b (r^2 + b^2)^(-1/2) */
+  {
+    const double s2 = r2 + bb * bb;
+    const double s = sqrt(s2);
+    const double f = G * mb / (s2 * s);
+    ax -= f * dx;
+    ay -= f * dy;
+    az -= f * dz;
+    ph -= G * mb / s;
+  }
+  /* disk */
+  {
+    const double zeta = sqrt(dz * dz + bd * bd);
+    const double w = ad + zeta;
+    const double D2 = dx * dx + dy * dy + w * w;
+    const double D = sqrt(D2);
+    const double f = G * md / (D2 * D);
+    ax -= f * dx;
+    ay -= f * dy;
+    az -= f * dz * w / zeta;
+    ph -= G * md / D;
+  }
+  /* halo */
+  {
+    const double rr = r < rcut ? r : rcut;
+    const double q = rr / ah;
+    const double u = pow(q, gam - 1.0);
+    const double Mr = mh * q * u / (1.0 + u);
+    if (r > 0.0) {
+      const double f = G * Mr / (r2 * r);
+      ax -= f * dx;
+      ay -= f * dy;
+      az -= f * dz;
+    }
+    if (r < rcut) {
+      const double qc = rcut / ah;
+      const double uc = pow(qc, gam - 1.0);
+      const double Fc = -(gam - 1.0) / (1.0 + uc) + log(1.0 + uc);
+      const double Fq = -(gam - 1.0) / (1.0 + u) + log(1.0 + u);
+      ph += (r > 0.0 ? -G * Mr / r : 0.0) - G * mh / ((gam - 1.0) * ah) * (Fc - Fq);
+    } else {
+      ph -= G * Mr / r;
+    }
+  }
+  if (acc) {
+    acc[0] = ax;
+    acc[1] = ay;
+    acc[2] = az;
+  }
+  if (phi) *phi = ph;
+}
+
+/* Acceleration (n,3) and potential (n) of the external field at x. */
+void orc_ext(int64_t n, const double *x, const double *p, double *acc, double *phi) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    ext_one(p, x + 3 * i, acc ? acc + 3 * i : NULL, phi ? phi + i : NULL);
 }

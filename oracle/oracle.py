@@ -82,6 +82,7 @@ def lib():
                                                  vp, vp, vp]
             L.orc_leapfrog_loss_grad.restype = d
             L.orc_leapfrog_adjoint_path.argtypes = [i64, vp, vp, d, d, d, i64, vp, vp, vp]
+            L.orc_ext.argtypes = [i64, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -270,12 +271,43 @@ SYMPLECTIC6_WEIGHTS = (SYMPLECTIC6_W3, SYMPLECTIC6_W2, SYMPLECTIC6_W1, SYMPLECTI
                        SYMPLECTIC6_W1, SYMPLECTIC6_W2, SYMPLECTIC6_W3)
 
 
-def symplectic(m, x, v, eps, dt, nsteps, order, G=1.0, weights=None):
+# Sec. 2.1: the Galactic field of Allen & Santillan (1991) in their units
+# (length 1 kpc, mass 2.32e7 solar masses, velocity 10 km/s, G = 1): bulge
+# M_b = 606, b_b = 0.3873; disk M_d = 3690, a_d = 5.3178, b_d = 0.25; halo
+# M_h = 4615, a_h = 12, gamma = 2.02, cut at r = 100.
+ALLEN_SANTILLAN = {"G": 1.0, "center": (0.0, 0.0, 0.0),
+                   "m_bulge": 606.0, "b_bulge": 0.3873,
+                   "m_disk": 3690.0, "a_disk": 5.3178, "b_disk": 0.25,
+                   "m_halo": 4615.0, "a_halo": 12.0, "gamma": 2.02, "r_cut": 100.0}
+
+
+def _ext_params(ext):
+    e = dict(ALLEN_SANTILLAN)
+    e.update(ext or {})
+    return np.array([e["G"], *e["center"], e["m_bulge"], e["b_bulge"], e["m_disk"],
+                     e["a_disk"], e["b_disk"], e["m_halo"], e["a_halo"], e["gamma"],
+                     e["r_cut"]], dtype=np.float64)
+
+
+def ext_field(x, ext=None):
+    """Acceleration (n, 3) and potential (n,) of the external field at x;
+    ``ext`` overrides entries of ALLEN_SANTILLAN."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3))
+    n = x.shape[0]
+    acc = np.zeros((n, 3))
+    phi = np.zeros(n)
+    lib().orc_ext(n, _p(x), _p(_ext_params(ext)), _p(acc), _p(phi))
+    return acc, phi
+
+
+def symplectic(m, x, v, eps, dt, nsteps, order, G=1.0, weights=None, ext=None):
     """Fixed-step symplectic integration of every particle (Sec. 2.2).
     Order 2: one kick-drift-kick leapfrog step of length dt per step.
     Order 6: per step, leapfrog steps of lengths w_k dt for the seven
     weights in order (``weights`` replaces them, for tests that plant a
-    wrong set).  Returns (x, v) after nsteps."""
+    wrong set).  With ``ext`` (a dict of external-field parameters, {} for
+    Allen & Santillan's) the field's acceleration is added to the pair
+    sum in every kick (Sec. 2.1).  Returns (x, v) after nsteps."""
     if order == 2:
         ws = (1.0,)
     elif order == 6:
@@ -284,9 +316,19 @@ def symplectic(m, x, v, eps, dt, nsteps, order, G=1.0, weights=None):
         raise ValueError("order must be 2 or 6")
     x = _f64(x).copy()
     v = _f64(v).copy()
+
+    def total_acc(xx):
+        return acc(m, xx, eps, G=G) + ext_field(xx, ext)[0]
+
     for _ in range(int(nsteps)):
         for w in ws:
-            x, v = leapfrog(m, x, v, eps, w * dt, 1, G=G)
+            if ext is None:
+                x, v = leapfrog(m, x, v, eps, w * dt, 1, G=G)
+            else:
+                h = w * dt
+                v = v + total_acc(x) * h / 2.0
+                x = x + v * h
+                v = v + total_acc(x) * h / 2.0
     return x, v
 
 

@@ -35,6 +35,10 @@ MUTANTS = {
     "adjoint_mass_sign": ("om += -(g[3 * j + 0] * dx", "om += (g[3 * j + 0] * dx"),
     "adjoint_drift": ("for (size_t q = 0; q < n3; ++q) lv[q] += lx[q] * dt;", "for (size_t q = 0; q < n3; ++q) lv[q] += lx[q] * dt / 2.0;"),
     "adjoint_kick_order": ("orc_acc_vjp(n, m, xb, G, eps, g, tx, tm);", "orc_acc_vjp(n, m, xa, G, eps, g, tx, tm);"),
+    "ext_disk_vertical_factor": ("az -= f * dz * w / zeta;", "az -= f * dz;"),
+    "ext_halo_bracket_sign": ("* (Fc - Fq);", "* (Fq - Fc);"),
+    "ext_bulge_power": ("const double f = G * mb / (s2 * s);", "const double f = G * mb / s2;"),
+    "ext_halo_mass_exponent": ("const double Mr = mh * q * u / (1.0 + u);", "const double Mr = mh * u / (1.0 + u);"),
 }
 
 
@@ -52,6 +56,7 @@ def test_planted_mistake_is_caught(tmp_path, name):
     env = dict(os.environ, NBODY_ORACLE_SO=str(so), OMP_NUM_THREADS="4")
     r = subprocess.run(
         [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-         "tests/test_oracle_force.py", "tests/test_oracle_integrators.py"],
+         "tests/test_oracle_force.py", "tests/test_oracle_integrators.py",
+         "tests/test_oracle_external.py"],
         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
