@@ -675,7 +675,9 @@ def run_symplectic(args):
     lets the split-precision kernel take its tile-relative far field).
     Accuracy (split precision, generation order): relative energy error at
     t = 1/8 at equal force evaluations, sixth order with dt = 2^-7..2^-10
-    against the leapfrog with dt / 7."""
+    against the leapfrog with dt / 7.  Galactic field (Sec. 2.1): a cluster
+    of N particles on a circular orbit at 8.5 kpc in Allen & Santillan's
+    field, energy error in both precisions and the field's cost."""
     import torch
 
     from paper_0909_0879_gb300 import _lib, metrics
@@ -713,11 +715,37 @@ def run_symplectic(args):
                 row[f"dE_over_E_order{order}"] = abs(s.energy()[2] / E0 - 1.0)
         accuracy.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
+    # The paper's configuration (Sec. 2.1): a cluster orbiting in the Galactic
+    # field of Allen & Santillan (kpc, 2.32e7 solar masses, 10 km/s): Plummer,
+    # 1e5 solar masses, virial radius 10 pc, eps = 0.1 pc, on the circular
+    # orbit through (8.5, 0, 0); sixth order, dt = 2^-10 (1/16 of the crossing
+    # time), 32 steps; energy (with the field's) in both precisions, and the
+    # step time with and without the field.
+    mc, xc, vc = ics.plummer(n, 1007)
+    Mc, Lc = 0.00431, 0.01
+    mc, xc, vc = (mc * Mc, xc * Lc + np.array([8.5, 0.0, 0.0]),
+                  vc * np.sqrt(Mc / Lc) + np.array([0.0, 22.0, 0.0]))
+    galactic = []
+    for prec in args.precisions.split(","):
+        row = {"precision": prec}
+        for field in (True, False):
+            with _lib.NBody(mc, xc, vc, eps=1e-4, precision=prec) as s:
+                if field:
+                    s.set_external({})
+                    E0 = s.energy()[2]
+                    s.symplectic(6, 2.0**-10, 32)
+                    row["dE_over_E_32_steps"] = abs(s.energy()[2] / E0 - 1.0)
+                per_step = _time_symplectic(torch, s, 6, 2.0**-10, 16)
+            row["s_per_step_with_field" if field else "s_per_step_without_field"] = per_step
+        galactic.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
     out = {"metric": "interactions/s and energy error of the symplectic integrators",
            "unit": "interactions/s", "workload": f"uniform_sphere_salpeter_q1_n{n}_eps0.1d",
            "flops_per_interaction": metrics.FLOPS_PER_ACC_INTERACTION,
            "peak_basis": "FP32 lanes x 2 x 2070 MHz", "speed": speed,
-           "energy_at_t_1/8": accuracy}
+           "energy_at_t_1/8": accuracy,
+           "galactic_cluster": {"workload": f"plummer_n{n}_1e5msun_rv10pc_at_8.5kpc_allen_santillan",
+                                "rows": galactic}}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -11,7 +11,10 @@
  * advances the system with the 4th-order Hermite predictor-corrector and
  * power-of-two block time steps (the paper's individual per-particle time
  * steps, Sec. 2, strategy (ii); the Hermite scheme itself is Makino &
- * Aarseth 1992 and is not printed in the paper).
+ * Aarseth 1992 and is not printed in the paper), or with the paper's own
+ * fixed-step symplectic integrators (Sec. 2.2: the leapfrog and a
+ * sixth-order composition) and, optionally, its external Galactic field
+ * (Sec. 2.1).
  *
  * Conventions (every entry point):
  *  - Every call returns nb_status; NB_OK is 0.  On error a message is kept
@@ -185,9 +188,51 @@ nb_status nb_last_block_path(nb_ctx *ctx, int32_t *fused);
  * non-finite dt, nsteps < 0. */
 nb_status nb_symplectic(nb_ctx *ctx, int32_t order, double dt, int64_t nsteps);
 
+/* External Galactic field (paper Sec. 2.1: the pair forces are summed with
+ * the field of Allen & Santillan 1991, a spherical bulge and halo and an
+ * axisymmetric disk).  With d = x - center, r = |d|, R^2 = d_x^2 + d_y^2,
+ * z = d_z:
+ *   bulge (Plummer)        Phi = -G m_bulge / sqrt(r^2 + b_bulge^2)
+ *   disk (Miyamoto-Nagai)  Phi = -G m_disk / sqrt(R^2 + (a_disk
+ *                                + sqrt(z^2 + b_disk^2))^2)
+ *   halo                   enclosed mass M(r) = m_halo q^g / (1 + q^(g-1)),
+ *                          q = r / a_halo, g = gamma_halo, constant beyond
+ *                          r_cut; force -G M(r) d / r^3; potential
+ *                          -G M(r)/r - G m_halo / ((g-1) a_halo)
+ *                          [F(q_cut) - F(q)], F(q) = ln(1 + q^(g-1))
+ *                          - (g-1) / (1 + q^(g-1)), inside the cut and
+ *                          -G M(r_cut) / r beyond.
+ * All parameters are in the context's units (G is the field's own
+ * gravitational constant). */
+typedef struct nb_external {
+  double G;
+  double center[3];
+  double m_bulge, b_bulge;
+  double m_disk, a_disk, b_disk;
+  double m_halo, a_halo, gamma_halo, r_cut;
+} nb_external;
+
+/* Fill e with Allen & Santillan's (1991) parameters in their units (length
+ * 1 kpc, mass 2.32e7 solar masses, velocity 10 km/s, G = 1): m_bulge = 606,
+ * b_bulge = 0.3873, m_disk = 3690, a_disk = 5.3178, b_disk = 0.25,
+ * m_halo = 4615, a_halo = 12, gamma_halo = 2.02, r_cut = 100, centre at
+ * the origin.  The model's circular speed at 8.5 kpc is 220 km/s. */
+void nb_external_allen_santillan(nb_external *e);
+
+/* Set (e non-NULL, copied) or remove (NULL) the context's external field.
+ * While set: nb_symplectic adds its acceleration (FP64, at each particle's
+ * own position) to the pair sum in every kick and leaves the total in a;
+ * nb_energy adds sum_i m_i Phi(x_i) to the potential energy; the Hermite
+ * calls (nb_next_block, nb_predict, nb_step, nb_run_blocks) answer
+ * NB_ERR_STATE.  NB_ERR_INVALID_ARG: a non-finite parameter, a negative G,
+ * mass or a_disk, b_bulge, b_disk, a_halo or r_cut not positive, or
+ * gamma_halo <= 1. */
+nb_status nb_set_external(nb_ctx *ctx, const nb_external *e);
+
 /* Energy of the current (synchronised) state in FP64 on the GPU:
  * K = 1/2 sum m v^2, W = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)
- * (the softened pair potential consistent with the force).  Uses the
+ * (the softened pair potential consistent with the force), plus
+ * sum_i m_i Phi_ext(x_i) when an external field is set.  Uses the
  * particles' own stored x, v (not predicted).  Synchronises. */
 nb_status nb_energy(nb_ctx *ctx, double *kin, double *pot, double *tot);
 

@@ -42,6 +42,14 @@ class Config(C.Structure):
     ]
 
 
+class External(C.Structure):
+    _fields_ = [("G", C.c_double), ("center", C.c_double * 3),
+                ("m_bulge", C.c_double), ("b_bulge", C.c_double),
+                ("m_disk", C.c_double), ("a_disk", C.c_double), ("b_disk", C.c_double),
+                ("m_halo", C.c_double), ("a_halo", C.c_double), ("gamma_halo", C.c_double),
+                ("r_cut", C.c_double)]
+
+
 # (name, restype, argtypes) for every entry point in include/nbody.h
 _vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
 _P = C.POINTER
@@ -59,6 +67,8 @@ SIGNATURES = [
     ("nb_set_block_mode", C.c_int, [_vp, _i32]),
     ("nb_last_block_path", C.c_int, [_vp, _P(_i32)]),
     ("nb_symplectic", C.c_int, [_vp, _i32, _d, _i64]),
+    ("nb_external_allen_santillan", None, [_P(External)]),
+    ("nb_set_external", C.c_int, [_vp, _P(External)]),
     ("nb_energy", C.c_int, [_vp, _P(_d), _P(_d), _P(_d)]),
     ("nb_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -297,6 +307,24 @@ class NBody:
         steps of dt.  Afterwards x, v and a (= A(x)) are current; Hermite
         calls need set_state first."""
         _check(self._L.nb_symplectic(self._h, int(order), float(dt), int(nsteps)))
+
+    def set_external(self, ext=None):
+        """Set the external Galactic field (a dict of nb_external fields,
+        missing ones from Allen & Santillan's model; {} for that model
+        itself) or remove it (None)."""
+        if ext is None:
+            _check(self._L.nb_set_external(self._h, None))
+            return
+        e = External()
+        self._L.nb_external_allen_santillan(C.byref(e))
+        for k, val in ext.items():
+            if k == "center":
+                e.center[:] = [float(c) for c in val]
+            elif k == "gamma":
+                e.gamma_halo = float(val)
+            else:
+                setattr(e, k, float(val))
+        _check(self._L.nb_set_external(self._h, C.byref(e)))
 
     def run_until(self, t_end: float):
         """Block steps until every particle has reached t_end (a tick multiple

@@ -183,9 +183,11 @@ struct nb_ctx {
   int sym_order = 0;
   double sym_dt = 0.0;
   int64_t sym_graph_launches = 0;
+  bool sym_graph_stale = false;  // the field changed since the capture
   // nb_symplectic moved x and v: the Hermite fields (jerk, times, levels)
   // no longer belong to them until nb_set_state
   bool sym_moved = false;
+  ExtField ext;  // external Galactic field (symplectic integrators, energy)
   std::vector<void *> allocs;
 };
 
@@ -260,6 +262,9 @@ nb_status check_hermite(nb_ctx *c) {
   if (c->sym_moved)
     return fail(NB_ERR_STATE, "nb_symplectic moved the particles; nb_set_state must give the "
                               "Hermite state (jerk, times, levels) before Hermite steps");
+  if (c->ext.on)
+    return fail(NB_ERR_STATE, "the Hermite integrator has no external field; remove it with "
+                              "nb_set_external(ctx, NULL) first");
   return NB_OK;
 }
 
@@ -909,7 +914,7 @@ nb_status queue_acc_all(nb_ctx *c, cudaStream_t s, int64_t *launches) {
 
 nb_status queue_kick_drift(nb_ctx *c, cudaStream_t s, double h, double d, bool rec,
                            int64_t *launches) {
-  NB_CUDA(launch_kick_drift(c->n, c->n_jt, h, d, rec, c->a, c->v, c->x, c->m,
+  NB_CUDA(launch_kick_drift(c->n, c->n_jt, h, d, rec, c->ext, c->a, c->v, c->x, c->m,
                             c->cfg.precision, c->jhi, c->jlo, c->jvel, c->jrel, c->tinfo, s));
   *launches += 1;
   return NB_OK;
@@ -959,6 +964,58 @@ nb_status capture_symplectic(nb_ctx *c, const double *w, int S, double dt) {
 
 }  // namespace
 
+extern "C" void nb_external_allen_santillan(nb_external *e) {
+  if (!e) return;
+  // Allen & Santillan (1991): length 1 kpc, mass 2.32e7 solar masses,
+  // velocity 10 km/s, G = 1
+  e->G = 1.0;
+  e->center[0] = e->center[1] = e->center[2] = 0.0;
+  e->m_bulge = 606.0;
+  e->b_bulge = 0.3873;
+  e->m_disk = 3690.0;
+  e->a_disk = 5.3178;
+  e->b_disk = 0.25;
+  e->m_halo = 4615.0;
+  e->a_halo = 12.0;
+  e->gamma_halo = 2.02;
+  e->r_cut = 100.0;
+}
+
+extern "C" nb_status nb_set_external(nb_ctx *c, const nb_external *e) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  ExtField f;
+  if (e) {
+    const double vals[] = {e->G,      e->center[0], e->center[1], e->center[2],
+                           e->m_bulge, e->b_bulge,  e->m_disk,    e->a_disk,
+                           e->b_disk,  e->m_halo,   e->a_halo,    e->gamma_halo,
+                           e->r_cut};
+    if (!finite_all(vals, static_cast<int64_t>(sizeof(vals) / sizeof(vals[0]))))
+      return fail(NB_ERR_INVALID_ARG, "non-finite external-field parameter");
+    if (e->G < 0 || e->m_bulge < 0 || e->m_disk < 0 || e->m_halo < 0 || e->a_disk < 0)
+      return fail(NB_ERR_INVALID_ARG, "negative G, mass or disk scale length");
+    if (!(e->b_bulge > 0) || !(e->b_disk > 0) || !(e->a_halo > 0) || !(e->r_cut > 0) ||
+        !(e->gamma_halo > 1))
+      return fail(NB_ERR_INVALID_ARG,
+                  "b_bulge, b_disk, a_halo and r_cut must be positive and gamma_halo > 1");
+    f.on = 1;
+    f.G = e->G;
+    for (int k = 0; k < 3; ++k) f.c[k] = e->center[k];
+    f.mb = e->m_bulge;
+    f.bb = e->b_bulge;
+    f.md = e->m_disk;
+    f.ad = e->a_disk;
+    f.bd = e->b_disk;
+    f.mh = e->m_halo;
+    f.ah = e->a_halo;
+    f.gam = e->gamma_halo;
+    f.rcut = e->r_cut;
+  }
+  c->ext = f;
+  c->sym_graph_stale = true;
+  return NB_OK;
+}
+
 extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t nsteps) {
   Range r("nb_symplectic");
   nb_status s = check_ctx(c);
@@ -982,16 +1039,22 @@ extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t 
   c->t_pred = -1;
   if (nsteps > 0) {
     if (!c->sym_graph || c->sym_order != order || c->sym_dt != dt ||
-        c->sym_graph_part != c->part) {
+        c->sym_graph_part != c->part || c->sym_graph_stale) {
       s = capture_symplectic(c, w, S, dt);
       if (s != NB_OK) return s;
       c->sym_order = order;
       c->sym_dt = dt;
       c->sym_graph_part = c->part;
+      c->sym_graph_stale = false;
     }
     for (int64_t k = 0; k < nsteps; ++k) NB_CUDA(cudaGraphLaunch(c->sym_graph, c->stream));
     c->launches += nsteps * c->sym_graph_launches;
     c->interactions += nsteps * S * c->n * c->n;
+  }
+  // the acceleration left in the state is the total one at the final x
+  if (c->ext.on) {
+    NB_CUDA(launch_ext_add(c->n, c->ext, c->x, c->a, c->stream));
+    c->launches += 1;
   }
   return sync_ctx(c);
 }
@@ -1100,18 +1163,19 @@ nb_status nb_energy(nb_ctx *c, double *kin, double *pot, double *tot) {
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   int nl = 0;
-  double *d_out = c->red + energy_scratch_doubles(c->n) - 2;
-  NB_CUDA(launch_energy(c->n, c->m, c->x, c->v, c->cfg.G, c->cfg.eps, c->red, d_out, c->stream,
-                        &nl));
+  double *d_out = c->red + energy_scratch_doubles(c->n) - 3;
+  NB_CUDA(launch_energy(c->n, c->m, c->x, c->v, c->cfg.G, c->cfg.eps, c->ext, c->red, d_out,
+                        c->stream, &nl));
   c->launches += nl;
-  NB_CUDA(cudaMemcpyAsync(c->h_energy, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+  NB_CUDA(cudaMemcpyAsync(c->h_energy, d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
   s = sync_ctx(c);
   if (s != NB_OK) return s;
+  const double w = c->h_energy[1] + c->h_energy[2];
   if (kin) *kin = c->h_energy[0];
-  if (pot) *pot = c->h_energy[1];
-  if (tot) *tot = c->h_energy[0] + c->h_energy[1];
-  if (!std::isfinite(c->h_energy[0]) || !std::isfinite(c->h_energy[1]))
+  if (pot) *pot = w;
+  if (tot) *tot = c->h_energy[0] + w;
+  if (!std::isfinite(c->h_energy[0]) || !std::isfinite(w))
     return fail(NB_ERR_NUMERIC, "non-finite energy");
   return NB_OK;
 }

@@ -486,5 +486,66 @@ __device__ __forceinline__ void correct_one(
                block_steps, n_clamped, lev_cnt);
 }
 
+// External Galactic field of Allen & Santillan (1991) at position x, FP64:
+// acceleration into a (added) and, when phi is set, the potential.  With
+// d = x - centre, r = |d|, R^2 = d_x^2 + d_y^2, z = d_z:
+//   bulge (Plummer)          Phi = -G M_b / sqrt(r^2 + b_b^2)
+//   disk (Miyamoto-Nagai)    Phi = -G M_d / sqrt(R^2 + (a_d + sqrt(z^2 + b_d^2))^2)
+//   halo                     M(r) = M_h q^gamma / (1 + q^(gamma-1)), q = r / a_h,
+//                            held at M(r_cut) beyond r_cut; force -G M(r) d / r^3;
+//                            Phi = -G M(r) / r - G M_h / ((gamma-1) a_h) (F(q_cut) - F(q))
+//                            inside the cut, F(q) = ln(1 + q^(gamma-1))
+//                            - (gamma-1) / (1 + q^(gamma-1)); -G M(r_cut) / r beyond.
+__device__ __forceinline__ void ext_field(const ExtField &E, const double x[3], double a[3],
+                                          double *phi) {
+  const double dx = x[0] - E.c[0], dy = x[1] - E.c[1], dz = x[2] - E.c[2];
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double r = sqrt(r2);
+  double ph = 0.0;
+  {
+    const double s2 = r2 + E.bb * E.bb;
+    const double s = sqrt(s2);
+    const double f = E.G * E.mb / (s2 * s);
+    a[0] -= f * dx;
+    a[1] -= f * dy;
+    a[2] -= f * dz;
+    ph -= E.G * E.mb / s;
+  }
+  {
+    const double zeta = sqrt(dz * dz + E.bd * E.bd);
+    const double w = E.ad + zeta;
+    const double D2 = dx * dx + dy * dy + w * w;
+    const double D = sqrt(D2);
+    const double f = E.G * E.md / (D2 * D);
+    a[0] -= f * dx;
+    a[1] -= f * dy;
+    a[2] -= f * dz * w / zeta;
+    ph -= E.G * E.md / D;
+  }
+  {
+    const double rr = r < E.rcut ? r : E.rcut;
+    const double q = rr / E.ah;
+    const double u = pow(q, E.gam - 1.0);
+    const double Mr = E.mh * q * u / (1.0 + u);
+    if (r > 0.0) {
+      const double f = E.G * Mr / (r2 * r);
+      a[0] -= f * dx;
+      a[1] -= f * dy;
+      a[2] -= f * dz;
+    }
+    if (phi) {
+      if (r < E.rcut) {
+        const double uc = pow(E.rcut / E.ah, E.gam - 1.0);
+        const double Fc = log(1.0 + uc) - (E.gam - 1.0) / (1.0 + uc);
+        const double Fq = log(1.0 + u) - (E.gam - 1.0) / (1.0 + u);
+        ph += (r > 0.0 ? -E.G * Mr / r : 0.0) - E.G * E.mh / ((E.gam - 1.0) * E.ah) * (Fc - Fq);
+      } else {
+        ph -= E.G * Mr / r;
+      }
+      *phi = ph;
+    }
+  }
+}
+
 }  // namespace dev
 }  // namespace nbi

@@ -310,6 +310,22 @@ __global__ void potential_kernel(int64_t n, const double *__restrict__ m,
 }
 
 // One CTA sums part[0..cnt) in a fixed order and writes out[slot].
+// e_i = m_i Phi_ext(x_i); the block's sum goes to part[blockIdx.x].
+__global__ void ext_potential_kernel(int64_t n, const ExtField E, const double *__restrict__ m,
+                                     const double *__restrict__ x, double *__restrict__ part) {
+  __shared__ double sh[kEnThreads];
+  double s = 0.0;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double xv[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+    double av[3] = {0.0, 0.0, 0.0}, phi = 0.0;
+    dev::ext_field(E, xv, av, &phi);
+    s = m[i] * phi;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void final_sum_kernel(int64_t cnt, const double *__restrict__ part, double scale,
                                  double *__restrict__ out, int slot) {
   __shared__ double sh[kEnThreads];
@@ -395,19 +411,22 @@ cudaError_t launch_next_block(int64_t n, const int64_t *t_tick, const int32_t *l
   return cudaGetLastError();
 }
 
-int64_t energy_scratch_doubles(int64_t n) { return 2 * ((n + kEnThreads - 1) / kEnThreads) + 2; }
+int64_t energy_scratch_doubles(int64_t n) { return 3 * ((n + kEnThreads - 1) / kEnThreads) + 3; }
 
 cudaError_t launch_energy(int64_t n, const double *m, const double *x, const double *v,
-                          double G, double eps, double *red, double *d_out, cudaStream_t s,
-                          int *launches) {
+                          double G, double eps, const ExtField &E, double *red, double *d_out,
+                          cudaStream_t s, int *launches) {
   const int64_t nb = (n + kEnThreads - 1) / kEnThreads;
   double *pk = red;
   double *pw = red + nb;
+  double *pe = red + 2 * nb;
   kinetic_kernel<<<static_cast<unsigned>(nb), kEnThreads, 0, s>>>(n, m, v, pk);
   potential_kernel<<<static_cast<unsigned>(nb), kEnThreads, 0, s>>>(n, m, x, eps * eps, pw);
+  if (E.on) ext_potential_kernel<<<static_cast<unsigned>(nb), kEnThreads, 0, s>>>(n, E, m, x, pe);
   final_sum_kernel<<<1, kEnThreads, 0, s>>>(nb, pk, 1.0, d_out, 0);
   final_sum_kernel<<<1, kEnThreads, 0, s>>>(nb, pw, -G, d_out, 1);
-  if (launches) *launches += 4;
+  final_sum_kernel<<<1, kEnThreads, 0, s>>>(E.on ? nb : 0, pe, 1.0, d_out, 2);
+  if (launches) *launches += E.on ? 6 : 5;
   return cudaGetLastError();
 }
 

@@ -44,6 +44,15 @@ struct ForceArgs {
   int64_t lo = 0, hi = 0;
 };
 
+// External Galactic field (Allen & Santillan 1991; parameters as in
+// nb_external of include/nbody.h).  on = 0: no field.
+struct ExtField {
+  int on = 0;
+  double G = 0.0, c[3] = {0.0, 0.0, 0.0};
+  double mb = 0.0, bb = 0.0;            // bulge
+  double md = 0.0, ad = 0.0, bd = 0.0;  // disk
+  double mh = 0.0, ah = 1.0, gam = 2.0, rcut = 1.0;  // halo
+};
 // Layout of the context's small device control array (int64 slots).
 constexpr int kCtlTnext = 0;    // t_next of the current block (ticks); -1 = stop
 constexpr int kCtlNact = 1;     // active count of the current block
@@ -172,10 +181,12 @@ cudaError_t launch_next_block(int64_t n, const int64_t *t_tick,
                               int32_t *blk_count, int64_t *d_scal,
                               cudaStream_t s, int *launches);
 int64_t next_block_scratch_ints(int64_t n);
-// Kinetic and softened potential energy in FP64; result in d_out[0..1].
+// Kinetic and softened potential energy in FP64 into d_out[0..1], and the
+// external field's potential energy sum_i m_i Phi(x_i) into d_out[2] (0
+// when E.on is 0).
 cudaError_t launch_energy(int64_t n, const double *m, const double *x,
-                          const double *v, double G, double eps, double *red,
-                          double *d_out, cudaStream_t s, int *launches);
+                          const double *v, double G, double eps, const ExtField &E,
+                          double *red, double *d_out, cudaStream_t s, int *launches);
 int64_t energy_scratch_doubles(int64_t n);
 
 // --- Fused device-resident block steps (nb_blockstep.cu) ---
@@ -226,10 +237,14 @@ constexpr int kEndThreads = 256;
 // Stage weights of the scheme of the given order into w (at most 7);
 // returns the stage count (1 for order 2, 7 for order 6, 0 otherwise).
 int symplectic_stages(int order, double *w);
-// v += h a, x += d v for every particle (a factor of 0 skips its update);
-// with rec set also the j-records and, when jrel is set, the tile frames.
+// v += h (a + a_ext(x)), x += d v for every particle (a factor of 0 skips
+// its update; a_ext only when E.on); with rec set also the j-records and,
+// when jrel is set, the tile frames.
 cudaError_t launch_kick_drift(int64_t n, int64_t n_jt, double h, double d, bool rec,
-                              const double *a, double *v, double *x, const double *m, int prec,
-                              float4 *jhi, float4 *jlo, float4 *jvel, float4 *jrel,
-                              float4 *tinfo, cudaStream_t s);
+                              const ExtField &E, const double *a, double *v, double *x,
+                              const double *m, int prec, float4 *jhi, float4 *jlo,
+                              float4 *jvel, float4 *jrel, float4 *tinfo, cudaStream_t s);
+// a += a_ext(x) for every particle.
+cudaError_t launch_ext_add(int64_t n, const ExtField &E, const double *x, double *a,
+                           cudaStream_t s);
 }  // namespace nbi

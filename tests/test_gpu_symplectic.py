@@ -163,3 +163,73 @@ def test_symplectic6_energy_at_bench_size(nb, oracle_mod):
             assert cond.max() <= TOL["ds"]
     print("dE/E order 2 %.3e, order 6 %.3e" % (dE[2], dE[6]))
     assert dE[6] < dE[2]
+
+
+def _cluster_in_galaxy(n, seed):
+    """A Plummer cluster of 1e5 solar masses (0.00431 units of 2.32e7) and
+    virial radius 10 pc, on the circular orbit through (8.5, 0, 0) kpc of
+    the Allen & Santillan field (22 units of 10 km/s)."""
+    m, x, v = ics.plummer(n, seed)
+    M, L = 0.00431, 0.01
+    return m * M, x * L + np.array([8.5, 0.0, 0.0]), v * np.sqrt(M / L) + np.array([0.0, 22.0, 0.0])
+
+
+def test_external_field_cluster_matches_oracle(nb, oracle_mod):
+    """The paper's configuration (Sec. 2.1): a star cluster orbiting in the
+    Galactic field.  N = 1000, eps = 1e-3 kpc (the closest pairs' orbital
+    time, sqrt(eps^3 / m) = 0.015, stays far above the run's 0.004), four
+    sixth-order steps of 1e-3 (1/15 of the cluster's crossing time), split
+    precision, against
+    the oracle with the same field, within the force-error bound; the
+    acceleration left in the state is pair sum + field at the final
+    positions; the energy includes sum m Phi_ext.  The same run in FP32
+    (positions rounded at 8.5 kpc, separations of 1e-3) is far less
+    accurate, which is the paper's case for extended precision."""
+    n, eps, dt, ns = 1000, 1e-3, 1e-3, 4
+    T = dt * ns
+    m, x, v = _cluster_in_galaxy(n, 21)
+    xo, vo = oracle_mod.symplectic(m, x, v, eps, dt, ns, 6, ext={})
+    aabs = _aabs_max(oracle_mod, m, (x, xo), eps)
+    errs = {}
+    for prec in ("ds", "fp32"):
+        with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+            s.set_external({})
+            k0, w0, e0 = s.energy()
+            s.symplectic(6, dt, ns)
+            st = s.get_state(want=("x", "v", "a"))
+        ex = np.linalg.norm(st["x"] - xo, axis=1)
+        errs[prec] = ex.max()
+        if prec != "ds":
+            continue
+        ev = np.linalg.norm(st["v"] - vo, axis=1)
+        print("ds max dx / bound %.3g, dv / bound %.3g"
+              % ((ex / (T * T * TOL["ds"] * aabs)).max(), (ev / (2 * T * TOL["ds"] * aabs)).max()))
+        assert np.all(ex <= T * T * TOL["ds"] * aabs)
+        assert np.all(ev <= 2 * T * TOL["ds"] * aabs)
+        zv = np.zeros_like(xo)
+        ao = oracle_mod.force_jerk(m, st["x"], zv, eps)[0] + oracle_mod.ext_field(st["x"])[0]
+        cond = np.linalg.norm(st["a"] - ao, axis=1) / _aabs_max(oracle_mod, m, (st["x"],), eps)
+        assert cond.max() <= TOL["ds"]
+        K, W, _ = oracle_mod.energy(m, x, v, eps)
+        W_ext = float(np.sum(m * oracle_mod.ext_field(x)[1]))
+        assert abs(k0 - K) <= 1e-14 * abs(K)
+        assert abs(w0 - (W + W_ext)) <= 1e-12 * abs(W + W_ext)
+    print("max position error ds %.3e fp32 %.3e" % (errs["ds"], errs["fp32"]))
+    assert errs["fp32"] > 10.0 * errs["ds"]
+
+
+def test_external_field_protocol(nb):
+    """Invalid parameters are rejected; Hermite calls are refused while a
+    field is set and work again once it is removed."""
+    m, x, v = _cluster_in_galaxy(300, 22)
+    with nb.NBody(m, x, v, eps=1e-4, precision="ds") as s:
+        for bad in ({"gamma": 1.0}, {"b_disk": 0.0}, {"m_halo": -1.0}, {"G": float("inf")}):
+            with pytest.raises(nb.NBodyError) as ei:
+                s.set_external(bad)
+            assert ei.value.status == 1
+        s.set_external({})
+        with pytest.raises(nb.NBodyError) as ei:
+            s.step()
+        assert ei.value.status == 2
+        s.set_external(None)
+        s.step()
