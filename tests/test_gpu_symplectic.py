@@ -77,19 +77,48 @@ def test_symplectic_matches_oracle(nb, oracle_mod, prec):
 
 
 @pytest.mark.parametrize("prec", ["ds", "fp32"])
-@pytest.mark.parametrize("n", [1000, 70001])
-def test_acceleration_only_kernel_equals_jerk_kernel(nb, prec, n):
+@pytest.mark.parametrize("n,eps", [(1000, 1e-3), (70001, 1e-3), (1000, 0.0), (70001, 0.0)])
+def test_acceleration_only_kernel_equals_jerk_kernel(nb, prec, n, eps):
     """nsteps = 0 only evaluates A(x) with the acceleration-only kernel; the
     acceleration sums are the same operations in the same order as those
     of the acceleration + jerk kernel that nb_init ran at the same
-    positions with the same shape and grid: bit-identical."""
+    positions with the same shape and grid: bit-identical.  eps = 0 takes
+    the masked shapes."""
     m, x, v = ics.plummer(n, 12)
-    with nb.NBody(m, x, v, eps=1e-3, precision=prec) as s:
+    with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
         a0 = s.get_state(want=("a",))["a"]
         s.symplectic(6, 1.0 / 64, 0)
         a1 = s.get_state(want=("a", "x"))
     assert np.array_equal(a1["x"], x)
     assert np.array_equal(a1["a"], a0)
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+def test_kepler_two_body_on_gpu(nb, oracle_mod, prec):
+    """Two bodies (eps = 0, the masked shapes; n = 2, one padded tile) on an
+    e = 0.5 orbit for 1000 sixth-order steps of 2/1000 (graph replayed
+    1000 times): the GPU follows the oracle's discrete map within the
+    force-error bound and both stay within 1e-6 of Kepler's closed form."""
+    import math
+
+    m = np.array([0.5, 0.5])
+    rp, vp = 0.5, math.sqrt(3.0)
+    x = np.array([[-rp / 2, 0.0, 0.0], [rp / 2, 0.0, 0.0]])
+    v = np.array([[0.0, -vp / 2, 0.0], [0.0, vp / 2, 0.0]])
+    dt, ns = 2.0 / 1000, 1000
+    with nb.NBody(m, x, v, eps=0.0, precision=prec) as s:
+        s.symplectic(6, dt, ns)
+        st = s.get_state(want=("x",))
+    xo, _ = oracle_mod.symplectic(m, x, v, 0.0, dt, ns, 6)
+    E = 2.0  # Kepler's equation at t = 2, a = 1, e = 0.5, n = 1
+    for _ in range(60):
+        E -= (E - 0.5 * math.sin(E) - 2.0) / (1 - 0.5 * math.cos(E))
+    rel = np.array([math.cos(E) - 0.5, math.sqrt(0.75) * math.sin(E), 0.0])
+    tol = TOL[prec]
+    # |a| <= 1 / r_p^2 = 4 along the orbit, T = 2: T^2 tol |a|
+    assert np.linalg.norm(st["x"] - xo) <= 4.0 * 4.0 * tol * 4.0
+    assert np.linalg.norm((xo[1] - xo[0]) - rel) < 1e-6
+    assert np.linalg.norm((st["x"][1] - st["x"][0]) - rel) < 1e-6 + 64 * tol
 
 
 def test_symplectic6_reversible_on_gpu(nb, oracle_mod):
