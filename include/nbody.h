@@ -168,7 +168,8 @@ nb_status nb_last_block_path(nb_ctx *ctx, int32_t *fused);
  * nsteps steps of length dt (any finite value; a negative dt integrates
  * backwards) of the scheme of the given order, on the context's FP64
  * state with forces in its precision (FP32 or split precision, softening
- * eps, no jerk).
+ * eps, no jerk; the built-in force shapes, not a forced variant or an
+ * installed tuning table).
  *   order 2: kick-drift-kick leapfrog, one force evaluation per step;
  *   order 6: the symmetric composition of seven leapfrog steps of lengths
  *            w_k dt with the sixth-order weights of Kinoshita, Yoshida &
