@@ -281,19 +281,41 @@ int orc_next_level(int lev_old, int lev_want, int64_t t_new, int lev_min) {
   return lev_old;
 }
 
+static void ext_one(const double *p, const double *xi, const double *vi, double *acc,
+                    double *jerk, double *phi);
+
 /* Initial acceleration, jerk and level for every particle at t = 0:
- * dt0 = eta_start |a| / |j|. */
-void orc_hermite_init(int64_t n, const double *m, const double *x,
-                      const double *v, double G, double eps, double eta_start,
-                      int lev_min, int lev_max, double *a, double *jk,
-                      int32_t *lev, int64_t *t_tick) {
+ * dt0 = eta_start |a| / |j|.  ext (13 doubles, see ext_one) or NULL: the
+ * external field's acceleration and jerk are added to the pair sums. */
+void orc_hermite_init_ext(int64_t n, const double *m, const double *x,
+                          const double *v, double G, double eps, double eta_start,
+                          int lev_min, int lev_max, const double *ext, double *a,
+                          double *jk, int32_t *lev, int64_t *t_tick) {
   orc_force_jerk(n, m, x, v, G, eps, n, NULL, a, jk);
+  if (ext) {
+    for (int64_t i = 0; i < n; ++i) {
+      double ea[3], ej[3];
+      ext_one(ext, x + 3 * i, v + 3 * i, ea, ej, NULL);
+      for (int c = 0; c < 3; ++c) {
+        a[3 * i + c] += ea[c];
+        jk[3 * i + c] += ej[c];
+      }
+    }
+  }
   for (int64_t i = 0; i < n; ++i) {
     double dt0 = eta_start * norm3(a + 3 * i) / norm3(jk + 3 * i);
     int cl = 0;
     lev[i] = orc_level_from_dt(dt0, lev_min, lev_max, &cl);
     t_tick[i] = 0;
   }
+}
+
+void orc_hermite_init(int64_t n, const double *m, const double *x,
+                      const double *v, double G, double eps, double eta_start,
+                      int lev_min, int lev_max, double *a, double *jk,
+                      int32_t *lev, int64_t *t_tick) {
+  orc_hermite_init_ext(n, m, x, v, G, eps, eta_start, lev_min, lev_max, NULL, a, jk, lev,
+                       t_tick);
 }
 
 /* One block step.
@@ -307,14 +329,16 @@ void orc_hermite_init(int64_t n, const double *m, const double *x,
  * the active set, and, if block_levels is non-zero, choose new levels with
  * the Aarseth criterion; otherwise keep the levels (shared fixed dt).
  * Returns n_act; writes t_next and the active list; adds to *n_clamped the
- * number of particles whose criterion fell below 2^-lev_max. */
-int64_t orc_block_step(int64_t n, const double *m, double *x, double *v,
-                       double *a, double *jk, int64_t *t_tick, int32_t *lev,
-                       double G, double eps, double eta, int lev_min,
-                       int lev_max, int block_levels, int64_t replay_t_next,
-                       int64_t replay_n_act, const int64_t *replay_act,
-                       int64_t *t_next_out, int64_t *act_out,
-                       int64_t *n_clamped) {
+ * number of particles whose criterion fell below 2^-lev_max.  ext (13
+ * doubles, see ext_one) or NULL: the external field's acceleration and jerk
+ * at the predicted position and velocity are added to the pair sums. */
+int64_t orc_block_step_ext(int64_t n, const double *m, double *x, double *v,
+                           double *a, double *jk, int64_t *t_tick, int32_t *lev,
+                           double G, double eps, double eta, int lev_min,
+                           int lev_max, int block_levels, int64_t replay_t_next,
+                           int64_t replay_n_act, const int64_t *replay_act,
+                           const double *ext, int64_t *t_next_out, int64_t *act_out,
+                           int64_t *n_clamped) {
   const double tick = ldexp(1.0, -ORC_TICKS_LOG2);
   int64_t t_next, n_act = 0;
   if (replay_n_act >= 0) {
@@ -344,6 +368,17 @@ int64_t orc_block_step(int64_t n, const double *m, double *x, double *v,
   double *a1 = (double *)malloc(sizeof(double) * 3 * (size_t)(n_act > 0 ? n_act : 1));
   double *j1 = (double *)malloc(sizeof(double) * 3 * (size_t)(n_act > 0 ? n_act : 1));
   orc_force_jerk(n, m, xp, vp, G, eps, n_act, act_out, a1, j1);
+  if (ext) {
+    for (int64_t k = 0; k < n_act; ++k) {
+      const int64_t i = act_out[k];
+      double ea[3], ej[3];
+      ext_one(ext, xp + 3 * i, vp + 3 * i, ea, ej, NULL);
+      for (int c = 0; c < 3; ++c) {
+        a1[3 * k + c] += ea[c];
+        j1[3 * k + c] += ej[c];
+      }
+    }
+  }
 
   int64_t clamped_here = 0;
   for (int64_t k = 0; k < n_act; ++k) {
@@ -373,6 +408,18 @@ int64_t orc_block_step(int64_t n, const double *m, double *x, double *v,
   free(a1);
   free(j1);
   return n_act;
+}
+
+int64_t orc_block_step(int64_t n, const double *m, double *x, double *v,
+                       double *a, double *jk, int64_t *t_tick, int32_t *lev,
+                       double G, double eps, double eta, int lev_min,
+                       int lev_max, int block_levels, int64_t replay_t_next,
+                       int64_t replay_n_act, const int64_t *replay_act,
+                       int64_t *t_next_out, int64_t *act_out,
+                       int64_t *n_clamped) {
+  return orc_block_step_ext(n, m, x, v, a, jk, t_tick, lev, G, eps, eta, lev_min, lev_max,
+                            block_levels, replay_t_next, replay_n_act, replay_act, NULL,
+                            t_next_out, act_out, n_clamped);
 }
 
 /* Shared fixed step dt = 2^-lev for nsteps steps (every particle active). */
@@ -535,15 +582,20 @@ double orc_leapfrog_loss_grad(int64_t n, const double *m, const double *x0,
  *          for r < r_cut with q = r / a_h and
  *          F(q) = -(gamma-1) / (1 + q^(gamma-1)) + ln(1 + q^(gamma-1)),
  *          and -G M(r_cut) / r beyond (so that dPhi_h/dr = G M(r) / r^2).
- * acc (3) and phi (1) may be NULL. */
-static void ext_one(const double *p, const double *xi, double *acc, double *phi) {
+ * The jerk is the time derivative of the acceleration along the velocity
+ * vi, d a(x + vi t)/dt at t = 0, written out per component below.
+ * acc (3), jerk (3, needs vi) and phi (1) may be NULL. */
+static void ext_one(const double *p, const double *xi, const double *vi, double *acc,
+                    double *jerk, double *phi) {
   const double G = p[0];
   const double dx = xi[0] - p[1], dy = xi[1] - p[2], dz = xi[2] - p[3];
   const double mb = p[4], bb = p[5], md = p[6], ad = p[7], bd = p[8];
   const double mh = p[9], ah = p[10], gam = p[11], rcut = p[12];
   const double r2 = dx * dx + dy * dy + dz * dz;
   const double r = sqrt(r2);
+  const double vx = vi ? vi[0] : 0.0, vy = vi ? vi[1] : 0.0, vz = vi ? vi[2] : 0.0;
   double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+  double jx = 0.0, jy = 0.0, jz = 0.0;
   /* bulge: -grad of -G M_b (r^2 + b^2)^(-1/2) */
   {
     const double s2 = r2 + bb * bb;
@@ -553,6 +605,11 @@ static void ext_one(const double *p, const double *xi, double *acc, double *phi)
     ay -= f * dy;
     az -= f * dz;
     ph -= G * mb / s;
+    /* d/dt of -G M d / s^3: -G M (v / s^3 - 3 (d.v) d / s^5) */
+    const double c = 3.0 * (dx * vx + dy * vy + dz * vz) / s2;
+    jx -= f * (vx - c * dx);
+    jy -= f * (vy - c * dy);
+    jz -= f * (vz - c * dz);
   }
   /* disk */
   {
@@ -565,6 +622,15 @@ static void ext_one(const double *p, const double *xi, double *acc, double *phi)
     ay -= f * dy;
     az -= f * dz * w / zeta;
     ph -= G * md / D;
+    /* with g = d_z w / zeta: dD/dt = (d_x v_x + d_y v_y + w d_z v_z / zeta) / D,
+     * dg/dt = v_z (1 + a_d b_d^2 / zeta^3); a = -G M_d (d_x, d_y, g) / D^3 */
+    const double Ddot = (dx * vx + dy * vy + w * dz * vz / zeta) / D;
+    const double g = dz * w / zeta;
+    const double gdot = vz * (1.0 + ad * bd * bd / (zeta * zeta * zeta));
+    const double c = 3.0 * Ddot / D;
+    jx -= f * (vx - c * dx);
+    jy -= f * (vy - c * dy);
+    jz -= f * (gdot - c * g);
   }
   /* halo */
   {
@@ -577,6 +643,14 @@ static void ext_one(const double *p, const double *xi, double *acc, double *phi)
       ax -= f * dx;
       ay -= f * dy;
       az -= f * dz;
+      /* d/dt of -G M(r) d / r^3 with dr/dt = d.v / r:
+       * -G [M v / r^3 + (M'(r) - 3 M / r) (d.v) d / r^4];
+       * M'(r) = M_h q^(gamma-1) (gamma + u) / ((1 + u)^2 a_h) inside the cut */
+      const double Mp = r < rcut ? mh * u * (gam + u) / ((1.0 + u) * (1.0 + u) * ah) : 0.0;
+      const double c = (Mp - 3.0 * Mr / r) * (dx * vx + dy * vy + dz * vz) / (r2 * r2);
+      jx -= f * vx + G * c * dx;
+      jy -= f * vy + G * c * dy;
+      jz -= f * vz + G * c * dz;
     }
     if (r < rcut) {
       const double qc = rcut / ah;
@@ -593,12 +667,20 @@ static void ext_one(const double *p, const double *xi, double *acc, double *phi)
     acc[1] = ay;
     acc[2] = az;
   }
+  if (jerk) {
+    jerk[0] = jx;
+    jerk[1] = jy;
+    jerk[2] = jz;
+  }
   if (phi) *phi = ph;
 }
 
-/* Acceleration (n,3) and potential (n) of the external field at x. */
-void orc_ext(int64_t n, const double *x, const double *p, double *acc, double *phi) {
+/* Acceleration (n,3), potential (n) and, with v, jerk (n,3) of the external
+ * field at x; any output may be NULL. */
+void orc_ext(int64_t n, const double *x, const double *v, const double *p, double *acc,
+             double *jerk, double *phi) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i)
-    ext_one(p, x + 3 * i, acc ? acc + 3 * i : NULL, phi ? phi + i : NULL);
+    ext_one(p, x + 3 * i, v ? v + 3 * i : NULL, acc ? acc + 3 * i : NULL,
+            (jerk && v) ? jerk + 3 * i : NULL, phi ? phi + i : NULL);
 }

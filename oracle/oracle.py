@@ -82,7 +82,13 @@ def lib():
                                                  vp, vp, vp]
             L.orc_leapfrog_loss_grad.restype = d
             L.orc_leapfrog_adjoint_path.argtypes = [i64, vp, vp, d, d, d, i64, vp, vp, vp]
-            L.orc_ext.argtypes = [i64, vp, vp, vp, vp]
+            L.orc_ext.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+            L.orc_hermite_init_ext.argtypes = [i64, vp, vp, vp, d, d, d, C.c_int, C.c_int,
+                                               vp, vp, vp, vp, vp]
+            L.orc_block_step_ext.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, d, d, d,
+                                             C.c_int, C.c_int, C.c_int, i64, i64, vp, vp,
+                                             vp, vp, vp]
+            L.orc_block_step_ext.restype = i64
             _lib = L
     return _lib
 
@@ -194,10 +200,12 @@ def next_level(lev_old, lev_want, t_new, lev_min=3):
 class HermiteState:
     """FP64 state of a Hermite-4 integration in the oracle (arrays owned by
     Python).  ``block_levels`` selects the Aarseth block-step scheme; with it
-    off every particle keeps its level (shared fixed dt = 2^-lev)."""
+    off every particle keeps its level (shared fixed dt = 2^-lev).  ``ext``
+    (a dict of external-field parameters, {} for Allen & Santillan's) adds
+    the field's acceleration and jerk to the pair sums (Sec. 2.1)."""
 
     def __init__(self, m, x, v, eps, G=1.0, eta=0.01, eta_start=0.01, lev_min=3,
-                 lev_max=20, block_levels=True, shared_lev=None):
+                 lev_max=20, block_levels=True, shared_lev=None, ext=None):
         self.m = _f64(m).copy()
         n = self.n = self.m.shape[0]
         self.x = _f64(x, (n, 3)).copy()
@@ -210,9 +218,11 @@ class HermiteState:
         self.lev_min, self.lev_max = int(lev_min), int(lev_max)
         self.block_levels = bool(block_levels)
         self.n_clamped = np.zeros(1, dtype=np.int64)
-        lib().orc_hermite_init(n, _p(self.m), _p(self.x), _p(self.v), self.G, self.eps,
-                               float(eta_start), self.lev_min, self.lev_max, _p(self.a),
-                               _p(self.jk), _p(self.lev), _p(self.t))
+        self._ext = None if ext is None else _ext_params(ext)
+        lib().orc_hermite_init_ext(n, _p(self.m), _p(self.x), _p(self.v), self.G, self.eps,
+                                   float(eta_start), self.lev_min, self.lev_max,
+                                   _p(self._ext), _p(self.a), _p(self.jk), _p(self.lev),
+                                   _p(self.t))
         if shared_lev is not None:
             self.lev[:] = int(shared_lev)
         self._act = np.zeros(n, dtype=np.int64)
@@ -227,23 +237,30 @@ class HermiteState:
             rt = int(replay[0])
             ra = np.ascontiguousarray(replay[1], dtype=np.int64)
             rn = ra.shape[0]
-        n_act = lib().orc_block_step(
+        n_act = lib().orc_block_step_ext(
             self.n, _p(self.m), _p(self.x), _p(self.v), _p(self.a), _p(self.jk),
             _p(self.t), _p(self.lev), self.G, self.eps, self.eta, self.lev_min,
-            self.lev_max, int(self.block_levels), rt, rn, _p(ra), _p(tn), _p(self._act),
-            _p(self.n_clamped))
+            self.lev_max, int(self.block_levels), rt, rn, _p(ra), _p(self._ext), _p(tn),
+            _p(self._act), _p(self.n_clamped))
         return int(tn[0]), self._act[:n_act].copy()
 
     def time(self) -> float:
         return float(self.t.max()) * 2.0 ** (-TICKS_LOG2)
 
     def energy(self):
-        return energy(self.m, self.x, self.v, self.eps, self.G)
+        """(K, W, E); with an external field W includes sum m Phi_ext."""
+        K, W, E = energy(self.m, self.x, self.v, self.eps, self.G)
+        if self._ext is not None:
+            phi = np.zeros(self.n)
+            lib().orc_ext(self.n, _p(self.x), None, _p(self._ext), None, None, _p(phi))
+            W_ext = float(np.sum(self.m * phi))
+            W, E = W + W_ext, E + W_ext
+        return K, W, E
 
 
-def hermite_shared(m, x, v, eps, lev, nsteps, G=1.0):
+def hermite_shared(m, x, v, eps, lev, nsteps, G=1.0, ext=None):
     """Shared fixed dt = 2^-lev; returns (x, v, a, jerk) after nsteps."""
-    st = HermiteState(m, x, v, eps, G=G, block_levels=False, shared_lev=lev)
+    st = HermiteState(m, x, v, eps, G=G, block_levels=False, shared_lev=lev, ext=ext)
     for _ in range(nsteps):
         st.step()
     return st.x, st.v, st.a, st.jk
@@ -289,15 +306,20 @@ def _ext_params(ext):
                      e["r_cut"]], dtype=np.float64)
 
 
-def ext_field(x, ext=None):
-    """Acceleration (n, 3) and potential (n,) of the external field at x;
-    ``ext`` overrides entries of ALLEN_SANTILLAN."""
+def ext_field(x, ext=None, v=None):
+    """Acceleration (n, 3) and potential (n,) of the external field at x,
+    and with velocities v also the jerk (n, 3), d a(x + v t)/dt; ``ext``
+    overrides entries of ALLEN_SANTILLAN."""
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3))
     n = x.shape[0]
     acc = np.zeros((n, 3))
     phi = np.zeros(n)
-    lib().orc_ext(n, _p(x), _p(_ext_params(ext)), _p(acc), _p(phi))
-    return acc, phi
+    jerk = None
+    if v is not None:
+        v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, 3))
+        jerk = np.zeros((n, 3))
+    lib().orc_ext(n, _p(x), _p(v), _p(_ext_params(ext)), _p(acc), _p(jerk), _p(phi))
+    return (acc, phi) if v is None else (acc, phi, jerk)
 
 
 def symplectic(m, x, v, eps, dt, nsteps, order, G=1.0, weights=None, ext=None):

@@ -1,6 +1,6 @@
 """Pins for the oracle's external Galactic field (Allen & Santillan 1991,
 the field the paper's Sec. 2.1 adds to the pair forces) and for the
-symplectic integrators with it (CPU only)."""
+symplectic and Hermite integrators with it (CPU only)."""
 import math
 
 import numpy as np
@@ -97,3 +97,42 @@ def test_energy_conserved_on_an_eccentric_orbit(oracle_mod):
         E = 0.5 * np.sum(v**2) + oracle_mod.ext_field(x)[1][0]
         worst = max(worst, abs(E / E0 - 1.0))
     assert worst < 1e-9, worst
+
+
+def test_field_jerk_is_time_derivative_of_acceleration(oracle_mod):
+    """The jerk d a(x + v t)/dt at t = 0 against central differences along
+    the straight line, at points in and off the plane, near the axis, near
+    the centre and beyond the halo cut, with random velocities."""
+    rng = np.random.default_rng(4)
+    pts = np.concatenate([
+        rng.normal(0.0, 6.0, (12, 3)),
+        [[R0, 0.0, 0.0], [0.05, 0.02, 0.3], [0.0, 0.0, 2.0], [3.0, -1.0, 0.01],
+         [80.0, 40.0, 30.0], [150.0, -20.0, 60.0]]])
+    vel = rng.normal(0.0, 15.0, pts.shape)
+    _, _, jk = oracle_mod.ext_field(pts, v=vel)
+    for p, u, jp in zip(pts, vel, jk):
+        h = 1e-6 * max(1.0, np.linalg.norm(p)) / max(1.0, np.linalg.norm(u))
+        ap = oracle_mod.ext_field([p + u * h])[0][0]
+        am = oracle_mod.ext_field([p - u * h])[0][0]
+        fd = (ap - am) / (2 * h)
+        assert np.linalg.norm(jp - fd) <= 1e-6 * np.linalg.norm(fd), (p, jp, fd)
+
+
+def test_hermite_with_field_circular_orbit(oracle_mod):
+    """A test particle on the circular orbit at R0, Hermite-4 with shared
+    steps and the field's acceleration and jerk: fourth-order convergence
+    towards the uniform circular motion over a fifth of a period."""
+    a, _ = oracle_mod.ext_field([[R0, 0.0, 0.0]])
+    vc = math.sqrt(-a[0, 0] * R0)
+    w = vc / R0
+    m = np.array([1e-12])
+    errs = []
+    t_end = 0.5  # a fifth of the 2.43-unit period
+    for lev in (6, 7, 8):
+        x, v, _, _ = oracle_mod.hermite_shared(m, [[R0, 0.0, 0.0]], [[0.0, vc, 0.0]], 0.0, lev,
+                                               int(t_end * 2**lev), ext={})
+        exact = R0 * np.array([math.cos(w * t_end), math.sin(w * t_end), 0.0])
+        errs.append(np.linalg.norm(x[0] - exact))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 12.0 < r1 < 20.0 and 12.0 < r2 < 20.0, errs
+    assert errs[2] < 1e-8 * R0

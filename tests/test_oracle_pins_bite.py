@@ -39,6 +39,9 @@ MUTANTS = {
     "ext_halo_bracket_sign": ("* (Fc - Fq);", "* (Fq - Fc);"),
     "ext_bulge_power": ("const double f = G * mb / (s2 * s);", "const double f = G * mb / s2;"),
     "ext_halo_mass_exponent": ("const double Mr = mh * q * u / (1.0 + u);", "const double Mr = mh * u / (1.0 + u);"),
+    "ext_disk_jerk_vertical": ("const double gdot = vz * (1.0 + ad * bd * bd / (zeta * zeta * zeta));", "const double gdot = vz;"),
+    "ext_halo_jerk_mass_slope": ("(Mp - 3.0 * Mr / r)", "(-3.0 * Mr / r)"),
+    "ext_hermite_jerk_dropped": ("j1[3 * k + c] += ej[c];", "j1[3 * k + c] += 0.0 * ej[c];"),
 }
 
 
