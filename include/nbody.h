@@ -221,11 +221,21 @@ typedef struct nb_external {
 void nb_external_allen_santillan(nb_external *e);
 
 /* Set (e non-NULL, copied) or remove (NULL) the context's external field.
- * While set: nb_symplectic adds its acceleration (FP64, at each particle's
- * own position) to the pair sum in every kick and leaves the total in a;
- * nb_energy adds sum_i m_i Phi(x_i) to the potential energy; the Hermite
- * calls (nb_next_block, nb_predict, nb_step, nb_run_blocks) answer
- * NB_ERR_STATE.  NB_ERR_INVALID_ARG: a non-finite parameter, a negative G,
+ * While set, everything is FP64 at each particle's own position:
+ *  - nb_symplectic adds the field's acceleration to the pair sum in every
+ *    kick and leaves the total in a;
+ *  - the Hermite corrector (nb_correct, nb_step, nb_run_blocks) adds the
+ *    field's acceleration and jerk (the time derivative of the
+ *    acceleration along the velocity) at each active particle's predicted
+ *    position and velocity to its pair sums, so a and jerk in the state
+ *    are totals and the predictor and step criterion use them;
+ *  - nb_energy adds sum_i m_i Phi(x_i) to the potential energy.
+ * The call itself moves the field into (or the previous one out of) every
+ * particle's stored a and jerk at its own stored x, v; on a context where
+ * no step has been taken since nb_init it also recomputes the initial
+ * levels from the totals.  With a field set, a and jerk given to
+ * nb_set_state must include it (as nb_get_state returns them).
+ * Synchronises.  NB_ERR_INVALID_ARG: a non-finite parameter, a negative G,
  * mass or a_disk, b_bulge, b_disk, a_halo or r_cut not positive, or
  * gamma_halo <= 1. */
 nb_status nb_set_external(nb_ctx *ctx, const nb_external *e);

@@ -184,6 +184,7 @@ struct nb_ctx {
   double sym_dt = 0.0;
   int64_t sym_graph_launches = 0;
   bool sym_graph_stale = false;  // the field changed since the capture
+  bool fresh = true;             // every particle still at t = 0 from nb_init
   // nb_symplectic moved x and v: the Hermite fields (jerk, times, levels)
   // no longer belong to them until nb_set_state
   bool sym_moved = false;
@@ -262,9 +263,6 @@ nb_status check_hermite(nb_ctx *c) {
   if (c->sym_moved)
     return fail(NB_ERR_STATE, "nb_symplectic moved the particles; nb_set_state must give the "
                               "Hermite state (jerk, times, levels) before Hermite steps");
-  if (c->ext.on)
-    return fail(NB_ERR_STATE, "the Hermite integrator has no external field; remove it with "
-                              "nb_set_external(ctx, NULL) first");
   return NB_OK;
 }
 
@@ -543,6 +541,7 @@ nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
   c->t_block = c->h_scal[kCtlTnext];
   c->n_act = c->h_scal[kCtlNact];
   c->have_block = true;
+  c->fresh = false;
   c->force_done = false;
   c->n_blocks += 1;
   if (t_next) *t_next = std::ldexp(static_cast<double>(c->t_block), -kTicksLog2);
@@ -669,7 +668,7 @@ nb_status nb_correct(nb_ctx *c, double t) {
                               "of the active list at the same time first");
   NB_CUDA(launch_correct(c->n_act, c->act, c->t_block, c->x, c->v, c->a, c->jk, c->t_tick,
                          c->lev, c->a1, c->j1, c->cfg.eta, c->cfg.lev_min, c->cfg.lev_max,
-                         c->cfg.block_steps, c->clamped, c->stream));
+                         c->cfg.block_steps, c->clamped, c->ext, c->stream));
   c->launches += 1;
   c->force_done = false;
   c->have_block = false;
@@ -761,7 +760,7 @@ nb_status queue_device_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
     }
     NB_CUDA(launch_correct(c->n, c->act, 0, c->x, c->v, c->a, c->jk, c->t_tick, c->lev, c->a1,
                            c->j1, c->cfg.eta, c->cfg.lev_min, c->cfg.lev_max,
-                           c->cfg.block_steps, c->clamped, s, c->scal));
+                           c->cfg.block_steps, c->clamped, c->ext, s, c->scal));
     ++nl;
     *launches += nl;
   }
@@ -821,6 +820,7 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   E.block_steps = c->cfg.block_steps;
   E.n_clamped = c->clamped;
   E.ctl = c->scal;
+  E.ext = c->ext;
   const int end_grid = c->num_sms * 2;
   // The bucket launches are independent graph branches (fork after
   // block_begin, join before block_end), so the ones outside their range
@@ -1011,9 +1011,33 @@ extern "C" nb_status nb_set_external(nb_ctx *c, const nb_external *e) {
     f.gam = e->gamma_halo;
     f.rcut = e->r_cut;
   }
+  // the stored a and jerk of every particle carry the field: take the old
+  // one out and put the new one in at each particle's own state; a state
+  // fresh from nb_init also gets its initial levels from the new totals
+  NB_CUDA(launch_ext_adjust(c->n, c->ext, -1.0, c->x, c->v, c->a, c->jk, c->stream));
+  NB_CUDA(launch_ext_adjust(c->n, f, 1.0, c->x, c->v, c->a, c->jk, c->stream));
+  c->launches += (c->ext.on ? 1 : 0) + (f.on ? 1 : 0);
+  if (c->fresh) {
+    NB_CUDA(launch_init_levels(c->n, c->a, c->jk, c->cfg.eta_start, c->cfg.lev_min,
+                               c->cfg.lev_max, c->cfg.block_steps, c->cfg.lev_shared, c->lev,
+                               c->t_tick, c->stream));
+    c->launches += 1;
+  }
   c->ext = f;
   c->sym_graph_stale = true;
-  return NB_OK;
+  // the block-step graphs hold the field in their kernels' arguments
+  if (c->blk_graph) {
+    cudaGraphExecDestroy(c->blk_graph);
+    c->blk_graph = nullptr;
+  }
+  if (c->fus_graph) {
+    cudaGraphExecDestroy(c->fus_graph);
+    c->fus_graph = nullptr;
+  }
+  c->have_block = false;
+  c->force_done = false;
+  c->t_pred = -1;
+  return sync_ctx(c);
 }
 
 extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t nsteps) {
@@ -1034,6 +1058,7 @@ extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t 
   c->launches += nl;
   c->interactions += c->n * c->n;
   c->sym_moved = true;
+  c->fresh = false;
   c->have_block = false;
   c->force_done = false;
   c->t_pred = -1;
@@ -1129,6 +1154,7 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
   if (s != NB_OK) return s;
   const int64_t done = c->h_scal[kCtlBlocks] - b0;
   c->n_blocks += done;
+  if (done > 0) c->fresh = false;
   c->interactions += c->h_scal[kCtlInter] - i0;
   c->have_block = false;
   c->force_done = false;
@@ -1225,6 +1251,7 @@ nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double
   c->force_done = false;
   c->t_pred = -1;
   c->sym_moved = false;
+  c->fresh = false;
   return sync_ctx(c);
 }
 

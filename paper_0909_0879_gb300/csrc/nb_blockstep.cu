@@ -302,7 +302,8 @@ __device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t 
       }
     }
     dev::correct_vals(ci, st, an, jn, t_next, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, E.eta,
-                      E.lev_min, E.lev_max, E.block_steps, E.n_clamped, E.ctl + kCtlLevCnt);
+                      E.lev_min, E.lev_max, E.block_steps, E.n_clamped, E.ctl + kCtlLevCnt,
+                      &E.ext);
   }
   __syncthreads();
 }

@@ -378,6 +378,101 @@ __device__ __forceinline__ void herm_component(const HermCoef &K, double x0, dou
   a3 = crackle;
 }
 
+// External Galactic field of Allen & Santillan (1991) at position x, FP64:
+// acceleration added into a, and, when v and jk are set, its time
+// derivative along v (the jerk) added into jk; the potential into *phi when
+// phi is set.  With d = x - centre, r = |d|, R^2 = d_x^2 + d_y^2, z = d_z:
+//   bulge (Plummer)          Phi = -G M_b / sqrt(r^2 + b_b^2)
+//   disk (Miyamoto-Nagai)    Phi = -G M_d / D, D^2 = R^2 + (a_d + zeta)^2,
+//                            zeta = sqrt(z^2 + b_d^2)
+//   halo                     M(r) = M_h q^gamma / (1 + q^(gamma-1)), q = r / a_h,
+//                            held at M(r_cut) beyond r_cut; force -G M(r) d / r^3;
+//                            Phi = -G M(r) / r - G M_h / ((gamma-1) a_h) (F(q_cut) - F(q))
+//                            inside the cut, F(q) = ln(1 + q^(gamma-1))
+//                            - (gamma-1) / (1 + q^(gamma-1)); -G M(r_cut) / r beyond.
+// Jerk terms: bulge -G M_b (v / s^3 - 3 (d.v) d / s^5), s^2 = r^2 + b_b^2;
+// disk -G M_d ((v_x, v_y, g') / D^3 - 3 D' (d_x, d_y, g) / D^4) with
+// g = z (a_d + zeta) / zeta, g' = v_z (1 + a_d b_d^2 / zeta^3),
+// D' = (d_x v_x + d_y v_y + (a_d + zeta) z v_z / zeta) / D; halo
+// -G (M v / r^3 + (M' - 3 M / r) (d.v) d / r^4), M' = dM/dr (0 beyond the cut).
+__device__ __forceinline__ void ext_field(const ExtField &E, const double x[3],
+                                          const double *v, double a[3], double *jk,
+                                          double *phi) {
+  const double dx = x[0] - E.c[0], dy = x[1] - E.c[1], dz = x[2] - E.c[2];
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double r = sqrt(r2);
+  const bool wj = v != nullptr && jk != nullptr;
+  const double vx = wj ? v[0] : 0.0, vy = wj ? v[1] : 0.0, vz = wj ? v[2] : 0.0;
+  const double dv = dx * vx + dy * vy + dz * vz;
+  double ph = 0.0;
+  {
+    const double s2 = r2 + E.bb * E.bb;
+    const double s = sqrt(s2);
+    const double f = E.G * E.mb / (s2 * s);
+    a[0] -= f * dx;
+    a[1] -= f * dy;
+    a[2] -= f * dz;
+    ph -= E.G * E.mb / s;
+    if (wj) {
+      const double c = 3.0 * dv / s2;
+      jk[0] -= f * (vx - c * dx);
+      jk[1] -= f * (vy - c * dy);
+      jk[2] -= f * (vz - c * dz);
+    }
+  }
+  {
+    const double zeta = sqrt(dz * dz + E.bd * E.bd);
+    const double w = E.ad + zeta;
+    const double D2 = dx * dx + dy * dy + w * w;
+    const double D = sqrt(D2);
+    const double f = E.G * E.md / (D2 * D);
+    const double g = dz * w / zeta;
+    a[0] -= f * dx;
+    a[1] -= f * dy;
+    a[2] -= f * g;
+    ph -= E.G * E.md / D;
+    if (wj) {
+      const double Ddot = (dx * vx + dy * vy + w * dz * vz / zeta) / D;
+      const double gdot = vz * (1.0 + E.ad * E.bd * E.bd / (zeta * zeta * zeta));
+      const double c = 3.0 * Ddot / D;
+      jk[0] -= f * (vx - c * dx);
+      jk[1] -= f * (vy - c * dy);
+      jk[2] -= f * (gdot - c * g);
+    }
+  }
+  {
+    const double rr = r < E.rcut ? r : E.rcut;
+    const double q = rr / E.ah;
+    const double u = pow(q, E.gam - 1.0);
+    const double Mr = E.mh * q * u / (1.0 + u);
+    if (r > 0.0) {
+      const double f = E.G * Mr / (r2 * r);
+      a[0] -= f * dx;
+      a[1] -= f * dy;
+      a[2] -= f * dz;
+      if (wj) {
+        const double Mp = r < E.rcut ? E.mh * u * (E.gam + u) / ((1.0 + u) * (1.0 + u) * E.ah)
+                                     : 0.0;
+        const double c = E.G * (Mp - 3.0 * Mr / r) * dv / (r2 * r2);
+        jk[0] -= f * vx + c * dx;
+        jk[1] -= f * vy + c * dy;
+        jk[2] -= f * vz + c * dz;
+      }
+    }
+    if (phi) {
+      if (r < E.rcut) {
+        const double uc = pow(E.rcut / E.ah, E.gam - 1.0);
+        const double Fc = log(1.0 + uc) - (E.gam - 1.0) / (1.0 + uc);
+        const double Fq = log(1.0 + u) - (E.gam - 1.0) / (1.0 + u);
+        ph += (r > 0.0 ? -E.G * Mr / r : 0.0) - E.G * E.mh / ((E.gam - 1.0) * E.ah) * (Fc - Fq);
+      } else {
+        ph -= E.G * Mr / r;
+      }
+      *phi = ph;
+    }
+  }
+}
+
 // State of one particle as the corrector reads it (loaded ahead of the
 // corrector so that the loads overlap other work).
 struct PState {
@@ -403,18 +498,38 @@ __device__ __forceinline__ void load_state(int64_t i, const double *__restrict__
   st.lev = lev[i];
 }
 
+// The field's acceleration and jerk at the predictor's position and
+// velocity (the expression of predict_pos_vel) added into an, jn.  Not
+// inlined: the corrector kernels keep their registers when no field is set.
+static __device__ __noinline__ void ext_at_prediction(const ExtField &E, const PState &st,
+                                                      double dt, double h2, double h3,
+                                                      double an[3], double jn[3]) {
+  double xp[3], vp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    xp[c] = st.x[c] + dt * (st.v[c] + h2 * (st.a[c] + h3 * st.j[c]));
+    vp[c] = st.v[c] + dt * (st.a[c] + h2 * st.j[c]);
+  }
+  ext_field(E, xp, vp, an, jn, nullptr);
+}
+
 // Hermite corrector, step criterion and new level of particle i (state st)
-// with its new force an, jn at t_next.  With lev_cnt set, a change of level
-// moves the particle between the per-level counts.
+// with its new pair force an, jn at t_next, plus, when ext is on, the
+// external field's acceleration and jerk at the predicted position and
+// velocity.  With lev_cnt set, a change of level moves the particle between
+// the per-level counts.
 __device__ __forceinline__ void correct_vals(
-    int64_t i, const PState &st, const double an3[3], const double jn3[3], int64_t t_next,
-    double *__restrict__ x, double *__restrict__ v, double *__restrict__ a,
+    int64_t i, const PState &st, const double an_pair[3], const double jn_pair[3],
+    int64_t t_next, double *__restrict__ x, double *__restrict__ v, double *__restrict__ a,
     double *__restrict__ jk, int64_t *__restrict__ t_tick, int32_t *__restrict__ lev,
     double eta, int lev_min, int lev_max, int block_steps, unsigned long long *n_clamped,
-    int64_t *lev_cnt) {
+    int64_t *lev_cnt, const ExtField *ext = nullptr) {
   const int64_t dtk = t_next - st.t;
   const double dt = static_cast<double>(dtk) * kTick;
   const double h2 = 0.5 * dt, h3 = dt * (1.0 / 3.0);
+  double an3[3] = {an_pair[0], an_pair[1], an_pair[2]};
+  double jn3[3] = {jn_pair[0], jn_pair[1], jn_pair[2]};
+  if (ext && ext->on) ext_at_prediction(*ext, st, dt, h2, h3, an3, jn3);
   const double dt2 = dt * dt, dt3 = dt2 * dt;
   // A due particle's step is a power of two of ticks, so 1/dt^2 and 1/dt^3
   // are powers of two, built exactly from the exponent (no division), and
@@ -476,75 +591,14 @@ __device__ __forceinline__ void correct_one(
     double *__restrict__ v, double *__restrict__ a, double *__restrict__ jk,
     int64_t *__restrict__ t_tick, int32_t *__restrict__ lev, const double *__restrict__ a1,
     const double *__restrict__ j1, double eta, int lev_min, int lev_max, int block_steps,
-    unsigned long long *n_clamped, int64_t *lev_cnt) {
+    unsigned long long *n_clamped, int64_t *lev_cnt, const ExtField *ext = nullptr) {
   const int64_t i = act[k];
   PState st;
   load_state(i, x, v, a, jk, t_tick, lev, st);
   const double an[3] = {a1[3 * k], a1[3 * k + 1], a1[3 * k + 2]};
   const double jn[3] = {j1[3 * k], j1[3 * k + 1], j1[3 * k + 2]};
   correct_vals(i, st, an, jn, t_next, x, v, a, jk, t_tick, lev, eta, lev_min, lev_max,
-               block_steps, n_clamped, lev_cnt);
-}
-
-// External Galactic field of Allen & Santillan (1991) at position x, FP64:
-// acceleration into a (added) and, when phi is set, the potential.  With
-// d = x - centre, r = |d|, R^2 = d_x^2 + d_y^2, z = d_z:
-//   bulge (Plummer)          Phi = -G M_b / sqrt(r^2 + b_b^2)
-//   disk (Miyamoto-Nagai)    Phi = -G M_d / sqrt(R^2 + (a_d + sqrt(z^2 + b_d^2))^2)
-//   halo                     M(r) = M_h q^gamma / (1 + q^(gamma-1)), q = r / a_h,
-//                            held at M(r_cut) beyond r_cut; force -G M(r) d / r^3;
-//                            Phi = -G M(r) / r - G M_h / ((gamma-1) a_h) (F(q_cut) - F(q))
-//                            inside the cut, F(q) = ln(1 + q^(gamma-1))
-//                            - (gamma-1) / (1 + q^(gamma-1)); -G M(r_cut) / r beyond.
-__device__ __forceinline__ void ext_field(const ExtField &E, const double x[3], double a[3],
-                                          double *phi) {
-  const double dx = x[0] - E.c[0], dy = x[1] - E.c[1], dz = x[2] - E.c[2];
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  const double r = sqrt(r2);
-  double ph = 0.0;
-  {
-    const double s2 = r2 + E.bb * E.bb;
-    const double s = sqrt(s2);
-    const double f = E.G * E.mb / (s2 * s);
-    a[0] -= f * dx;
-    a[1] -= f * dy;
-    a[2] -= f * dz;
-    ph -= E.G * E.mb / s;
-  }
-  {
-    const double zeta = sqrt(dz * dz + E.bd * E.bd);
-    const double w = E.ad + zeta;
-    const double D2 = dx * dx + dy * dy + w * w;
-    const double D = sqrt(D2);
-    const double f = E.G * E.md / (D2 * D);
-    a[0] -= f * dx;
-    a[1] -= f * dy;
-    a[2] -= f * dz * w / zeta;
-    ph -= E.G * E.md / D;
-  }
-  {
-    const double rr = r < E.rcut ? r : E.rcut;
-    const double q = rr / E.ah;
-    const double u = pow(q, E.gam - 1.0);
-    const double Mr = E.mh * q * u / (1.0 + u);
-    if (r > 0.0) {
-      const double f = E.G * Mr / (r2 * r);
-      a[0] -= f * dx;
-      a[1] -= f * dy;
-      a[2] -= f * dz;
-    }
-    if (phi) {
-      if (r < E.rcut) {
-        const double uc = pow(E.rcut / E.ah, E.gam - 1.0);
-        const double Fc = log(1.0 + uc) - (E.gam - 1.0) / (1.0 + uc);
-        const double Fq = log(1.0 + u) - (E.gam - 1.0) / (1.0 + u);
-        ph += (r > 0.0 ? -E.G * Mr / r : 0.0) - E.G * E.mh / ((E.gam - 1.0) * E.ah) * (Fc - Fq);
-      } else {
-        ph -= E.G * Mr / r;
-      }
-      *phi = ph;
-    }
-  }
+               block_steps, n_clamped, lev_cnt, ext);
 }
 
 }  // namespace dev

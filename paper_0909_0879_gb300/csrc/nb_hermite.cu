@@ -68,7 +68,8 @@ __global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, i
                                int64_t *__restrict__ t_tick, int32_t *__restrict__ lev,
                                const double *__restrict__ a1, const double *__restrict__ j1,
                                double eta, int lev_min, int lev_max, int block_steps,
-                               unsigned long long *n_clamped, const int64_t *ctl) {
+                               unsigned long long *n_clamped, const ExtField E,
+                               const int64_t *ctl) {
   if (ctl) {
     t_next = ctl[kCtlTnext];
     n_act = ctl[kCtlNact];
@@ -77,7 +78,24 @@ __global__ void correct_kernel(int64_t n_act, const int32_t *__restrict__ act, i
   for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n_act;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x)
     dev::correct_one(k, act, t_next, x, v, a, jk, t_tick, lev, a1, j1, eta, lev_min, lev_max,
-                     block_steps, n_clamped, nullptr);
+                     block_steps, n_clamped, nullptr, &E);
+}
+
+// a += sign a_ext(x), jk += sign jerk_ext(x, v) for every particle at its
+// own stored position and velocity.
+__global__ void ext_adjust_kernel(int64_t n, const ExtField E, double sign,
+                                  const double *__restrict__ x, const double *__restrict__ v,
+                                  double *__restrict__ a, double *__restrict__ jk) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double xv[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  const double vv[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+  double ea[3] = {0.0, 0.0, 0.0}, ej[3] = {0.0, 0.0, 0.0};
+  dev::ext_field(E, xv, vv, ea, ej, nullptr);
+  for (int c = 0; c < 3; ++c) {
+    a[3 * i + c] += sign * ea[c];
+    jk[3 * i + c] += sign * ej[c];
+  }
 }
 
 __global__ void init_levels_kernel(int64_t n, const double *__restrict__ a,
@@ -319,7 +337,7 @@ __global__ void ext_potential_kernel(int64_t n, const ExtField E, const double *
   if (i < n) {
     const double xv[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
     double av[3] = {0.0, 0.0, 0.0}, phi = 0.0;
-    dev::ext_field(E, xv, av, &phi);
+    dev::ext_field(E, xv, nullptr, av, nullptr, &phi);
     s = m[i] * phi;
   }
   s = block_sum(s, sh);
@@ -368,14 +386,22 @@ cudaError_t launch_correct(int64_t n_act, const int32_t *act, int64_t t_next, do
                            double *v, double *a, double *jk, int64_t *t_tick, int32_t *lev,
                            const double *a1, const double *j1, double eta, int lev_min,
                            int lev_max, int block_steps, unsigned long long *n_clamped,
-                           cudaStream_t s, const int64_t *ctl) {
+                           const ExtField &E, cudaStream_t s, const int64_t *ctl) {
   if (n_act <= 0) return cudaSuccess;
   const int tb = 128;
   int64_t nb = (n_act + tb - 1) / tb;
   if (ctl && nb > 1216) nb = 1216;  // grid-stride over a bound on the count
   correct_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(
       n_act, act, t_next, x, v, a, jk, t_tick, lev, a1, j1, eta, lev_min, lev_max,
-      block_steps, n_clamped, ctl);
+      block_steps, n_clamped, E, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ext_adjust(int64_t n, const ExtField &E, double sign, const double *x,
+                              const double *v, double *a, double *jk, cudaStream_t s) {
+  if (n <= 0 || !E.on) return cudaSuccess;
+  ext_adjust_kernel<<<static_cast<unsigned>((n + 127) / 128), 128, 0, s>>>(n, E, sign, x, v,
+                                                                          a, jk);
   return cudaGetLastError();
 }
 

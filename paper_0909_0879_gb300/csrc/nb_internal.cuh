@@ -164,8 +164,12 @@ cudaError_t launch_correct(int64_t n_act, const int32_t *act, int64_t t_next,
                            int64_t *t_tick, int32_t *lev, const double *a1,
                            const double *j1, double eta, int lev_min,
                            int lev_max, int block_steps,
-                           unsigned long long *n_clamped, cudaStream_t s,
-                           const int64_t *ctl = nullptr);
+                           unsigned long long *n_clamped, const ExtField &E,
+                           cudaStream_t s, const int64_t *ctl = nullptr);
+// a += sign a_ext(x), jk += sign jerk_ext(x, v) for every particle (its own
+// stored state); a no-op unless E.on.
+cudaError_t launch_ext_adjust(int64_t n, const ExtField &E, double sign, const double *x,
+                              const double *v, double *a, double *jk, cudaStream_t s);
 cudaError_t launch_init_levels(int64_t n, const double *a, const double *jk,
                                double eta_start, int lev_min, int lev_max,
                                int block_steps, int lev_shared, int32_t *lev,
@@ -229,6 +233,7 @@ struct EndArgs {
   int lev_min, lev_max, block_steps;
   unsigned long long *n_clamped;
   int64_t *ctl;
+  ExtField ext;                      // external field (on = 0: none)
 };
 cudaError_t launch_block_end(const EndArgs &E, int grid, cudaStream_t s);
 constexpr int kEndThreads = 256;

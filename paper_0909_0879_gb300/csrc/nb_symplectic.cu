@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kJT)
     }
     if (h != 0.0) {
       double at[3] = {a[3 * j], a[3 * j + 1], a[3 * j + 2]};
-      if (E.on) dev::ext_field(E, xv, at, nullptr);
+      if (E.on) dev::ext_field(E, xv, nullptr, at, nullptr, nullptr);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         vv[c] = fma(h, at[c], vv[c]);
@@ -77,7 +77,7 @@ __global__ void ext_add_kernel(int64_t n, const ExtField E, const double *__rest
   if (i >= n) return;
   const double xv[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
   double av[3] = {a[3 * i], a[3 * i + 1], a[3 * i + 2]};
-  dev::ext_field(E, xv, av, nullptr);
+  dev::ext_field(E, xv, nullptr, av, nullptr, nullptr);
   for (int c = 0; c < 3; ++c) a[3 * i + c] = av[c];
 }
 
