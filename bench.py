@@ -720,8 +720,9 @@ def run_symplectic(args):
     # 1e5 solar masses, virial radius 10 pc, eps = 0.1 pc, on the circular
     # orbit through (8.5, 0, 0); sixth order to t = 1/32 (two crossing times)
     # with dt = 2^-10 and 2^-12; the energy change (with the field's) over the
-    # cluster's pair potential energy in both precisions, and the step time
-    # with and without the field.
+    # cluster's pair potential energy in both precisions, the step time with
+    # and without the field, and 2000 Hermite block steps with and without
+    # it.
     mc, xc, vc = ics.plummer(n, 1007)
     Mc, Lc = 0.00431, 0.01
     mc, xc, vc = (mc * Mc, xc * Lc + np.array([8.5, 0.0, 0.0]),
@@ -744,6 +745,23 @@ def run_symplectic(args):
                     s.set_external({})
                 per_step = _time_symplectic(torch, s, 6, 2.0**-10, 16)
             row["s_per_step_with_field" if field else "s_per_step_without_field"] = per_step
+        # Hermite block steps (device-resident, eta = 0.01, levels 8..20) of
+        # the same cluster, 2000 block steps, with and without the field
+        for field in (True, False):
+            with _lib.NBody(mc, xc, vc, eps=1e-4, precision=prec, eta=0.01, lev_min=8,
+                            lev_max=20) as s:
+                if field:
+                    s.set_external({})
+                c0 = s.counters()["interactions"]
+                e0, e1 = _events(torch)
+                e0.record()
+                done, _ = s.run_blocks(1.0, max_blocks=2000)
+                e1.record()
+                torch.cuda.synchronize()
+                inter = s.counters()["interactions"] - c0
+            key = "hermite_blocks_with_field" if field else "hermite_blocks_without_field"
+            row[key] = {"block_steps": done, "ms": e0.elapsed_time(e1),
+                        "interactions_per_s": inter / (e0.elapsed_time(e1) / 1e3)}
         galactic.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
     out = {"metric": "interactions/s and energy error of the symplectic integrators",
