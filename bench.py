@@ -209,6 +209,20 @@ def cpu_baseline(m, x, v, n, seconds):
             "seconds": dt}
 
 
+def _oracle_beside(work, units, unit, sample):
+    """The FP64 oracle timed beside a GPU workload: `work` runs a bounded
+    sample of the workload's own work in the oracle on every host core;
+    `units` of it, reported per second in `unit`."""
+    from oracle import oracle as O
+
+    O.build()
+    t0 = time.perf_counter()
+    work()
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": unit, "cores": O.max_threads(), "kind": "oracle",
+            "sample": sample, "seconds": dt}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -463,6 +477,12 @@ def run_shared1024(args):
         out["results"][prec] = {"value": steps * n * n / ms / 1e6, "ms": ms,
                                 "dE_over_E": abs(E1 - E0) / abs(E0),
                                 "dP": float(np.abs(P).max()), "dL": float(np.abs(L - L0).max())}
+    if not args.no_cpu:
+        from oracle import oracle as O
+
+        out["cpu_baseline"] = _oracle_beside(
+            lambda: O.hermite_shared(m, x, v, eps, lev, steps), steps * n * n / 1e9, UNIT,
+            "the FP64 oracle's shared-step Hermite loop, the same 256 steps")
     print(json.dumps(out), flush=True)
     return 0
 
@@ -538,6 +558,8 @@ def run_block65536(args):
             "n_act_log2_histogram": {str(k): v for k, v in sorted(hist.items())},
             "device_resident": dev_res,
             "note": "value/ms: host-driven nb_step loop; device_resident: nb_run_blocks"}
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(m, x, v, n, 3.0)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -597,6 +619,26 @@ def run_batched(args):
             "dE_over_E_median_after_2000_steps": float(np.median(dE)),
             "note": "dt = 1/256 with eps = 1e-3 does not resolve close encounters in small "
                     "clusters; the FP64 oracle loses energy at the same level"}
+    if not args.no_cpu:
+        from oracle import oracle as O
+
+        # the oracle's shared-step loop over clusters until ~4e8 interactions
+        take, work = [], 0.0
+        for c in range(len(sizes)):
+            take.append(c)
+            work += 16.0 * float(sizes[c]) ** 2
+            if work >= 4e8:
+                break
+
+        def run_clusters():
+            for c in take:
+                a, b_ = off[c], off[c + 1]
+                O.hermite_shared(m[a:b_], x[a:b_], v[a:b_], 1e-3, 8, 16)
+
+        out["cpu_baseline"] = _oracle_beside(
+            run_clusters, work / 1e9, UNIT,
+            f"the FP64 oracle's shared-step Hermite loop, 16 steps of the first {len(take)} "
+            "clusters")
     print(json.dumps(out), flush=True)
     return 0
 
@@ -643,6 +685,15 @@ def run_adjoint(args):
            "checkpoint_bytes": 4 * _lib.lf_ckpt_floats(n, steps, ck),
            "work_bytes": 4 * _lib.lf_work_floats(n, ck),
            "full_tape_bytes_for_comparison": 4 * (steps + 1) * 6 * n}
+    if not args.no_cpu:
+        from oracle import oracle as O
+
+        yh = y.double().cpu().numpy()
+        cb = _oracle_beside(lambda: O.leapfrog_loss_grad(m, x, v, yh, eps, dt, steps), 1.0,
+                            "forward+backward/s",
+                            "the FP64 oracle's loss and exact adjoint gradient, same 64 steps")
+        cb["forward_backward_ms"] = cb["seconds"] * 1e3
+        out["cpu_baseline"] = cb
     print(json.dumps(out), flush=True)
     return 0
 
@@ -771,6 +822,13 @@ def run_symplectic(args):
            "energy_at_t_1/8": accuracy,
            "galactic_cluster": {"workload": f"plummer_n{n}_1e5msun_rv10pc_at_8.5kpc_allen_santillan",
                                 "rows": galactic}}
+    if not args.no_cpu:
+        from oracle import oracle as O
+
+        out["cpu_baseline"] = _oracle_beside(
+            lambda: O.acc(m, x, eps), n * n / 1e9, UNIT,
+            "one FP64 acceleration evaluation of all N particles by the oracle (the "
+            "symplectic integrators' force)")
     print(json.dumps(out), flush=True)
     return 0
 
