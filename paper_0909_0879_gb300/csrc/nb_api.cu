@@ -883,10 +883,10 @@ nb_status capture_blocks(nb_ctx *c, bool fused, cudaGraphExec_t *out, int64_t *l
 // ---- fixed-step symplectic integration
 
 // Acceleration of every particle into c->a (acceleration-only kernel of the
-// built-in shape for n, which every built-in shape has).
+// built-in shape for n, or its acceleration-only counterpart).
 nb_status queue_acc_all(nb_ctx *c, cudaStream_t s, int64_t *launches) {
-  const int v = choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, c->n, c->n_jt,
-                               c->num_sms);
+  const int v = acc_shape(choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, c->n,
+                                         c->n_jt, c->num_sms));
   if (!has_acc_only(v)) return fail(NB_ERR_STATE, "force shape %d has no acceleration-only kernel", v);
   const int grid = force_grid(v, c->n, c->n_jt, c->num_sms, 0);
   if (part_bytes(v, grid) > c->part_cap)

@@ -130,6 +130,8 @@ size_t part_bytes(int v, int grid);
 int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap);
 // The variant has an acceleration-only kernel (the built-in shapes).
 bool has_acc_only(int v);
+// The shape the acceleration-only evaluation takes for built-in shape v.
+int acc_shape(int v);
 // Queue the force kernel (and its fix-up when i-blocks are split) on `s`.
 // With A.jerk null the acceleration-only kernel runs (cudaErrorInvalidValue
 // when the variant has none).  Returns the number of kernel launches

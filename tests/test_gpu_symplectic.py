@@ -78,19 +78,26 @@ def test_symplectic_matches_oracle(nb, oracle_mod, prec):
 
 @pytest.mark.parametrize("prec", ["ds", "fp32"])
 @pytest.mark.parametrize("n,eps", [(1000, 1e-3), (70001, 1e-3), (1000, 0.0), (70001, 0.0)])
-def test_acceleration_only_kernel_equals_jerk_kernel(nb, prec, n, eps):
+def test_acceleration_only_kernel_equals_jerk_kernel(nb, oracle_mod, prec, n, eps):
     """nsteps = 0 only evaluates A(x) with the acceleration-only kernel; the
     acceleration sums are the same operations in the same order as those
     of the acceleration + jerk kernel that nb_init ran at the same
     positions with the same shape and grid: bit-identical.  eps = 0 takes
-    the masked shapes."""
+    the masked shapes.  The FP32 long-list case is the exception: there the
+    acceleration-only form holds 8 particles per thread instead of 4, which
+    groups the sums differently, so it meets the FP32 force bar instead."""
     m, x, v = ics.plummer(n, 12)
     with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
         a0 = s.get_state(want=("a",))["a"]
         s.symplectic(6, 1.0 / 64, 0)
         a1 = s.get_state(want=("a", "x"))
     assert np.array_equal(a1["x"], x)
-    assert np.array_equal(a1["a"], a0)
+    if prec == "fp32" and n > 4096 and eps > 0:
+        aabs, _ = oracle_mod.force_jerk_abs(m, x, np.zeros_like(x), eps)
+        assert np.all(np.linalg.norm(a1["a"] - a0, axis=1) <= 2 * TOL["fp32"] * aabs)
+        assert not np.array_equal(a1["a"], a0)
+    else:
+        assert np.array_equal(a1["a"], a0)
 
 
 @pytest.mark.parametrize("prec", ["ds", "fp32"])
