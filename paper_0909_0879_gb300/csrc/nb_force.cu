@@ -471,7 +471,32 @@ __global__ void __launch_bounds__(NT, 1)
       }
       const int kk = g + q * NG;
       const int64_t k = static_cast<int64_t>(ib) * BI + kk;
-      if (r == 0 && k < n_i) {
+      if (TPI >= 4 && full) {
+        // every thread of the i-particle holds the sums: thread r converts
+        // components r, r + TPI, ..., so the FP64 work (whose warp
+        // instructions cost the same however few lanes are active) takes
+        // one or two rounds instead of six
+        if (k < n_i) {
+#pragma unroll
+          for (int base = 0; base < (JRK ? 6 : 3); base += TPI) {
+            const int c = base + r;
+            if (c < (JRK ? 6 : 3)) {
+              float hh = oh[0], ll = ol[0];
+#pragma unroll
+              for (int cc = 1; cc < 6; ++cc)
+                if (c == cc) {
+                  hh = oh[cc];
+                  ll = ol[cc];
+                }
+              const double val = dev::ds_to_double(hh, ll, A.G);
+              if (c < 3)
+                A.acc[3 * k + c] = val;
+              else
+                A.jerk[3 * k + c - 3] = val;
+            }
+          }
+        }
+      } else if (r == 0 && k < n_i) {
         if (full) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -518,12 +543,23 @@ __global__ void force_fixup_kernel(const float2 *__restrict__ part, int64_t n_i,
   if (plo == phi) return;  // written directly by its only CTA
   float h[6], l[6];
   dev::fixup_warp(part, ib, kk, plo, phi, U, P, n_jt, BI, lane, h, l);
-  if (lane == 0) {
+  // Every lane holds the six sums: lane c converts component c, so the
+  // warp issues one round of FP64 work instead of six (an FP64 warp
+  // instruction costs the same however few lanes are active).
+  const int nc = jerk ? 6 : 3;
+  if (lane < nc) {
+    float hh = h[0], ll = l[0];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      acc[3 * k + c] = dev::ds_to_double(h[c], l[c], G);
-      if (jerk) jerk[3 * k + c] = dev::ds_to_double(h[3 + c], l[3 + c], G);
-    }
+    for (int c = 1; c < 6; ++c)
+      if (lane == c) {
+        hh = h[c];
+        ll = l[c];
+      }
+    const double val = dev::ds_to_double(hh, ll, G);
+    if (lane < 3)
+      acc[3 * k + lane] = val;
+    else
+      jerk[3 * k + lane - 3] = val;
   }
 }
 
