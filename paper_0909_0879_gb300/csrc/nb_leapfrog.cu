@@ -189,12 +189,15 @@ __global__ void __launch_bounds__(kLfT) lf_acc_wide_kernel(int64_t n, const floa
   }
 }
 
-// lx_k += dL/dx_k and lm_k += dL/dm_k for the cotangent g = h * lv.
+// lx_k += dL/dx_k and lm_k += dL/dm_k for the cotangent g = h * lv; with
+// lv_out set, also lv_out_k = lv_k + dlv lx_k with the updated lx_k (the
+// adjoint of the drift, as a separate elementwise launch would compute it).
 template <int MASK>
 __global__ void __launch_bounds__(kLfT)
     lf_vjp_kernel(int64_t n, const float *__restrict__ x, const float *__restrict__ m,
                   const float *__restrict__ lv, float h, float eps2, float G,
-                  float *__restrict__ lx, float *__restrict__ lm) {
+                  float *__restrict__ lx, float *__restrict__ lm, float *__restrict__ lv_out,
+                  float dlv) {
   __shared__ float4 sx[kLfJT];
   __shared__ float4 sg[kLfJT];
   const int g = threadIdx.x / kLfTpi, r = threadIdx.x % kLfTpi;
@@ -251,9 +254,13 @@ __global__ void __launch_bounds__(kLfT)
     om += __shfl_xor_sync(0xffffffffu, om, off);
   }
   if (r == 0 && k < n) {
-    lx[3 * k] += G * ox;
-    lx[3 * k + 1] += G * oy;
-    lx[3 * k + 2] += G * oz;
+    const float o3[3] = {ox, oy, oz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float lxn = lx[3 * k + c] + G * o3[c];
+      lx[3 * k + c] = lxn;
+      if (lv_out) lv_out[3 * k + c] = fmaf(dlv, lxn, lv[3 * k + c]);
+    }
     lm[k] += G * om;
   }
 }
@@ -268,11 +275,28 @@ __global__ void lf_kick_drift_kernel(int64_t n3, float *__restrict__ x, float *_
   if (drift) x[q] = fmaf(vn, dt, x[q]);
 }
 
-// y += s * z (elementwise)
-__global__ void lf_axpy_kernel(int64_t n3, float *__restrict__ y, const float *__restrict__ z,
-                               float s) {
+// One drift of a run of KDK steps with the kicks around it merged: with
+// close set, the previous step's closing kick v += a h first; then, when
+// ck_x is set, the checkpoint (x, v) of the step boundary; then this step's
+// opening kick v += a h and the drift x_out = x_in + v dt.  The same
+// per-element operations in the same order as separate kick and drift
+// launches.  x_in may equal x_out.
+__global__ void lf_step_kernel(int64_t n3, const float *x_in, float *x_out,
+                               float *__restrict__ v, const float *__restrict__ a, float h,
+                               float dt, int close, float *__restrict__ ck_x,
+                               float *__restrict__ ck_v) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q < n3) y[q] = fmaf(s, z[q], y[q]);
+  if (q >= n3) return;
+  const float aq = a[q], xq = x_in[q];
+  float vq = v[q];
+  if (close) vq = fmaf(aq, h, vq);
+  if (ck_x) {
+    ck_x[q] = xq;
+    ck_v[q] = vq;
+  }
+  vq = fmaf(aq, h, vq);
+  v[q] = vq;
+  x_out[q] = fmaf(vq, dt, xq);
 }
 
 struct LfCtx {
@@ -331,12 +355,15 @@ cudaError_t lf_acc(LfCtx &C, const float *x, float *acc) {
   return cudaGetLastError();
 }
 
-cudaError_t lf_vjp(LfCtx &C, const float *x, const float *lv, float h, float *lx, float *lm) {
+cudaError_t lf_vjp(LfCtx &C, const float *x, const float *lv, float h, float *lx, float *lm,
+                   float *lv_out = nullptr, float dlv = 0.f) {
   const unsigned grid = static_cast<unsigned>((C.n + kLfI - 1) / kLfI);
   if (C.mask)
-    lf_vjp_kernel<1><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, lv, h, C.eps2, C.G, lx, lm);
+    lf_vjp_kernel<1><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, lv, h, C.eps2, C.G, lx, lm, lv_out,
+                                             dlv);
   else
-    lf_vjp_kernel<0><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, lv, h, C.eps2, C.G, lx, lm);
+    lf_vjp_kernel<0><<<grid, kLfT, 0, C.s>>>(C.n, x, C.m, lv, h, C.eps2, C.G, lx, lm, lv_out,
+                                             dlv);
   ++C.launches;
   return cudaGetLastError();
 }
@@ -349,18 +376,17 @@ cudaError_t lf_kick(LfCtx &C, float *x, float *v, const float *a, float h, float
   return cudaGetLastError();
 }
 
-cudaError_t lf_axpy(LfCtx &C, float *y, const float *z, float s) {
+// The drift of one KDK step with the kicks around it (see lf_step_kernel),
+// then A(x_out) into acc; the step's own closing kick is left to the next
+// call (close = 1) or to a final lf_kick without drift.
+cudaError_t lf_half_step(LfCtx &C, const float *x_in, float *x_out, float *v, float *acc,
+                         float dt, bool close, float *ck) {
   const int64_t n3 = 3 * C.n;
-  lf_axpy_kernel<<<static_cast<unsigned>((n3 + 255) / 256), 256, 0, C.s>>>(n3, y, z, s);
+  lf_step_kernel<<<static_cast<unsigned>((n3 + 255) / 256), 256, 0, C.s>>>(
+      n3, x_in, x_out, v, acc, 0.5f * dt, dt, close ? 1 : 0, ck, ck ? ck + n3 : nullptr);
   ++C.launches;
-  return cudaGetLastError();
-}
-
-// One KDK step; acc holds A(x) on entry and A(x') on exit.
-cudaError_t lf_step(LfCtx &C, float *x, float *v, float *acc, float dt) {
-  cudaError_t e = lf_kick(C, x, v, acc, 0.5f * dt, dt, 1);
-  if (e == cudaSuccess) e = lf_acc(C, x, acc);
-  if (e == cudaSuccess) e = lf_kick(C, x, v, acc, 0.5f * dt, dt, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = lf_acc(C, x_out, acc);
   return e;
 }
 
@@ -445,16 +471,12 @@ nb_status nb_lf_forward(int64_t n, const float *d_m, float *d_x, float *d_v, flo
   if (!d_v || !d_acc || nsteps < 0 || ckpt_every < 1 || !(std::isfinite(dt)))
     return static_cast<nb_status>(set_error(NB_ERR_INVALID_ARG, "bad leapfrog arguments"));
   LfCtx C = make_ctx(n, d_m, eps, G, stream);
-  const size_t n3b = 3 * static_cast<size_t>(n) * sizeof(float);
   cudaError_t e = lf_acc(C, d_x, d_acc);
   for (int64_t st = 0; st < nsteps && e == cudaSuccess; ++st) {
-    if (d_ckpt && st % ckpt_every == 0) {
-      float *slot = d_ckpt + (st / ckpt_every) * 6 * n;
-      e = cudaMemcpyAsync(slot, d_x, n3b, cudaMemcpyDeviceToDevice, C.s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(slot + 3 * n, d_v, n3b, cudaMemcpyDeviceToDevice, C.s);
-    }
-    if (e == cudaSuccess) e = lf_step(C, d_x, d_v, d_acc, dt);
+    float *ck = (d_ckpt && st % ckpt_every == 0) ? d_ckpt + (st / ckpt_every) * 6 * n : nullptr;
+    e = lf_half_step(C, d_x, d_x, d_v, d_acc, dt, st > 0, ck);
   }
+  if (e == cudaSuccess && nsteps > 0) e = lf_kick(C, d_x, d_v, d_acc, 0.5f * dt, dt, 0);
   return e == cudaSuccess ? NB_OK : lf_err(e);
 }
 
@@ -480,17 +502,22 @@ nb_status nb_lf_backward(int64_t n, const float *d_m, const float *d_ckpt, int64
     e = cudaMemcpyAsync(xs, slot, n3b, cudaMemcpyDeviceToDevice, C.s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(v, slot + n3, n3b, cudaMemcpyDeviceToDevice, C.s);
     if (e == cudaSuccess) e = lf_acc(C, xs, acc);
-    for (int64_t q = 0; q < L && e == cudaSuccess; ++q) {
-      float *xn = xs + (q + 1) * n3;
-      e = cudaMemcpyAsync(xn, xs + q * n3, n3b, cudaMemcpyDeviceToDevice, C.s);
-      if (e == cudaSuccess) e = lf_step(C, xn, v, acc, dt);
-    }
+    // the segment's positions again (the velocity after the last drift is
+    // not needed, so the last closing kick is left out)
+    for (int64_t q = 0; q < L && e == cudaSuccess; ++q)
+      e = lf_half_step(C, xs + q * n3, xs + (q + 1) * n3, v, acc, dt, q > 0, nullptr);
+    // the sweep: second kick, drift (fused into the second kick's launch,
+    // writing the new lv to the other of d_lv and the now free velocity
+    // buffer), first kick
+    float *cur = d_lv, *other = v;
     for (int64_t q = L - 1; q >= 0 && e == cudaSuccess; --q) {
       const float *xa = xs + q * n3, *xb = xs + (q + 1) * n3;
-      e = lf_vjp(C, xb, d_lv, 0.5f * dt, d_lx, d_lm);      // second kick
-      if (e == cudaSuccess) e = lf_axpy(C, d_lv, d_lx, dt);  // drift
-      if (e == cudaSuccess) e = lf_vjp(C, xa, d_lv, 0.5f * dt, d_lx, d_lm);  // first kick
+      e = lf_vjp(C, xb, cur, 0.5f * dt, d_lx, d_lm, other, dt);  // second kick, drift
+      std::swap(cur, other);
+      if (e == cudaSuccess) e = lf_vjp(C, xa, cur, 0.5f * dt, d_lx, d_lm);  // first kick
     }
+    if (e == cudaSuccess && cur != d_lv)
+      e = cudaMemcpyAsync(d_lv, cur, n3b, cudaMemcpyDeviceToDevice, C.s);
   }
   return e == cudaSuccess ? NB_OK : lf_err(e);
 }
