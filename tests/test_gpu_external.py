@@ -155,3 +155,25 @@ def test_fused_and_general_block_steps_with_field_match_host(nb, prec):
         assert done == steps and t_last == t_end
         for k in sa:
             assert np.array_equal(sa[k], sb[k]), (prec, mode, k)
+
+
+def test_field_parameters_reach_the_device(nb, oracle_mod):
+    """A field with every parameter changed from Allen & Santillan's (centre
+    off the origin, other masses, scales, exponent and cut) moves the same
+    acceleration and jerk into the state as the oracle computes."""
+    ext = {"G": 0.9, "center": (0.4, -0.3, 0.2), "m_bulge": 500.0, "b_bulge": 0.5,
+           "m_disk": 3000.0, "a_disk": 4.0, "b_disk": 0.3, "m_halo": 5000.0,
+           "a_halo": 10.0, "gamma": 2.2, "r_cut": 9.0}
+    n = 500
+    m, x, v = _cluster(n, 35)
+    x = x + np.array([0.0, 0.0, 0.5])  # off the plane
+    with nb.NBody(m, x, v, eps=1e-3, precision="ds") as s:
+        s0 = s.get_state(want=("a", "jerk"))
+        s.set_external(ext)
+        s1 = s.get_state(want=("a", "jerk"))
+        _, w, _ = s.energy()
+    ea, phi, ej = oracle_mod.ext_field(x, ext, v=v)
+    assert np.abs(s1["a"] - s0["a"] - ea).max() <= 1e-12 * np.abs(ea).max()
+    assert np.abs(s1["jerk"] - s0["jerk"] - ej).max() <= 1e-12 * np.abs(ej).max()
+    W = oracle_mod.energy(m, x, v, 1e-3)[1] + float(np.sum(m * phi))
+    assert abs(w - W) <= 1e-12 * abs(W)

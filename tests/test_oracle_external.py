@@ -136,3 +136,17 @@ def test_hermite_with_field_circular_orbit(oracle_mod):
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 12.0 < r1 < 20.0 and 12.0 < r2 < 20.0, errs
     assert errs[2] < 1e-8 * R0
+
+
+def test_field_centre_is_a_translation(oracle_mod):
+    """The field about a centre c at x equals the field about the origin at
+    x - c (acceleration, jerk and potential)."""
+    rng = np.random.default_rng(5)
+    pts = rng.normal(0.0, 5.0, (10, 3))
+    vel = rng.normal(0.0, 10.0, (10, 3))
+    c = np.array([1.5, -2.0, 0.7])
+    a1, p1, j1 = oracle_mod.ext_field(pts, {"center": tuple(c)}, v=vel)
+    a2, p2, j2 = oracle_mod.ext_field(pts - c, v=vel)
+    assert np.allclose(a1, a2, rtol=1e-14, atol=0)
+    assert np.allclose(j1, j2, rtol=1e-14, atol=1e-14 * np.abs(j2).max())
+    assert np.allclose(p1, p2, rtol=1e-14, atol=0)
