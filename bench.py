@@ -871,6 +871,17 @@ def run_nsweep(args):
                 e1.record()
                 torch.cuda.synchronize()
                 row[f"hermite_{prec}_s"] = e0.elapsed_time(e1) / 1e3 / steps
+        # the same shared steps device-resident (graph replays, no host
+        # round trip per step)
+        with _lib.NBody(m, x, v, eps=eps, precision="ds", block_steps=False,
+                        lev_shared=10) as s:
+            s.run_blocks(2.0**-10)
+            e0, e1 = _events(torch)
+            e0.record()
+            done, _ = s.run_blocks((1 + steps) * 2.0**-10)
+            e1.record()
+            torch.cuda.synchronize()
+            row["hermite_ds_device_resident_s"] = e0.elapsed_time(e1) / 1e3 / max(done, 1)
         with _lib.NBody(m, x, v, eps=eps, precision="ds") as s:
             row["symplectic6_ds_s"] = _time_symplectic(torch, s, 6, 2.0**-10, steps)
         fm = torch.tensor(m, dtype=torch.float32, device=dev)
