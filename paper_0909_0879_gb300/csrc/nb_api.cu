@@ -93,7 +93,22 @@ namespace {
 // Balanced recursive bisection: split [lo, hi) of perm at a multiple of
 // `leaf` particles along the longest side of its bounding box (ties broken
 // by index, so the order is fully determined), recurse on both halves.
-void kd_split(const double *x, int64_t *perm, int64_t lo, int64_t hi, int64_t leaf) {
+// Levels of the bisection that may split off a thread: up to ~16 workers.
+int kd_threads() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  int lv = 0;
+  while (lv < 4 && (2u << lv) <= (hw ? hw : 1u)) ++lv;
+  return lv;
+}
+
+// Balanced bisection of perm[lo, hi) along the widest axis of its box, down
+// to leaves of `leaf` records.  With par > 0 the left half of a split runs
+// on another thread (par - 1 levels deeper may split again); the halves are
+// disjoint and the comparator is a total order, so the result does not
+// depend on the threads.
+void kd_split(const double *x, int64_t *perm, int64_t lo, int64_t hi, int64_t leaf,
+              int par = 0) {
+  std::vector<std::thread> workers;
   while (hi - lo > leaf) {
     double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
     for (int64_t k = lo; k < hi; ++k)
@@ -111,9 +126,15 @@ void kd_split(const double *x, int64_t *perm, int64_t lo, int64_t hi, int64_t le
       const double va = x[3 * a + ax], vb = x[3 * b + ax];
       return va < vb || (va == vb && a < b);
     });
-    kd_split(x, perm, lo, mid, leaf);
+    if (par > 0 && mid - lo > (int64_t(1) << 15)) {
+      workers.emplace_back(kd_split, x, perm, lo, mid, leaf, par - 1);
+      --par;
+    } else {
+      kd_split(x, perm, lo, mid, leaf, 0);
+    }
     lo = mid;  // tail loop on the right half
   }
+  for (auto &w : workers) w.join();
 }
 
 }  // namespace
@@ -124,7 +145,7 @@ extern "C" nb_status nb_spatial_order(int64_t n, const double *x, int64_t leaf,
     return fail(NB_ERR_INVALID_ARG, "need n >= 0, leaf >= 1 and non-null arrays");
   if (!finite_all(x, 3 * n)) return fail(NB_ERR_INVALID_ARG, "non-finite position");
   std::iota(perm, perm + n, int64_t(0));
-  kd_split(x, perm, 0, n, leaf);
+  kd_split(x, perm, 0, n, leaf, kd_threads());
   return NB_OK;
 }
 

@@ -127,3 +127,12 @@ def test_spatial_order_is_a_balanced_tree_layout(lib):
         sorted(map(tuple, np.sort(p[: 9984].reshape(-1, 256), axis=1)))
     with pytest.raises(_lib.NBodyError):
         _lib.spatial_order(np.full((3, 3), np.nan), 256)
+    # large sets split their upper levels over threads: the same permutation
+    # every time, and every 256-record leaf compact along a bisection
+    big = np.random.default_rng(2).normal(0.0, 1.0, (300000, 3))
+    pb = _lib.spatial_order(big, 256)
+    assert np.array_equal(np.sort(pb), np.arange(300000))
+    for _ in range(3):
+        assert np.array_equal(pb, _lib.spatial_order(big, 256))
+    leaf_ext = np.ptp(big[pb[: 299776]].reshape(-1, 256, 3), axis=1).max(axis=1)
+    assert np.median(leaf_ext) < 0.2 * np.ptp(big, axis=0).max()
