@@ -701,9 +701,10 @@ def run_adjoint(args):
 def _time_symplectic(torch, s, order, dt, steps):
     """Seconds per step of s.symplectic: the difference of a 0-step call
     (which only evaluates the acceleration at the start) and a `steps`
-    call, so each step carries exactly its own force evaluations.  The
-    step's graph is captured by a 1-step call first."""
-    s.symplectic(order, dt, 1)
+    call, so each step carries exactly its own force evaluations (and, in
+    a spatial layout, the run's share of its ordering).  A first call of
+    the same length captures the step's graph."""
+    s.symplectic(order, dt, steps)
     ms = []
     for k in (0, steps):
         e0, e1 = _events(torch)
@@ -741,15 +742,22 @@ def run_symplectic(args):
     props = torch.cuda.get_device_properties(0)
     peak = metrics.fp32_peak_tflops(props.multi_processor_count, 2070.0) * 1e12
     speed = []
+    # input order x the library's layout setting: generation order stepped as
+    # given, generation order with the automatic layout (the default), and
+    # input presorted with nb_spatial_order stepped as given
+    cases = (("generation", "as_given"), ("generation", "auto"), ("spatial", "as_given"))
     for prec in args.precisions.split(","):
-        for lay in ("generation", "spatial") if prec == "ds" else ("generation",):
+        for lay, mode in cases if prec == "ds" else (("generation", "as_given"),):
             mm, xx, vv = layouts[lay]
             for order in (6, 2):
                 with _lib.NBody(mm, xx, vv, eps=eps, precision=prec) as s:
+                    s.set_symplectic_layout(mode)
                     per_step = _time_symplectic(torch, s, order, 2.0**-8, 16)
+                    used = s.last_symplectic_layout()
                 stages = 7 if order == 6 else 1
                 ips = stages * n * n / per_step
-                speed.append({"precision": prec, "layout": lay, "order": order,
+                speed.append({"precision": prec, "input_order": lay, "layout_setting": mode,
+                              "layout_used": used, "order": order,
                               "s_per_step": per_step,
                               "ms_per_force_evaluation": per_step / stages * 1e3,
                               "interactions_per_s": ips,

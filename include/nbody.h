@@ -186,11 +186,27 @@ nb_status nb_last_block_path(nb_ctx *ctx, int32_t *fused);
  * and jerk are not advanced, so Hermite calls (nb_next_block, nb_predict,
  * nb_step, nb_run_blocks) answer NB_ERR_STATE until nb_set_state gives a
  * Hermite state.  Synchronises.  NB_ERR_INVALID_ARG: order not 2 or 6,
- * non-finite dt, nsteps < 0.  In split precision, particles stored in a
- * spatial order (see nb_spatial_order) let the force kernel take its
- * tile-relative far field for distant tiles: 10 % faster at N = 65,536 and
- * 26 % at 262,144 on a uniform sphere than in a random order. */
+ * non-finite dt, nsteps < 0.  In split precision, particles in a spatial
+ * order let the force kernel take its tile-relative far field for distant
+ * tiles (10 % faster at N = 65,536 and 26 % at 262,144 on a uniform sphere
+ * than in a random order); see nb_set_symplectic_layout. */
 nb_status nb_symplectic(nb_ctx *ctx, int32_t order, double dt, int64_t nsteps);
+
+/* Particle layout of nb_symplectic runs.  NB_LAYOUT_SPATIAL: each run with
+ * nsteps > 0 orders the particles by a balanced bisection of their current
+ * positions (nb_spatial_order with 256-particle leaves, on the host cores),
+ * gathers x, v, m into that order on the device, steps them there and
+ * scatters x, v, a back, so the caller sees its own order; the force sums
+ * then run in another order, which changes results only by rounding.
+ * NB_LAYOUT_AS_GIVEN: the particles' own order.  NB_LAYOUT_AUTO (default):
+ * spatial in split precision for N >= 16,384 when the run's estimated
+ * force time is large against the ordering's cost, else as given.
+ * NB_ERR_INVALID_ARG for another value. */
+enum { NB_LAYOUT_AUTO = 0, NB_LAYOUT_AS_GIVEN = 1, NB_LAYOUT_SPATIAL = 2 };
+nb_status nb_set_symplectic_layout(nb_ctx *ctx, int32_t mode);
+
+/* *spatial = 1 if the last nb_symplectic call ran in the spatial layout. */
+nb_status nb_last_symplectic_layout(nb_ctx *ctx, int32_t *spatial);
 
 /* External Galactic field (paper Sec. 2.1: the pair forces are summed with
  * the field of Allen & Santillan 1991, a spherical bulge and halo and an

@@ -67,6 +67,8 @@ SIGNATURES = [
     ("nb_set_block_mode", C.c_int, [_vp, _i32]),
     ("nb_last_block_path", C.c_int, [_vp, _P(_i32)]),
     ("nb_symplectic", C.c_int, [_vp, _i32, _d, _i64]),
+    ("nb_set_symplectic_layout", C.c_int, [_vp, _i32]),
+    ("nb_last_symplectic_layout", C.c_int, [_vp, _P(_i32)]),
     ("nb_external_allen_santillan", None, [_P(External)]),
     ("nb_set_external", C.c_int, [_vp, _P(External)]),
     ("nb_energy", C.c_int, [_vp, _P(_d), _P(_d), _P(_d)]),
@@ -307,6 +309,18 @@ class NBody:
         steps of dt.  Afterwards x, v and a (= A(x)) are current; Hermite
         calls need set_state first."""
         _check(self._L.nb_symplectic(self._h, int(order), float(dt), int(nsteps)))
+
+    SYMPLECTIC_LAYOUTS = {"auto": 0, "as_given": 1, "spatial": 2}
+
+    def set_symplectic_layout(self, mode: str):
+        """'auto', 'as_given' or 'spatial': the particle order symplectic
+        runs step in (the state is returned in the caller's order)."""
+        _check(self._L.nb_set_symplectic_layout(self._h, self.SYMPLECTIC_LAYOUTS[mode]))
+
+    def last_symplectic_layout(self) -> str:
+        f = C.c_int32()
+        _check(self._L.nb_last_symplectic_layout(self._h, C.byref(f)))
+        return "spatial" if f.value else "as_given"
 
     def set_external(self, ext=None):
         """Set the external Galactic field (a dict of nb_external fields,

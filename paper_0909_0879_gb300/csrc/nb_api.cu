@@ -205,6 +205,13 @@ struct nb_ctx {
   double sym_dt = 0.0;
   int64_t sym_graph_launches = 0;
   bool sym_graph_stale = false;  // the field changed since the capture
+  const double *sym_graph_x = nullptr;  // the position array the graph steps
+  // spatial layout of the symplectic steps: the state gathered into a
+  // bisection order, stepped there and scattered back
+  int sym_layout = 0;            // NB_LAYOUT_AUTO / AS_GIVEN / SPATIAL
+  int last_sym_spatial = 0;
+  double *lx = nullptr, *lv = nullptr, *la = nullptr, *lm = nullptr;
+  int64_t *lperm = nullptr;
   bool fresh = true;             // every particle still at t = 0 from nb_init
   // nb_symplectic moved x and v: the Hermite fields (jerk, times, levels)
   // no longer belong to them until nb_set_state
@@ -903,9 +910,16 @@ nb_status capture_blocks(nb_ctx *c, bool fused, cudaGraphExec_t *out, int64_t *l
 
 // ---- fixed-step symplectic integration
 
-// Acceleration of every particle into c->a (acceleration-only kernel of the
+// The arrays a symplectic run steps: the context's own, or the
+// spatially ordered copies.
+struct SymArrays {
+  double *x, *v, *a;
+  const double *m;
+};
+
+// Acceleration of every particle into S.a (acceleration-only kernel of the
 // built-in shape for n, or its acceleration-only counterpart).
-nb_status queue_acc_all(nb_ctx *c, cudaStream_t s, int64_t *launches) {
+nb_status queue_acc_all(nb_ctx *c, const SymArrays &S, cudaStream_t s, int64_t *launches) {
   const int v = acc_shape(choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, c->n,
                                          c->n_jt, c->num_sms));
   if (!has_acc_only(v)) return fail(NB_ERR_STATE, "force shape %d has no acceleration-only kernel", v);
@@ -923,7 +937,7 @@ nb_status queue_acc_all(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   A.n_i = c->n;
   A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
   A.G = c->cfg.G;
-  A.acc = c->a;
+  A.acc = S.a;
   A.jerk = nullptr;
   A.part = reinterpret_cast<float2 *>(c->part);
   A.err = c->err;
@@ -933,9 +947,9 @@ nb_status queue_acc_all(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   return NB_OK;
 }
 
-nb_status queue_kick_drift(nb_ctx *c, cudaStream_t s, double h, double d, bool rec,
-                           int64_t *launches) {
-  NB_CUDA(launch_kick_drift(c->n, c->n_jt, h, d, rec, c->ext, c->a, c->v, c->x, c->m,
+nb_status queue_kick_drift(nb_ctx *c, const SymArrays &S, cudaStream_t s, double h, double d,
+                           bool rec, int64_t *launches) {
+  NB_CUDA(launch_kick_drift(c->n, c->n_jt, h, d, rec, c->ext, S.a, S.v, S.x, S.m,
                             c->cfg.precision, c->jhi, c->jlo, c->jvel, c->jrel, c->tinfo, s));
   *launches += 1;
   return NB_OK;
@@ -943,18 +957,18 @@ nb_status queue_kick_drift(nb_ctx *c, cudaStream_t s, double h, double d, bool r
 
 // One step: the stages' kick-drift + force with the kicks between two
 // drifts merged, then the closing half kick.
-nb_status queue_symplectic_step(nb_ctx *c, cudaStream_t s, const double *w, int S, double dt,
-                                int64_t *launches) {
+nb_status queue_symplectic_step(nb_ctx *c, const SymArrays &A, cudaStream_t s, const double *w,
+                                int S, double dt, int64_t *launches) {
   for (int k = 0; k < S; ++k) {
     const double h = 0.5 * dt * ((k > 0 ? w[k - 1] : 0.0) + w[k]);
-    nb_status st = queue_kick_drift(c, s, h, w[k] * dt, true, launches);
-    if (st == NB_OK) st = queue_acc_all(c, s, launches);
+    nb_status st = queue_kick_drift(c, A, s, h, w[k] * dt, true, launches);
+    if (st == NB_OK) st = queue_acc_all(c, A, s, launches);
     if (st != NB_OK) return st;
   }
-  return queue_kick_drift(c, s, 0.5 * dt * w[S - 1], 0.0, false, launches);
+  return queue_kick_drift(c, A, s, 0.5 * dt * w[S - 1], 0.0, false, launches);
 }
 
-nb_status capture_symplectic(nb_ctx *c, const double *w, int S, double dt) {
+nb_status capture_symplectic(nb_ctx *c, const SymArrays &A, const double *w, int S, double dt) {
   if (c->sym_graph) {
     cudaGraphExecDestroy(c->sym_graph);
     c->sym_graph = nullptr;
@@ -965,7 +979,7 @@ nb_status capture_symplectic(nb_ctx *c, const double *w, int S, double dt) {
   int64_t nl = 0;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   nb_status qs = NB_ERR_CUDA;
-  if (e == cudaSuccess) qs = queue_symplectic_step(c, cs, w, S, dt, &nl);
+  if (e == cudaSuccess) qs = queue_symplectic_step(c, A, cs, w, S, dt, &nl);
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
   cudaStreamDestroy(cs);
   if (qs != NB_OK && qs != NB_ERR_CUDA) {
@@ -980,6 +994,55 @@ nb_status capture_symplectic(nb_ctx *c, const double *w, int S, double dt) {
   if (e != cudaSuccess)
     return fail(NB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
   c->sym_graph_launches = nl;
+  return NB_OK;
+}
+
+// Whether a run takes the spatial layout.  Automatic: split precision (the
+// far field is what the layout buys; measured 10 % faster per evaluation
+// at N = 65,536 and 26 % at 262,144 on a uniform sphere in random order),
+// N >= 16,384, and an estimated saving (10 % of the run's force time at
+// ~2e12 interactions/s) above twice the layout's cost (the bisection on the
+// host cores, ~3 ns per particle and level, and the copies).
+bool symplectic_spatial(const nb_ctx *c, int S, int64_t nsteps) {
+  if (c->sym_layout == NB_LAYOUT_AS_GIVEN || nsteps == 0) return false;
+  if (c->sym_layout == NB_LAYOUT_SPATIAL) return true;
+  if (c->cfg.precision != NB_DS || c->n < 16384) return false;
+  const double n = static_cast<double>(c->n);
+  const double run_s = static_cast<double>(nsteps) * S * n * n / 2e12;
+  const double layout_s = n * std::log2(n) * 3e-9 + n * 2e-8;
+  return 0.1 * run_s > 2.0 * layout_s;
+}
+
+// Gather x, v, m into a bisection order of the current positions.
+nb_status spatial_gather(nb_ctx *c, SymArrays *A) {
+  const int64_t n = c->n;
+  const size_t n3 = 3 * static_cast<size_t>(n);
+  if (!c->lx) {
+    nb_status s = dev_alloc_t(c, &c->lx, n3);
+    if (s == NB_OK) s = dev_alloc_t(c, &c->lv, n3);
+    if (s == NB_OK) s = dev_alloc_t(c, &c->la, n3);
+    if (s == NB_OK) s = dev_alloc_t(c, &c->lm, n);
+    if (s == NB_OK) s = dev_alloc_t(c, &c->lperm, n);
+    if (s != NB_OK) return s;
+  }
+  std::vector<double> hx(n3);
+  std::vector<int64_t> perm(n);
+  NB_CUDA(cudaMemcpyAsync(hx.data(), c->x, n3 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  nb_status s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  std::iota(perm.begin(), perm.end(), int64_t(0));
+  kd_split(hx.data(), perm.data(), 0, n, kJT, kd_threads());
+  NB_CUDA(cudaMemcpyAsync(c->lperm, perm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                          c->stream));
+  NB_CUDA(launch_permute(n, c->lperm, c->x, c->lx, 3, false, c->stream));
+  NB_CUDA(launch_permute(n, c->lperm, c->v, c->lv, 3, false, c->stream));
+  NB_CUDA(launch_permute(n, c->lperm, c->m, c->lm, 1, false, c->stream));
+  c->launches += 3;
+  // the host arrays go out of scope: the copy from them must be done first
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  *A = SymArrays{c->lx, c->lv, c->la, c->lm};
   return NB_OK;
 }
 
@@ -1070,11 +1133,18 @@ extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t 
   if (S == 0) return fail(NB_ERR_INVALID_ARG, "symplectic order %d is not 2 or 6", order);
   if (!std::isfinite(dt)) return fail(NB_ERR_INVALID_ARG, "non-finite time step");
   if (nsteps < 0) return fail(NB_ERR_INVALID_ARG, "negative step count");
+  SymArrays A{c->x, c->v, c->a, c->m};
+  const bool spatial = symplectic_spatial(c, S, nsteps);
+  if (spatial) {
+    s = spatial_gather(c, &A);
+    if (s != NB_OK) return s;
+  }
+  c->last_sym_spatial = spatial ? 1 : 0;
   // the acceleration at the current positions, then nsteps replays of one
   // step's graph
   int64_t nl = 0;
-  s = queue_kick_drift(c, c->stream, 0.0, 0.0, true, &nl);
-  if (s == NB_OK) s = queue_acc_all(c, c->stream, &nl);
+  s = queue_kick_drift(c, A, c->stream, 0.0, 0.0, true, &nl);
+  if (s == NB_OK) s = queue_acc_all(c, A, c->stream, &nl);
   if (s != NB_OK) return s;
   c->launches += nl;
   c->interactions += c->n * c->n;
@@ -1085,13 +1155,14 @@ extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t 
   c->t_pred = -1;
   if (nsteps > 0) {
     if (!c->sym_graph || c->sym_order != order || c->sym_dt != dt ||
-        c->sym_graph_part != c->part || c->sym_graph_stale) {
-      s = capture_symplectic(c, w, S, dt);
+        c->sym_graph_part != c->part || c->sym_graph_stale || c->sym_graph_x != A.x) {
+      s = capture_symplectic(c, A, w, S, dt);
       if (s != NB_OK) return s;
       c->sym_order = order;
       c->sym_dt = dt;
       c->sym_graph_part = c->part;
       c->sym_graph_stale = false;
+      c->sym_graph_x = A.x;
     }
     for (int64_t k = 0; k < nsteps; ++k) NB_CUDA(cudaGraphLaunch(c->sym_graph, c->stream));
     c->launches += nsteps * c->sym_graph_launches;
@@ -1099,10 +1170,33 @@ extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t 
   }
   // the acceleration left in the state is the total one at the final x
   if (c->ext.on) {
-    NB_CUDA(launch_ext_add(c->n, c->ext, c->x, c->a, c->stream));
+    NB_CUDA(launch_ext_add(c->n, c->ext, A.x, A.a, c->stream));
     c->launches += 1;
   }
+  if (spatial) {
+    NB_CUDA(launch_permute(c->n, c->lperm, c->lx, c->x, 3, true, c->stream));
+    NB_CUDA(launch_permute(c->n, c->lperm, c->lv, c->v, 3, true, c->stream));
+    NB_CUDA(launch_permute(c->n, c->lperm, c->la, c->a, 3, true, c->stream));
+    c->launches += 3;
+  }
   return sync_ctx(c);
+}
+
+extern "C" nb_status nb_set_symplectic_layout(nb_ctx *c, int32_t mode) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (mode != NB_LAYOUT_AUTO && mode != NB_LAYOUT_AS_GIVEN && mode != NB_LAYOUT_SPATIAL)
+    return fail(NB_ERR_INVALID_ARG, "unknown symplectic layout %d", mode);
+  c->sym_layout = mode;
+  return NB_OK;
+}
+
+extern "C" nb_status nb_last_symplectic_layout(nb_ctx *c, int32_t *spatial) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (!spatial) return fail(NB_ERR_INVALID_ARG, "null output pointer");
+  *spatial = c->last_sym_spatial;
+  return NB_OK;
 }
 
 extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,

@@ -251,6 +251,10 @@ cudaError_t launch_kick_drift(int64_t n, int64_t n_jt, double h, double d, bool 
                               const ExtField &E, const double *a, double *v, double *x,
                               const double *m, int prec, float4 *jhi, float4 *jlo,
                               float4 *jvel, float4 *jrel, float4 *tinfo, cudaStream_t s);
+// Rows of w doubles: dst[k] = src[perm[k]], or with scatter dst[perm[k]] =
+// src[k].
+cudaError_t launch_permute(int64_t n, const int64_t *perm, const double *src, double *dst,
+                           int w, bool scatter, cudaStream_t s);
 // a += a_ext(x) for every particle.
 cudaError_t launch_ext_add(int64_t n, const ExtField &E, const double *x, double *a,
                            cudaStream_t s);

@@ -81,7 +81,27 @@ __global__ void ext_add_kernel(int64_t n, const ExtField E, const double *__rest
   for (int c = 0; c < 3; ++c) a[3 * i + c] = av[c];
 }
 
+// dst[k] = src[perm[k]] (gather) or dst[perm[k]] = src[k] (scatter) for
+// rows of w doubles.
+__global__ void permute_kernel(int64_t n, const int64_t *__restrict__ perm,
+                               const double *__restrict__ src, double *__restrict__ dst, int w,
+                               int scatter) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int64_t p = perm[k];
+  const int64_t from = scatter ? k : p, to = scatter ? p : k;
+  for (int c = 0; c < w; ++c) dst[w * to + c] = src[w * from + c];
+}
+
 }  // namespace
+
+cudaError_t launch_permute(int64_t n, const int64_t *perm, const double *src, double *dst,
+                           int w, bool scatter, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  permute_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(n, perm, src, dst, w,
+                                                                       scatter ? 1 : 0);
+  return cudaGetLastError();
+}
 
 int symplectic_stages(int order, double *w) {
   if (order == 2) {

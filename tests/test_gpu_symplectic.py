@@ -273,3 +273,54 @@ def test_external_field_protocol(nb):
         s.step()
         s.set_external(None)
         s.step()
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+def test_spatial_layout_matches_oracle(nb, oracle_mod, prec):
+    """The spatial layout (state gathered into a bisection order, stepped,
+    scattered back) within the same force-error bound as the particles' own
+    order, with x, v and a returned in the caller's order."""
+    n, eps, dt, ns = 1000, 0.05, 1.0 / 32, 4
+    T = dt * ns
+    m, x, v = ics.plummer(n, 11)
+    with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+        s.set_symplectic_layout("spatial")
+        s.symplectic(6, dt, ns)
+        assert s.last_symplectic_layout() == "spatial"
+        st = s.get_state(want=("x", "v", "a"))
+    xo, vo = oracle_mod.symplectic(m, x, v, eps, dt, ns, 6)
+    aabs = _aabs_max(oracle_mod, m, (x, xo), eps)
+    assert np.all(np.linalg.norm(st["x"] - xo, axis=1) <= T * T * TOL[prec] * aabs)
+    assert np.all(np.linalg.norm(st["v"] - vo, axis=1) <= 2 * T * TOL[prec] * aabs)
+    ao, _ = oracle_mod.force_jerk(m, st["x"], np.zeros_like(xo), eps)
+    cond = np.linalg.norm(st["a"] - ao, axis=1) / _aabs_max(oracle_mod, m, (st["x"],), eps)
+    assert cond.max() <= TOL[prec]
+
+
+def test_automatic_layout_choice(nb):
+    """Automatic layout: the particles' own order for FP32, for zero steps
+    and for short split-precision runs; the spatial order for long ones;
+    both orders agree to rounding of the force sums."""
+    n = 20000
+    m, x, v = ics.uniform_sphere(n, 1006, Q=1.0, masses=ics.salpeter_masses(n, 1006))
+    eps = 0.1 * (4.0 * np.pi / (3.0 * n)) ** (1.0 / 3.0)
+    with nb.NBody(m, x, v, eps=eps, precision="fp32") as s:
+        s.symplectic(2, 2.0**-10, 200)
+        assert s.last_symplectic_layout() == "as_given"
+    res = {}
+    for mode in ("auto", "as_given"):
+        with nb.NBody(m, x, v, eps=eps, precision="ds") as s:
+            s.set_symplectic_layout(mode)
+            s.symplectic(2, 2.0**-10, 0)
+            assert s.last_symplectic_layout() == "as_given"
+            s.symplectic(2, 2.0**-10, 2)
+            assert s.last_symplectic_layout() == "as_given"
+            s.symplectic(2, 2.0**-10, 200)
+            res[mode] = (s.last_symplectic_layout(), s.get_state(want=("x", "v")))
+    assert res["auto"][0] == "spatial" and res["as_given"][0] == "as_given"
+    xa, xg = res["auto"][1]["x"], res["as_given"][1]["x"]
+    assert not np.array_equal(xa, xg)
+    assert np.abs(xa - xg).max() < 1e-6  # a misplaced particle would differ by O(0.1)
+    with nb.NBody(m, x, v, eps=eps) as s:
+        with pytest.raises(KeyError):
+            s.set_symplectic_layout("diagonal")
