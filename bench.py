@@ -743,9 +743,10 @@ def run_symplectic(args):
     peak = metrics.fp32_peak_tflops(props.multi_processor_count, 2070.0) * 1e12
     speed = []
     # input order x the library's layout setting: generation order stepped as
-    # given, generation order with the automatic layout (the default), and
-    # input presorted with nb_spatial_order stepped as given
-    cases = (("generation", "as_given"), ("generation", "auto"), ("spatial", "as_given"))
+    # given, with the automatic layout (the default), and with the spatial
+    # layout forced; and input presorted with nb_spatial_order stepped as given
+    cases = (("generation", "as_given"), ("generation", "auto"), ("generation", "spatial"),
+             ("spatial", "as_given"))
     for prec in args.precisions.split(","):
         for lay, mode in cases if prec == "ds" else (("generation", "as_given"),):
             mm, xx, vv = layouts[lay]

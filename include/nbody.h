@@ -199,7 +199,7 @@ nb_status nb_symplectic(nb_ctx *ctx, int32_t order, double dt, int64_t nsteps);
  * scatters x, v, a back, so the caller sees its own order; the force sums
  * then run in another order, which changes results only by rounding.
  * NB_LAYOUT_AS_GIVEN: the particles' own order.  NB_LAYOUT_AUTO (default):
- * spatial in split precision for N >= 16,384 when the run's estimated
+ * spatial in split precision for N >= 131,072 when the run's estimated
  * force time is large against the ordering's cost, else as given.
  * NB_ERR_INVALID_ARG for another value. */
 enum { NB_LAYOUT_AUTO = 0, NB_LAYOUT_AS_GIVEN = 1, NB_LAYOUT_SPATIAL = 2 };

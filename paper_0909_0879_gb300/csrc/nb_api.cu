@@ -126,7 +126,7 @@ void kd_split(const double *x, int64_t *perm, int64_t lo, int64_t hi, int64_t le
       const double va = x[3 * a + ax], vb = x[3 * b + ax];
       return va < vb || (va == vb && a < b);
     });
-    if (par > 0 && mid - lo > (int64_t(1) << 15)) {
+    if (par > 0 && mid - lo > (int64_t(1) << 12)) {
       workers.emplace_back(kd_split, x, perm, lo, mid, leaf, par - 1);
       --par;
     } else {
@@ -998,19 +998,21 @@ nb_status capture_symplectic(nb_ctx *c, const SymArrays &A, const double *w, int
 }
 
 // Whether a run takes the spatial layout.  Automatic: split precision (the
-// far field is what the layout buys; measured 10 % faster per evaluation
-// at N = 65,536 and 26 % at 262,144 on a uniform sphere in random order),
-// N >= 16,384, and an estimated saving (10 % of the run's force time at
-// ~2e12 interactions/s) above twice the layout's cost (the bisection on the
-// host cores, ~3 ns per particle and level, and the copies).
+// far field is what the layout buys), N >= 131,072 (on a uniform sphere in
+// random order the layout measured 26-30 % faster per evaluation from N =
+// 262,144 up, but only 8 % at 65,536 and nothing on a concentrated
+// Plummer cluster there), and an estimated saving, a quarter of the run's
+// force time at ~2e12 interactions/s, above 1.5 times the layout's cost
+// (the bisection on the host cores, ~8 ns per particle and level, and the
+// copies).
 bool symplectic_spatial(const nb_ctx *c, int S, int64_t nsteps) {
   if (c->sym_layout == NB_LAYOUT_AS_GIVEN || nsteps == 0) return false;
   if (c->sym_layout == NB_LAYOUT_SPATIAL) return true;
-  if (c->cfg.precision != NB_DS || c->n < 16384) return false;
+  if (c->cfg.precision != NB_DS || c->n < 131072) return false;
   const double n = static_cast<double>(c->n);
   const double run_s = static_cast<double>(nsteps) * S * n * n / 2e12;
-  const double layout_s = n * std::log2(n) * 3e-9 + n * 2e-8;
-  return 0.1 * run_s > 2.0 * layout_s;
+  const double layout_s = n * std::log2(n) * 8e-9 + n * 2e-8;
+  return 0.25 * run_s > 1.5 * layout_s;
 }
 
 // Gather x, v, m into a bisection order of the current positions.

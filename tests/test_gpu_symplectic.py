@@ -301,11 +301,11 @@ def test_automatic_layout_choice(nb):
     """Automatic layout: the particles' own order for FP32, for zero steps
     and for short split-precision runs; the spatial order for long ones;
     both orders agree to rounding of the force sums."""
-    n = 20000
+    n = 131072
     m, x, v = ics.uniform_sphere(n, 1006, Q=1.0, masses=ics.salpeter_masses(n, 1006))
     eps = 0.1 * (4.0 * np.pi / (3.0 * n)) ** (1.0 / 3.0)
     with nb.NBody(m, x, v, eps=eps, precision="fp32") as s:
-        s.symplectic(2, 2.0**-10, 200)
+        s.symplectic(2, 2.0**-10, 40)
         assert s.last_symplectic_layout() == "as_given"
     res = {}
     for mode in ("auto", "as_given"):
@@ -315,7 +315,7 @@ def test_automatic_layout_choice(nb):
             assert s.last_symplectic_layout() == "as_given"
             s.symplectic(2, 2.0**-10, 2)
             assert s.last_symplectic_layout() == "as_given"
-            s.symplectic(2, 2.0**-10, 200)
+            s.symplectic(2, 2.0**-10, 40)
             res[mode] = (s.last_symplectic_layout(), s.get_state(want=("x", "v")))
     assert res["auto"][0] == "spatial" and res["as_given"][0] == "as_given"
     xa, xg = res["auto"][1]["x"], res["as_given"][1]["x"]
