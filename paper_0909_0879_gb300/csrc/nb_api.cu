@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <new>
 #include <numeric>
 #include <chrono>
 #include <cmath>
@@ -126,12 +127,16 @@ void kd_split(const double *x, int64_t *perm, int64_t lo, int64_t hi, int64_t le
       const double va = x[3 * a + ax], vb = x[3 * b + ax];
       return va < vb || (va == vb && a < b);
     });
+    bool spawned = false;
     if (par > 0 && mid - lo > (int64_t(1) << 12)) {
-      workers.emplace_back(kd_split, x, perm, lo, mid, leaf, par - 1);
-      --par;
-    } else {
-      kd_split(x, perm, lo, mid, leaf, 0);
+      try {
+        workers.emplace_back(kd_split, x, perm, lo, mid, leaf, par - 1);
+        spawned = true;
+        --par;
+      } catch (...) {  // no thread to be had: this one does the half
+      }
     }
+    if (!spawned) kd_split(x, perm, lo, mid, leaf, 0);
     lo = mid;  // tail loop on the right half
   }
   for (auto &w : workers) w.join();
@@ -145,7 +150,11 @@ extern "C" nb_status nb_spatial_order(int64_t n, const double *x, int64_t leaf,
     return fail(NB_ERR_INVALID_ARG, "need n >= 0, leaf >= 1 and non-null arrays");
   if (!finite_all(x, 3 * n)) return fail(NB_ERR_INVALID_ARG, "non-finite position");
   std::iota(perm, perm + n, int64_t(0));
-  kd_split(x, perm, 0, n, leaf, kd_threads());
+  try {
+    kd_split(x, perm, 0, n, leaf, kd_threads());
+  } catch (...) {
+    return fail(NB_ERR_OOM, "host memory for the bisection");
+  }
   return NB_OK;
 }
 
@@ -235,7 +244,13 @@ nb_status dev_alloc(nb_ctx *c, void **p, size_t bytes) {
     return fail(e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA,
                 "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   }
-  c->allocs.push_back(*p);
+  try {
+    c->allocs.push_back(*p);
+  } catch (...) {  // no C++ exception leaves the library
+    cudaFree(*p);
+    *p = nullptr;
+    return fail(NB_ERR_OOM, "host memory for the allocation list");
+  }
   return NB_OK;
 }
 
@@ -445,7 +460,8 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   for (int64_t i = 0; i < n; ++i)
     if (m[i] < 0) return fail(NB_ERR_INVALID_ARG, "negative mass at %lld", (long long)i);
 
-  nb_ctx *c = new nb_ctx();
+  nb_ctx *c = new (std::nothrow) nb_ctx();
+  if (!c) return fail(NB_ERR_OOM, "host memory for the context");
   c->cfg = *cfg;
   c->n = n;
   c->n_jt = (n + kJT - 1) / kJT;
@@ -542,7 +558,13 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRY(sync_ctx(c));
   // initial force must be finite
   {
-    std::vector<double> probe(n3);
+    std::vector<double> probe;
+    try {
+      probe.resize(n3);
+    } catch (...) {
+      nb_destroy(c);
+      return fail(NB_ERR_OOM, "host memory for the initial-force check");
+    }
     TRYC(cudaMemcpy(probe.data(), c->a, n3 * sizeof(double), cudaMemcpyDeviceToHost));
     if (!finite_all(probe.data(), static_cast<int64_t>(n3))) {
       nb_destroy(c);
@@ -1027,14 +1049,24 @@ nb_status spatial_gather(nb_ctx *c, SymArrays *A) {
     if (s == NB_OK) s = dev_alloc_t(c, &c->lperm, n);
     if (s != NB_OK) return s;
   }
-  std::vector<double> hx(n3);
-  std::vector<int64_t> perm(n);
+  std::vector<double> hx;
+  std::vector<int64_t> perm;
+  try {
+    hx.resize(n3);
+    perm.resize(n);
+  } catch (...) {
+    return fail(NB_ERR_OOM, "host memory for the spatial layout");
+  }
   NB_CUDA(cudaMemcpyAsync(hx.data(), c->x, n3 * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
   nb_status s = sync_ctx(c);
   if (s != NB_OK) return s;
   std::iota(perm.begin(), perm.end(), int64_t(0));
-  kd_split(hx.data(), perm.data(), 0, n, kJT, kd_threads());
+  try {
+    kd_split(hx.data(), perm.data(), 0, n, kJT, kd_threads());
+  } catch (...) {
+    return fail(NB_ERR_OOM, "host memory for the bisection");
+  }
   NB_CUDA(cudaMemcpyAsync(c->lperm, perm.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice,
                           c->stream));
   NB_CUDA(launch_permute(n, c->lperm, c->x, c->lx, 3, false, c->stream));

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -475,7 +476,8 @@ nb_status nb_batched_init(nb_batch **out, int32_t n_clusters, const int64_t *off
   for (int64_t i = 0; i < n; ++i)
     if (!(m[i] >= 0)) return bfail(NB_ERR_INVALID_ARG, "negative or non-finite mass");
 
-  nb_batch *b = new nb_batch();
+  nb_batch *b = new (std::nothrow) nb_batch();
+  if (!b) return bfail(NB_ERR_OOM, "host memory for the batch");
   b->n_clusters = n_clusters;
   b->n = n;
   b->max_n = max_n;
@@ -495,7 +497,13 @@ nb_status nb_batched_init(nb_batch **out, int32_t n_clusters, const int64_t *off
       *p = nullptr;
       return bfail(NB_ERR_CUDA, "cudaMalloc", e);
     }
-    b->allocs.push_back(*p);
+    try {
+      b->allocs.push_back(*p);
+    } catch (...) {  // no C++ exception leaves the library
+      cudaFree(*p);
+      *p = nullptr;
+      return bfail(NB_ERR_OOM, "host memory for the allocation list");
+    }
     return NB_OK;
   };
   const size_t n3 = 3 * static_cast<size_t>(n) * sizeof(double);
@@ -516,7 +524,13 @@ nb_status nb_batched_init(nb_batch **out, int32_t n_clusters, const int64_t *off
   if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
     return cleanup(bfail(NB_ERR_CUDA, "event creation failed"));
   // processing order: largest cost (n^2) first, ties by index
-  std::vector<int32_t> order(n_clusters), ident(n_clusters);
+  std::vector<int32_t> order, ident;
+  try {
+    order.resize(n_clusters);
+    ident.resize(n_clusters);
+  } catch (...) {
+    return cleanup(bfail(NB_ERR_OOM, "host memory for the processing order"));
+  }
   std::iota(order.begin(), order.end(), 0);
   std::iota(ident.begin(), ident.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t q) {
