@@ -27,7 +27,6 @@ import hashlib
 import json
 import math
 import os
-import re
 import subprocess
 import sys
 import threading
@@ -59,7 +58,8 @@ def parse():
     p.add_argument("--no-energy", action="store_true", help="skip the FP64 energy check")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=0,
+                   help="steps of the end-to-end leg (0 = as many as --steps)")
     p.add_argument("--variant", type=int, default=-1)
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--workload", default="king1m",
@@ -149,21 +149,19 @@ class ClockSampler:
 
 
 def force_traffic_from_profile(n):
-    """DRAM bytes per force launch from the committed ncu summary, if it was
-    taken on the current force-kernel source; otherwise None."""
-    path = os.path.join(ROOT, "profiles", "force_jerk_ds_traffic.md")
+    """DRAM bytes per force launch from the committed ncu record
+    (profiles/force_jerk_ds_traffic.json), if it was taken on the current
+    force-kernel source at this N; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "force_jerk_ds_traffic.json")
     src = os.path.join(ROOT, "paper_0909_0879_gb300", "csrc", "nb_force.cu")
-    if not os.path.exists(path):
-        return None
-    txt = open(path).read()
-    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    b = re.search(r"dram_bytes_per_launch_at_n1048576:\s*([0-9.eE+]+)", txt)
-    if not h or not b:
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
         return None
     cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if cur != h.group(1) or n != N_DEFAULT:
+    if rec.get("source_sha256") != cur or int(rec.get("n", -1)) != n:
         return None
-    return float(b.group(1))
+    return float(rec["dram_bytes_per_launch"])
 
 
 def peak_info(num_sms):
@@ -184,9 +182,11 @@ def peak_info(num_sms):
 # ------------------------------------------------------------- CPU leg
 
 
-def cpu_baseline(m, x, v, n, seconds):
+def cpu_baseline(m, x, v, n, seconds, keep=False):
     """Time the FP64 oracle's force + jerk for a bounded sample of
-    i-particles against all n j-particles on every host core."""
+    i-particles against all n j-particles on every host core.  With keep,
+    the sample's indices and the oracle's acceleration and jerk come back
+    too (keys "idx", "acc", "jerk")."""
     from oracle import oracle as O
 
     O.build()
@@ -201,12 +201,37 @@ def cpu_baseline(m, x, v, n, seconds):
     ns = max(cores, ns - ns % cores)
     sample = np.sort(rng.choice(n, ns, replace=False))
     t0 = time.perf_counter()
-    O.force_jerk(m, x, v, EPS, idx=sample)
+    ra, rj = O.force_jerk(m, x, v, EPS, idx=sample)
     dt = time.perf_counter() - t0
-    return {"value": ns * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{ns} random i-particles x {n} j-particles, FP64 acc+jerk, "
-                      f"{dt:.1f} s on {cores} OpenMP threads",
-            "seconds": dt}
+    out = {"value": ns * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{ns} random i-particles x {n} j-particles, FP64 acc+jerk, "
+                     f"{dt:.1f} s on {cores} OpenMP threads",
+           "seconds": dt}
+    if keep:
+        out.update(idx=sample, acc=ra, jerk=rj)
+    return out
+
+
+def force_error(acc, jerk, ra, rj, cond=None):
+    """Errors of GPU force + jerk rows against the FP64 oracle's on the same
+    particles: per-particle e_i = |da_i| / max(|a_i|, 1e-3 rms|a|) (max and
+    99th percentile), norm-wise ||da|| / ||a||, and, with cond = (sum_j
+    |f_ij|, sum_j |jerk_ij|) on the first rows, the condition-relative
+    |da_i| / sum_j |f_ij|."""
+    def per(g, r):
+        sc = np.sqrt(np.mean(np.sum(r * r, 1)))
+        return np.linalg.norm(g - r, axis=1) / np.maximum(np.linalg.norm(r, axis=1), 1e-3 * sc)
+
+    ea, ej = per(acc, ra), per(jerk, rj)
+    out = {"acc_max_ei": float(ea.max()), "acc_p99_ei": float(np.quantile(ea, 0.99)),
+           "jerk_max_ei": float(ej.max()), "jerk_p99_ei": float(np.quantile(ej, 0.99)),
+           "acc_norm": float(np.linalg.norm(acc - ra) / np.linalg.norm(ra)),
+           "jerk_norm": float(np.linalg.norm(jerk - rj) / np.linalg.norm(rj))}
+    if cond is not None:
+        k = len(cond[0])
+        out["acc_cond_max"] = float((np.linalg.norm(acc[:k] - ra[:k], axis=1) / cond[0]).max())
+        out["jerk_cond_max"] = float((np.linalg.norm(jerk[:k] - rj[:k], axis=1) / cond[1]).max())
+    return out
 
 
 def _oracle_beside(work, units, unit, sample):
@@ -276,6 +301,7 @@ def run_ours(args, rank, world, local_rank):
         s.set_force_variant(args.variant, args.grid)
     props = torch.cuda.get_device_properties(dev)
     num_sms = props.multi_processor_count
+    st0 = s.get_state()  # the initial state, for the force-error check
 
     E0 = None
     if not args.no_energy:
@@ -334,7 +360,7 @@ def run_ours(args, rank, world, local_rank):
         pinned[k] = t.numpy()
         pinned[k][...] = a
     st = pinned
-    e2e_steps = max(1, args.e2e_steps)
+    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else max(1, args.steps)
     h2d = sum(a.nbytes for a in st.values())
     d2h = h2d
     torch.cuda.synchronize(dev)
@@ -375,15 +401,41 @@ def run_ours(args, rank, world, local_rank):
         s.close()
         return 0
 
+    # Force error against the FP64 oracle, outside the timed region: the
+    # initial state, all N particles evaluated in the bench's launch
+    # configuration (identity i-list of length N, the same built-in shape
+    # and grid as the timed force call), compared on the oracle's sample.
+    s.set_state(st0)
+    s.predict(0.0)
+    d_idx = torch.arange(n, dtype=torch.int32, device=dev)
+    d_acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    d_jrk = torch.empty_like(d_acc)
+    s.force_jerk_dev(d_idx, n, d_acc, d_jrk)
+    torch.cuda.synchronize(dev)
     force_s = float(np.mean(force_ms)) / 1e3
     achieved = metrics.FLOPS_PER_INTERACTION * n * n / force_s / 1e12
     peak, sm_max, peak_src = peak_info(num_sms)
     traffic = force_traffic_from_profile(n) if args.precision == "ds" else None
     clk_mhz = clocks.get("sm_mhz") if clocks else None
     cpu = None
+    ferr = None
     if not args.no_cpu:
-        cpu = cpu_baseline(m, x, v, n, args.cpu_seconds)
+        from oracle import oracle as O
+
+        cpu = cpu_baseline(m, x, v, n, args.cpu_seconds, keep=True)
+        samp = cpu.pop("idx")
+        ra, rj = cpu.pop("acc"), cpu.pop("jerk")
         cpu.pop("seconds", None)
+        sel = torch.from_numpy(samp).to(dev)
+        ga = d_acc[sel].cpu().numpy()
+        gj = d_jrk[sel].cpu().numpy()
+        kc = min(1024, len(samp))
+        cond = O.force_jerk_abs(m, x, v, EPS, idx=samp[:kc])
+        ferr = force_error(ga, gj, ra, rj, cond)
+        ferr["sample"] = (f"the CPU baseline's {len(samp)} random particles (condition sums on "
+                          f"the first {kc}), initial state; GPU: all N evaluated as in a timed "
+                          f"step")
+    del d_acc, d_jrk, d_idx
     out = {
         "metric": METRIC,
         "value": value,
@@ -432,6 +484,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "force_err": ferr,
     }
     if sweep is not None:
         out["sweep"] = sweep
@@ -485,6 +538,45 @@ def run_shared1024(args):
             "the FP64 oracle's shared-step Hermite loop, the same 256 steps")
     print(json.dumps(out), flush=True)
     return 0
+
+
+def block_force_errors(_lib, m, x, v, eps, precs, checkpoints=(0, 5, 15), ns=4096):
+    """Force + jerk errors of the block-step workload against the FP64
+    oracle: at the given block steps (from the start), the GPU's force on
+    ns sampled particles (seed 2002) at the predicted state, against the
+    oracle's on the same state (predicted in FP64 by the oracle from the
+    GPU's stored state)."""
+    from oracle import oracle as O
+
+    n = len(m)
+    sample = np.sort(np.random.default_rng(2002).choice(n, ns, replace=False)).astype(np.int32)
+    rows = {}
+    for prec in precs:
+        rows[prec] = []
+        with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3,
+                        lev_max=20) as s:
+            done = 0
+            for k in checkpoints:
+                while done < k:
+                    s.step()
+                    done += 1
+                st = s.get_state()
+                t, na = s.next_block()
+                s.predict(t)
+                dt = (int(round(t * 2**20)) - st["t_tick"]) * 2.0**-20
+                xp, vp = O.predict(st["x"], st["v"], st["a"], st["jerk"], dt)
+                acc, jerk = s.force_jerk(sample)
+                ra, rj = O.force_jerk(m, xp, vp, eps, idx=sample)
+                cond = O.force_jerk_abs(m, xp, vp, eps, idx=sample)
+                r = force_error(acc, jerk, ra, rj, cond)
+                r.update(block_step=k, t=t, n_act=na)
+                rows[prec].append(r)
+                s.force_jerk_dev(None, na, None, None)
+                s.correct(t)
+                done += 1
+    return {"rows": rows,
+            "sample": f"{ns} random particles (seed 2002) at the predicted state of block "
+                      f"steps {list(checkpoints)}, FP64 oracle on the same state"}
 
 
 def run_block65536(args):
@@ -559,6 +651,7 @@ def run_block65536(args):
             "device_resident": dev_res,
             "note": "value/ms: host-driven nb_step loop; device_resident: nb_run_blocks"}
     if not args.no_cpu:
+        out["force_err"] = block_force_errors(_lib, m, x, v, eps, args.precisions.split(","))
         out["cpu_baseline"] = cpu_baseline(m, x, v, n, 3.0)
     print(json.dumps(out), flush=True)
     return 0

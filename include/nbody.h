@@ -317,12 +317,15 @@ nb_status nb_spatial_order(int64_t n, const double *x, int64_t leaf,
 
 /* Install a tuning table for the built-in variant choice: for an active
  * list of n_i particles the first entry k (in order) with n_i >= min_n[k]
- * gives the variant; lists shorter than every min_n fall back to the
- * built-in choice.  count == 0 removes the table.  Variants must match the
- * context's precision and eps == 0 masking (NB_ERR_INVALID_ARG); at most 32
- * entries.  An explicit nb_set_force_variant still takes precedence. */
+ * gives the variant and, when grid_ctas is non-NULL and grid_ctas[k] > 0,
+ * a cap on its persistent grid (fewer CTAs split each i-block's j-range
+ * into fewer stream-K segments); lists shorter than every min_n fall back
+ * to the built-in choice.  count == 0 removes the table.  Variants must
+ * match the context's precision and eps masking (NB_ERR_INVALID_ARG), grid
+ * caps must be >= 0; at most 32 entries.  An explicit nb_set_force_variant
+ * still takes precedence. */
 nb_status nb_set_force_table(nb_ctx *ctx, int32_t count, const int64_t *min_n,
-                             const int32_t *variant);
+                             const int32_t *variant, const int32_t *grid_ctas);
 
 /* Describe compiled force-kernel variant v: precision, i-particles per
  * thread, threads per i-particle, threads per CTA, and whether it packs two
@@ -332,10 +335,18 @@ nb_status nb_set_force_table(nb_ctx *ctx, int32_t count, const int64_t *min_n,
 nb_status nb_variant_info(int32_t v, int32_t *precision, int32_t *ipt,
                           int32_t *tpi, int32_t *threads, int32_t *packed);
 
-/* Host-side fault injection for tests: kind 1 makes the next device
- * allocation of nb_init fail with NB_ERR_OOM (process-wide, one shot);
- * kind 2 makes the next synchronisation of ctx report NB_ERR_TIMEOUT
- * (ctx required).  No GPU fault is ever caused. */
+/* Fault injection for tests: kind 1 makes the next device allocation of
+ * nb_init fail with NB_ERR_OOM (process-wide, one shot); kind 2 makes the
+ * next synchronisation of ctx report NB_ERR_TIMEOUT (ctx required); kind 3
+ * makes every bounded wait of the fused block steps' look-back (the
+ * ordered compaction of the active list in nb_run_blocks) wait a few polls
+ * for a word that no CTA publishes, so each runs out and nb_run_blocks
+ * returns NB_ERR_DEVICE (ctx required; in force until kind 0); kind 0
+ * clears the context's injections.  No GPU fault is ever caused.
+ *
+ * Device-side errors (NB_ERR_DEVICE) are reported once: the device error
+ * word is cleared when it is read.  The particle state after the failed
+ * call is unspecified; nb_set_state restores a saved one. */
 nb_status nb_debug_inject(nb_ctx *ctx, int32_t kind);
 
 /* ------------------------------------------------------------------------
@@ -445,9 +456,12 @@ nb_status nb_lf_backward(int64_t n, const float *d_m, const float *d_ckpt,
  * no context and calls no cudaMalloc, cudaFree or allocating library
  * routine.
  *
- * Computes, on the caller's stream, the acceleration and jerk (eq. 1 and its
- * time derivative, Plummer softening eps, constant G) on the particles
- * d_idx[0..n_idx) (NULL: 0..n_idx-1, n_idx <= n) from all n particles.
+ * Computes, on the caller's stream, the softened acceleration
+ * a_i = G sum_j m_j d / (|d|^2 + eps^2)^(3/2), d = x_j - x_i, and its time
+ * derivative (the jerk) on the particles d_idx[0..n_idx) (NULL:
+ * 0..n_idx-1, n_idx <= n; an index list may repeat indices and be longer
+ * than n) from all n particles.  When eps^2 is not a normal FP32 number
+ * (eps == 0 included) the i == j term is zeroed explicitly.
  * Inputs: d_m (n), d_x and d_v ((n,3) row-major), all float64 device
  * arrays; outputs d_acc and d_jerk, float64 (n_idx,3), device.  precision:
  * NB_FP32 or NB_DS.  Indices must lie in [0, n) (not checked on the device).
@@ -466,7 +480,9 @@ nb_status nb_lf_backward(int64_t n, const float *d_m, const float *d_ckpt,
  * occupancy; make that first call before any stream capture begins.
  * Errors: NB_ERR_INVALID_ARG for n outside [1, 2^31-1], n_idx outside
  * [0, 2^31-1] (or above n without an index list), a NULL pointer, eps < 0,
- * G <= 0 or an unknown precision; NB_ERR_CUDA for a failed launch or set-up.
+ * G <= 0 or an unknown precision; NB_ERR_CUDA for a failed launch or set-up,
+ * and, without launching anything, when a CUDA error from earlier work is
+ * already pending on the calling thread (that error is left set).
  * Asynchronous; n_idx == 0 is a no-op.
  * ---------------------------------------------------------------------- */
 nb_status nb_force_jerk_noalloc(int64_t n, const double *d_m,

@@ -20,6 +20,20 @@ NB_FP32, NB_DS = 0, 1
 TICKS_LOG2 = 20
 
 
+def eps_masks(eps: float) -> int:
+    """1 when the kernels zero the i == j pair explicitly: eps^2 in FP32 is
+    not a normal number (the library's rule)."""
+    return 1 if float(np.float32(eps * eps)) < float(np.finfo(np.float32).tiny) else 0
+
+
+def _precision(p) -> int:
+    if p in ("ds", NB_DS) and not isinstance(p, bool):
+        return NB_DS
+    if p in ("fp32", NB_FP32) and not isinstance(p, bool):
+        return NB_FP32
+    raise ValueError(f"precision must be 'ds', 'fp32', NB_DS or NB_FP32, not {p!r}")
+
+
 class NBodyError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"[{status}] {message}")
@@ -80,7 +94,7 @@ SIGNATURES = [
     ("nb_launch_count", _i64, [_vp]),
     ("nb_set_force_variant", C.c_int, [_vp, _i32, _i32]),
     ("nb_spatial_order", C.c_int, [_i64, _vp, _i64, _vp]),
-    ("nb_set_force_table", C.c_int, [_vp, _i32, _vp, _vp]),
+    ("nb_set_force_table", C.c_int, [_vp, _i32, _vp, _vp, _vp]),
     ("nb_variant_info", C.c_int, [_i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     ("nb_debug_inject", C.c_int, [_vp, _i32]),
     ("nb_batched_init", C.c_int, [_P(_vp), _i32, _vp, _vp, _vp, _vp, _P(Config)]),
@@ -206,7 +220,7 @@ class NBody:
         cfg = default_config()
         cfg.G, cfg.eps, cfg.eta, cfg.eta_start = float(G), float(eps), float(eta), float(eta_start)
         cfg.lev_min, cfg.lev_max = int(lev_min), int(lev_max)
-        cfg.precision = NB_DS if precision in ("ds", NB_DS) else NB_FP32
+        cfg.precision = _precision(precision)
         cfg.block_steps = 1 if block_steps else 0
         cfg.lev_shared = int(lev_shared)
         cfg.sync_timeout_ms = int(sync_timeout_ms)
@@ -426,12 +440,16 @@ class NBody:
         _check(self._L.nb_set_force_variant(self._h, int(variant), int(grid_ctas)))
 
     def set_force_table(self, table):
-        """table: list of (min_active, variant), checked in order."""
+        """table: list of (min_active, variant) or (min_active, variant,
+        grid_cap), checked in order (grid_cap 0: the full persistent
+        grid)."""
         mins = np.ascontiguousarray([t[0] for t in table], dtype=np.int64)
         vars_ = np.ascontiguousarray([t[1] for t in table], dtype=np.int32)
-        _check(self._L.nb_set_force_table(self._h, len(table),
-                                          mins.ctypes.data if len(table) else None,
-                                          vars_.ctypes.data if len(table) else None))
+        grids = np.ascontiguousarray([t[2] if len(t) > 2 else 0 for t in table], dtype=np.int32)
+        k = len(table)
+        _check(self._L.nb_set_force_table(self._h, k, mins.ctypes.data if k else None,
+                                          vars_.ctypes.data if k else None,
+                                          grids.ctypes.data if k else None))
 
     def inject(self, kind: int):
         _check(self._L.nb_debug_inject(self._h, int(kind)))
@@ -469,14 +487,14 @@ class Batch:
         cfg.G, cfg.eps = float(G), float(eps)
         cfg.block_steps = 0
         cfg.lev_shared = int(lev_shared)
-        cfg.precision = NB_DS if precision in ("ds", NB_DS) else NB_FP32
+        cfg.precision = _precision(precision)
         if stream is not None:
             cfg.stream = (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)) or None
         self.n_clusters = off.shape[0] - 1
         self.n = n
         self.offsets = off
         self.precision = cfg.precision
-        self.mask = 1 if cfg.eps == 0.0 else 0
+        self.mask = eps_masks(cfg.eps)
         h = C.c_void_p()
         _check(L.nb_batched_init(C.byref(h), self.n_clusters, off.ctypes.data, m.ctypes.data,
                                  x.ctypes.data, v.ctypes.data, C.byref(cfg)))
@@ -541,7 +559,7 @@ def force_jerk_noalloc(n, d_m, d_x, d_v, d_idx, n_idx, d_acc, d_jerk, *, eps, G=
         sp = stream.cuda_stream or None
     else:
         sp = int(stream) or None
-    prec = NB_DS if precision in ("ds", NB_DS) else NB_FP32
+    prec = _precision(precision)
     _check(L.nb_force_jerk_noalloc(int(n), _ptr(d_m), _ptr(d_x), _ptr(d_v), _ptr(d_idx),
                                    int(n_idx), float(eps), float(G), prec, _ptr(d_acc),
                                    _ptr(d_jerk), sp))

@@ -196,9 +196,11 @@ struct nb_ctx {
   int table_count = 0;
   int64_t table_min[32];
   int32_t table_var[32];
+  int32_t table_grid[32];  // persistent-grid cap of each entry (0: full grid)
   int grid_cap = 0;
   int64_t launches = 0, n_blocks = 0, interactions = 0;
   bool inject_timeout = false;
+  bool inject_lookback = false;  // fused look-back waits run out (test injection)
   cudaGraphExec_t blk_graph = nullptr;  // device-resident block steps, general scheduler
   double *blk_graph_part = nullptr;
   cudaGraphExec_t fus_graph = nullptr;  // device-resident block steps, fused kernels
@@ -287,10 +289,15 @@ nb_status sync_ctx(nb_ctx *c) {
     if (us > 2000) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
   const int err = static_cast<int>(c->h_scal[kCtlErr] & 0xffffffff);
-  if (err != 0)
+  if (err != 0) {
+    // reported once: clear the word (stream-ordered) so that the context
+    // can go on after the caller restores a state
+    c->h_scal[kCtlErr] = 0;
+    cudaMemsetAsync(c->scal + kCtlErr, 0, sizeof(int64_t), c->stream);
     return fail(NB_ERR_DEVICE, "a bounded device-side wait ran out: %s%s(device error word 0x%x)",
                 (err & kErrWaitTimeout) ? "force kernel shared-memory tile; " : "",
                 (err & kErrScanTimeout) ? "active-list look-back; " : "", err);
+  }
   return NB_OK;
 }
 
@@ -309,11 +316,17 @@ nb_status check_hermite(nb_ctx *c) {
   return NB_OK;
 }
 
-int pick_variant(nb_ctx *c, int64_t n_i) {
+// Force shape for n_i active particles, and the cap of its persistent grid
+// (which sets the stream-K j-split) through *grid_cap.
+int pick_variant(nb_ctx *c, int64_t n_i, int *grid_cap) {
+  *grid_cap = c->grid_cap;
   if (c->variant_override >= 0) return c->variant_override;
   for (int k = 0; k < c->table_count; ++k)
-    if (n_i >= c->table_min[k]) return c->table_var[k];
-  return choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, n_i, c->n_jt, c->num_sms);
+    if (n_i >= c->table_min[k]) {
+      if (c->table_grid[k] > 0) *grid_cap = c->table_grid[k];
+      return c->table_var[k];
+    }
+  return choose_variant(c->cfg.precision, eps_masks(c->cfg.eps), n_i, c->n_jt, c->num_sms);
 }
 
 nb_status ensure_part(nb_ctx *c, size_t bytes) {
@@ -338,8 +351,9 @@ nb_status ensure_part(nb_ctx *c, size_t bytes) {
 nb_status queue_force(nb_ctx *c, const int32_t *d_idx, int64_t n_i, double *d_acc,
                       double *d_jerk) {
   if (n_i == 0) return NB_OK;
-  const int v = pick_variant(c, n_i);
-  const int grid = force_grid(v, n_i, c->n_jt, c->num_sms, c->grid_cap);
+  int cap = 0;
+  const int v = pick_variant(c, n_i, &cap);
+  const int grid = force_grid(v, n_i, c->n_jt, c->num_sms, cap);
   nb_status s = ensure_part(c, part_bytes(v, grid));
   if (s != NB_OK) return s;
   ForceArgs A;
@@ -351,7 +365,7 @@ nb_status queue_force(nb_ctx *c, const int32_t *d_idx, int64_t n_i, double *d_ac
   A.n_jt = c->n_jt;
   A.idx = d_idx;
   A.n_i = n_i;
-  A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
+  A.eps2 = eps2_f32(c->cfg.eps);
   A.G = c->cfg.G;
   A.acc = d_acc;
   A.jerk = d_jerk;
@@ -755,7 +769,7 @@ struct Bucket {
 };
 
 int step_buckets(const nb_ctx *c, Bucket *b) {
-  const ShapeBuckets sb = shape_buckets(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, c->n_jt,
+  const ShapeBuckets sb = shape_buckets(c->cfg.precision, eps_masks(c->cfg.eps), c->n_jt,
                                         c->num_sms);
   // buckets no active count can reach (or empty ones) are left out
   int k = 0;
@@ -776,7 +790,7 @@ ForceArgs device_force_args(const nb_ctx *c, const Bucket &b) {
   A.n_jt = c->n_jt;
   A.idx = c->act;
   A.n_i = 0;
-  A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
+  A.eps2 = eps2_f32(c->cfg.eps);
   A.G = c->cfg.G;
   A.acc = c->a1;
   A.jerk = c->j1;
@@ -843,6 +857,11 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   B.act = c->act;
   B.ctl = c->scal;
   B.status = c->lb_status;
+  if (c->inject_lookback) {
+    // test injection: a few polls for an epoch no CTA ever publishes
+    B.lb_wait_limit = 256;
+    B.lb_epoch_skew = uint64_t(1) << 24;
+  }
   EndArgs E;
   E.n = c->n;
   E.n_jt = c->n_jt;
@@ -942,7 +961,7 @@ struct SymArrays {
 // Acceleration of every particle into S.a (acceleration-only kernel of the
 // built-in shape for n, or its acceleration-only counterpart).
 nb_status queue_acc_all(nb_ctx *c, const SymArrays &S, cudaStream_t s, int64_t *launches) {
-  const int v = acc_shape(choose_variant(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0, c->n,
+  const int v = acc_shape(choose_variant(c->cfg.precision, eps_masks(c->cfg.eps), c->n,
                                          c->n_jt, c->num_sms));
   if (!has_acc_only(v)) return fail(NB_ERR_STATE, "force shape %d has no acceleration-only kernel", v);
   const int grid = force_grid(v, c->n, c->n_jt, c->num_sms, 0);
@@ -957,7 +976,7 @@ nb_status queue_acc_all(nb_ctx *c, const SymArrays &S, cudaStream_t s, int64_t *
   A.n_jt = c->n_jt;
   A.idx = nullptr;
   A.n_i = c->n;
-  A.eps2 = static_cast<float>(c->cfg.eps * c->cfg.eps);
+  A.eps2 = eps2_f32(c->cfg.eps);
   A.G = c->cfg.G;
   A.acc = S.a;
   A.jerk = nullptr;
@@ -1246,7 +1265,7 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
   // partial-sum scratch for every shape the device-resident steps may run
   size_t pb = 0;
   {
-    const ShapeBuckets sb = shape_buckets(c->cfg.precision, c->cfg.eps == 0.0 ? 1 : 0,
+    const ShapeBuckets sb = shape_buckets(c->cfg.precision, eps_masks(c->cfg.eps),
                                           c->n_jt, c->num_sms);
     for (int q = 0; q < sb.nbk; ++q) {
       const size_t bytes = part_bytes(sb.v[q], c->num_sms * ctas_per_sm(sb.v[q]));
@@ -1448,8 +1467,8 @@ nb_status nb_set_force_variant(nb_ctx *c, int32_t variant, int32_t grid_ctas) {
     const Variant &V = variant_at(variant);
     if (V.prec != c->cfg.precision)
       return fail(NB_ERR_INVALID_ARG, "variant %d has the other precision", variant);
-    if (V.mask != (c->cfg.eps == 0.0 ? 1 : 0))
-      return fail(NB_ERR_INVALID_ARG, "variant %d does not match the eps == 0 masking", variant);
+    if (V.mask != eps_masks(c->cfg.eps))
+      return fail(NB_ERR_INVALID_ARG, "variant %d does not match the self-pair masking of this eps", variant);
   }
   c->variant_override = variant;
   c->grid_cap = grid_ctas > 0 ? grid_ctas : 0;
@@ -1457,7 +1476,7 @@ nb_status nb_set_force_variant(nb_ctx *c, int32_t variant, int32_t grid_ctas) {
 }
 
 nb_status nb_set_force_table(nb_ctx *c, int32_t count, const int64_t *min_n,
-                             const int32_t *variant) {
+                             const int32_t *variant, const int32_t *grid_ctas) {
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   if (count < 0 || count > 32) return fail(NB_ERR_INVALID_ARG, "table holds 0..32 entries");
@@ -1466,8 +1485,10 @@ nb_status nb_set_force_table(nb_ctx *c, int32_t count, const int64_t *min_n,
     if (variant[k] < 0 || variant[k] >= num_variants())
       return fail(NB_ERR_INVALID_ARG, "unknown force variant %d", variant[k]);
     const Variant &V = variant_at(variant[k]);
-    if (V.prec != c->cfg.precision || V.mask != (c->cfg.eps == 0.0 ? 1 : 0))
+    if (V.prec != c->cfg.precision || V.mask != eps_masks(c->cfg.eps))
       return fail(NB_ERR_INVALID_ARG, "variant %d does not match the context", variant[k]);
+    if (grid_ctas && grid_ctas[k] < 0)
+      return fail(NB_ERR_INVALID_ARG, "negative grid cap %d", grid_ctas[k]);
   }
   // partial-sum scratch for the largest grid any table entry can use
   size_t pb = 0;
@@ -1481,6 +1502,7 @@ nb_status nb_set_force_table(nb_ctx *c, int32_t count, const int64_t *min_n,
   for (int k = 0; k < count; ++k) {
     c->table_min[k] = min_n[k];
     c->table_var[k] = variant[k];
+    c->table_grid[k] = grid_ctas ? grid_ctas[k] : 0;
   }
   return NB_OK;
 }
@@ -1505,6 +1527,19 @@ nb_status nb_debug_inject(nb_ctx *c, int32_t kind) {
   if (kind == 2) {
     if (!c) return fail(NB_ERR_INVALID_ARG, "timeout injection needs a context");
     c->inject_timeout = true;
+    return NB_OK;
+  }
+  if (kind == 3 || kind == 0) {
+    if (!c) return fail(NB_ERR_INVALID_ARG, "this injection needs a context");
+    const bool want = kind == 3;
+    if (kind == 0) c->inject_timeout = false;
+    if (c->inject_lookback != want) {
+      // the fused block-step graph holds the waits' arguments: capture anew
+      cudaStreamSynchronize(c->stream);
+      if (c->fus_graph) cudaGraphExecDestroy(c->fus_graph);
+      c->fus_graph = nullptr;
+      c->inject_lookback = want;
+    }
     return NB_OK;
   }
   return fail(NB_ERR_INVALID_ARG, "unknown injection kind %d", kind);

@@ -373,7 +373,7 @@ nb_status bfail(nb_status s, const char *msg, cudaError_t e = cudaSuccess) {
 
 int pick_bvariant(const nb_batch *b) {
   if (b->variant >= 0) return b->variant;
-  const int mask = b->cfg.eps == 0.0 ? 1 : 0;
+  const int mask = eps_masks(b->cfg.eps);
   if (mask) return b->cfg.precision ? 8 : 9;
   return b->cfg.precision ? 0 : 4;
 }
@@ -412,7 +412,7 @@ nb_status launch_batch(nb_batch *b, int v, int grid, int32_t n_items, const int3
   A.dt = std::ldexp(1.0, -b->cfg.lev_shared);
   A.idt2 = std::ldexp(1.0, 2 * b->cfg.lev_shared);
   A.idt3 = std::ldexp(1.0, 3 * b->cfg.lev_shared);
-  A.eps2 = static_cast<float>(b->cfg.eps * b->cfg.eps);
+  A.eps2 = eps2_f32(b->cfg.eps);
   A.G = b->cfg.G;
   A.nsteps = nsteps;
   A.cap = b->max_n;
@@ -575,7 +575,7 @@ nb_status nb_batched_set_tuning(nb_batch *b, int32_t variant, int32_t steps_per_
     return bfail(NB_ERR_INVALID_ARG, "unknown batched variant");
   if (variant >= 0) {
     const BEntry &E = kBTable[variant];
-    if (E.prec != b->cfg.precision || E.mask != (b->cfg.eps == 0.0 ? 1 : 0))
+    if (E.prec != b->cfg.precision || E.mask != eps_masks(b->cfg.eps))
       return bfail(NB_ERR_INVALID_ARG, "variant precision or eps == 0 masking differs from the batch");
   }
   if (steps_per_launch < 1) return bfail(NB_ERR_INVALID_ARG, "steps_per_launch must be >= 1");

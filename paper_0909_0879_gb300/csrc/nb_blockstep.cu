@@ -61,7 +61,8 @@ __device__ __forceinline__ uint64_t lb_word(uint64_t epoch, uint64_t flag, uint6
 // prefix and stops there, or moves 32 tiles further back.  Returns false if
 // a wait ran out.  Warp-uniform.
 __device__ __forceinline__ bool look_back(const unsigned long long *status, int64_t vid,
-                                          uint64_t epoch, int lane, int64_t *excl_out) {
+                                          uint64_t epoch, uint32_t limit, int lane,
+                                          int64_t *excl_out) {
   int64_t excl = 0;
   for (int64_t top = vid - 1; top >= 0; top -= 32) {
     const int64_t j = top - lane;
@@ -71,7 +72,7 @@ __device__ __forceinline__ bool look_back(const unsigned long long *status, int6
       if (j >= 0) w = ld_relaxed(status + j);
       const bool ready = j < 0 || (w >> 40) == epoch;
       if (__all_sync(0xffffffffu, ready)) break;
-      if (it >= kWaitLimit) return false;
+      if (it >= limit) return false;
     }
     const bool pre = j >= 0 && ((w >> kValBits) & 3) == kFlagPre;
     const unsigned pm = __ballot_sync(0xffffffffu, pre);
@@ -148,7 +149,8 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
       st_relaxed(B.status + vid,
                  lb_word(epoch, vid == 0 ? kFlagPre : kFlagAgg, static_cast<uint64_t>(agg)));
     int64_t excl = 0;
-    const bool ok = look_back(B.status, vid, epoch, lane, &excl);
+    const bool ok = look_back(B.status, vid, epoch + B.lb_epoch_skew, B.lb_wait_limit, lane,
+                              &excl);
     if (lane == 0) {
       if (!ok)
         atomicOr(reinterpret_cast<int *>(ctl + kCtlErr), kErrScanTimeout);

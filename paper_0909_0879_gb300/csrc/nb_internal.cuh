@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cfloat>
+
 namespace nbi {
 
 // Time is an integer count of 2^-20 ticks.
@@ -20,6 +22,18 @@ constexpr uint32_t kWaitLimit = 1u << 24;
 
 // Device error-word bits.
 constexpr int kErrWaitTimeout = 1;
+
+// Whether the kernels must zero the i == j pair term explicitly: eps^2 in
+// FP32 is not a normal number (eps == 0, or so small that the device, which
+// flushes subnormals to zero, would see eps^2 = 0 and evaluate the self
+// pair as 0 * rsqrt(0) = NaN).
+inline int eps_masks(double eps) {
+  return static_cast<float>(eps * eps) < FLT_MIN ? 1 : 0;
+}
+// eps^2 as the FP32 kernels take it: 0 when the masked kernels run.
+inline float eps2_f32(double eps) {
+  return eps_masks(eps) ? 0.f : static_cast<float>(eps * eps);
+}
 
 // One force + jerk evaluation: active i-list against all (padded) j-records.
 struct ForceArgs {
@@ -215,6 +229,11 @@ struct BeginArgs {
   int32_t *act;
   int64_t *ctl;
   unsigned long long *status;        // n_jt look-back words
+  // Look-back waits: polls before giving up, and an offset added to the
+  // epoch the waits look for (nonzero only for the test injection that
+  // makes every wait run out: no CTA publishes that epoch).
+  uint32_t lb_wait_limit = kWaitLimit;
+  uint64_t lb_epoch_skew = 0;
 };
 cudaError_t launch_block_begin(const BeginArgs &B, cudaStream_t s);
 

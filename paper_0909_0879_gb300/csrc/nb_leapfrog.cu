@@ -408,9 +408,11 @@ LfCtx make_ctx(int64_t n, const float *m, float eps, float G, void *stream) {
   LfCtx C;
   C.n = n;
   C.m = m;
-  C.eps2 = eps * eps;
+  // eps^2 not a normal float: the kernels zero the i == j term (and take
+  // eps^2 = 0, which is what the device's flush of subnormals would make of it)
+  C.mask = eps * eps < FLT_MIN ? 1 : 0;
+  C.eps2 = C.mask ? 0.f : eps * eps;
   C.G = G;
-  C.mask = eps == 0.f ? 1 : 0;
   // A failed query leaves its error for the launch's error check to report.
   int dev = 0;
   C.sms = 0;

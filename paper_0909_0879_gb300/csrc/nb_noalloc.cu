@@ -299,7 +299,7 @@ extern "C" nb_status nb_force_jerk_noalloc(int64_t n, const double *d_m, const d
   NaDevice *D = nullptr;
   int st = na_setup(dev, &D);
   if (st != NB_OK) return static_cast<nb_status>(st);
-  const int mask = eps == 0.0 ? 1 : 0;
+  const int mask = eps_masks(eps);
   const uint64_t n_jt = static_cast<uint64_t>((n + kNaJT - 1) / kNaJT);
   const uint64_t n_ib = static_cast<uint64_t>((n_idx + kNaBI - 1) / kNaBI);
   const uint64_t U = n_ib * n_jt;
@@ -318,12 +318,20 @@ extern "C" nb_status nb_force_jerk_noalloc(int64_t n, const double *d_m, const d
   A.v = d_v;
   A.idx = d_idx;
   A.n_i = n_idx;
-  A.eps2 = static_cast<float>(eps * eps);
+  A.eps2 = eps2_f32(eps);
   A.G = G;
   A.acc = d_acc;
   A.jerk = d_jerk;
   A.part = D->part;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // An error left pending by earlier work on this thread would be returned
+  // by the launch check below and blamed on this call: report it as what it
+  // is (without clearing it) and launch nothing.
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return static_cast<nb_status>(set_error(
+        NB_ERR_CUDA, "a CUDA error from earlier work is pending (left set): %s",
+        cudaGetErrorString(e)));
   na_kernel(precision, mask)<<<static_cast<unsigned>(P), kNaNT, 0, s>>>(A, U,
                                                                          static_cast<int>(P));
   e = cudaGetLastError();

@@ -2,8 +2,11 @@
 
 Force kernel: for each active-list length bucket (powers of two of the
 active fraction), every compiled variant of the context's precision is
-timed on a random active subset with CUDA events; the fastest per bucket
-forms a table installed with ``nb_set_force_table``.
+timed on a random active subset with CUDA events (L2 flushed before each
+timing), then the fastest few again with smaller persistent grids, which
+sets how finely the stream-K split cuts each i-block's j-range (the
+j-split); the fastest (variant, grid cap) per bucket forms a table
+installed with ``nb_set_force_table``.
 
 Batched kernel: every compatible (variant, steps per launch) pair is timed
 on the actual cluster set for a few steps under the CUDA graph; the
@@ -48,37 +51,71 @@ def _save_cache(c):
     os.replace(tmp, CACHE)
 
 
-def _time_ms(fn, reps=2):
+_FLUSH = {}
+
+
+def _flush_l2():
+    """Write 256 MB (more than the 129 MB L2) so that the next timing starts
+    from a cold cache, as a force call in a real step does."""
     import torch
 
-    best = float("inf")
+    dev = torch.cuda.current_device()
+    buf = _FLUSH.get(dev)
+    if buf is None:
+        buf = _FLUSH[dev] = torch.empty(64 * 1024 * 1024, dtype=torch.float32,
+                                        device=torch.device("cuda", dev))
+    buf.zero_()
+
+
+def _time_ms(fn, reps=2, flush=False):
+    """Median of reps CUDA-event timings of fn (L2 flushed before each one,
+    outside the events, when flush is set)."""
+    import torch
+
+    ts = []
     for _ in range(reps):
+        if flush:
+            _flush_l2()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         fn()
         e1.record()
         torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    return best
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
 
 
-def tune_force(s: "_lib.NBody", fractions=(1.0, 1 / 8, 1 / 64, 1 / 1024), seed=7, reps=2,
-               use_cache=True):
-    """Time every compatible variant for active lists of n * fraction
-    particles; install and return the table [(min_active, variant), ...]."""
+def grid_caps(num_sms):
+    """Caps of the persistent grid searched with each shape: the full grid
+    (0), two and one CTA per SM, and half and a quarter of the SMs.  A
+    smaller grid gives each CTA a longer contiguous range of (i-block,
+    j-tile) units, so fewer i-blocks have their j-range split into stream-K
+    segments (less fix-up work) at the cost of fewer busy SMs."""
+    return [0, 2 * num_sms, num_sms, num_sms // 2, num_sms // 4]
+
+
+def tune_force(s: "_lib.NBody", fractions=(1.0, 1 / 8, 1 / 64, 1 / 1024), seed=7, reps=3,
+               use_cache=True, finalists=3):
+    """For active lists of n * fraction particles, time every compatible
+    variant at the full persistent grid, then the `finalists` fastest with
+    each cap of grid_caps() (the stream-K j-split), L2 flushed before every
+    timing; install and return the table [(min_active, variant, grid_cap),
+    ...] and the timings."""
     import torch
 
     n = s.n
     prec = s.cfg.precision
-    mask = 1 if s.cfg.eps == 0.0 else 0
-    key = f"force|{_gpu_key()}|p{prec}|m{mask}|n{n}|" + ",".join(f"{f:g}" for f in fractions)
+    mask = _lib.eps_masks(s.cfg.eps)
+    key = (f"force2|{_gpu_key()}|p{prec}|m{mask}|n{n}|" +
+           ",".join(f"{f:g}" for f in fractions))
     cache = _load_cache() if use_cache else {}
     if key in cache:
         table = [tuple(t) for t in cache[key]["table"]]
         s.set_force_table(table)
         return table, cache[key]["timings"]
     dev = torch.device("cuda", torch.cuda.current_device())
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     cands = []
     for v in range(_lib.num_variants()):
         info = _lib.variant_info(v)
@@ -96,19 +133,28 @@ def tune_force(s: "_lib.NBody", fractions=(1.0, 1 / 8, 1 / 64, 1 / 1024), seed=7
         idx = torch.from_numpy(ics.random_active_subset(n, na, seed)).to(dev)
         acc = torch.empty((na, 3), dtype=torch.float64, device=dev)
         jrk = torch.empty_like(acc)
-        best = None
-        for v in cands:
-            s.set_force_variant(v, 0)
-            s.force_jerk_dev(idx, na, acc, jrk)  # warm-up
-            ms = _time_ms(lambda: s.force_jerk_dev(idx, na, acc, jrk), reps)
-            timings[f"{na}:{v}"] = ms
-            if best is None or ms < best[1]:
-                best = (v, ms)
-        table.append((na, best[0]))
+
+        def run(v, cap):
+            s.set_force_variant(v, cap)
+            s.force_jerk_dev(idx, na, acc, jrk)  # warm-up (and scratch sizing)
+            ms = _time_ms(lambda: s.force_jerk_dev(idx, na, acc, jrk), reps, flush=True)
+            timings[f"{na}:{v}:{cap}"] = ms
+            return ms
+
+        first = sorted((run(v, 0), v) for v in cands)
+        best = (first[0][1], 0, first[0][0])
+        for _, v in first[:finalists]:
+            for cap in grid_caps(num_sms)[1:]:
+                if cap < 1:
+                    continue
+                ms = run(v, cap)
+                if ms < best[2]:
+                    best = (v, cap, ms)
+        table.append((na, best[0], best[1]))
     s.set_force_variant(-1, 0)
     # a bucket applies from its own length upwards until the next larger one
     table.sort(key=lambda t: -t[0])
-    table[-1] = (1, table[-1][1])
+    table[-1] = (1,) + tuple(table[-1][1:])
     s.set_force_table(table)
     if use_cache:
         cache[key] = {"table": table, "timings": timings}
@@ -137,7 +183,7 @@ def tune_batched(b: "_lib.Batch", steps=50, spl=(1000, 10), use_cache=True):
             except _lib.NBodyError:
                 break
             b.run(steps)  # capture + warm-up
-            ms = _time_ms(lambda: b.run(steps), 1)
+            ms = _time_ms(lambda: b.run(steps), 1)  # the ~100 MB state stays in L2
             timings[f"{v}:{S}"] = ms
             if best is None or ms < best[2]:
                 best = (v, S, ms)

@@ -122,6 +122,21 @@ def test_eps_zero_masks_self_term(nb, oracle_mod, prec):
     check(acc, jerk, ra, rj, prec, cond)
 
 
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+def test_tiny_eps_takes_masked_kernels(nb, prec):
+    """An eps whose square is not a normal FP32 number is zero on the
+    device (subnormals flush to zero), so the context runs the kernels that
+    zero the i == j term: finite, and bit for bit the eps = 0 result."""
+    m, x, v = ics.plummer(500, 10)
+    idx = np.arange(500, dtype=np.int32)
+    out = []
+    for eps in (0.0, 1e-20):
+        with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+            out.append(s.force_jerk(idx))
+    assert np.isfinite(out[1][0]).all() and np.isfinite(out[1][1]).all()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_deterministic_and_duplicate_indices(nb):
     n = 5000
     m, x, v = ics.plummer(n, 3)
@@ -166,8 +181,10 @@ def test_device_pointer_path_matches_host_path(nb):
 
 def test_king_1m_sampled_parity(nb, oracle_mod):
     """Full-size single evaluation (N = 1,048,576 King W0 = 7, eps = 1e-4),
-    every particle active, in the bench's launch configuration; 256 sampled
-    particles against the oracle."""
+    every particle active, particles in generation order (i-blocks and
+    j-tiles spread over the cluster, so nearly every tile takes the
+    split-precision difference); 256 sampled particles against the
+    oracle."""
     import torch
 
     n, eps = 1 << 20, 1e-4
@@ -241,3 +258,49 @@ def test_tile_relative_far_field_on_sorted_particles(nb, oracle_mod):
             acc, jerk = s.force_jerk(idx)
             print(k, "errors", check(acc[sample], jerk[sample], ra, rj, "ds", cond))
             assert np.linalg.norm(acc - a12) / np.linalg.norm(a12) < 1e-6
+
+
+def test_king_1m_bench_layout_parity(nb, oracle_mod):
+    """The headline evaluation exactly as the bench times it: N = 1,048,576
+    King W0 = 7, eps = 1e-4, particles stored in nb_spatial_order (256 per
+    leaf), Hermite shared step 2^-10 with every particle active, the force
+    call of a step (active list from nb_next_block, built-in shape and grid)
+    at the predicted state.  In this layout most (i-block, tile) pairs take
+    the tile-relative FP32 far field; the built-in long-list shape must be
+    the tile-relative one (bitwise equal to forcing variant 26).  1024
+    sampled particles against the oracle on the same predicted state: the
+    condition-relative and norm-wise bars, and the per-particle e_i <= 1e-6
+    of the split-precision target."""
+    import torch
+
+    n, eps = 1 << 20, 1e-4
+    m, x, v = ics.king(n, 7.0, 1003)
+    perm = nb.spatial_order(x, 256)
+    m, x, v = m[perm], x[perm], v[perm]
+    sample = np.sort(np.random.default_rng(2013).choice(n, 1024, replace=False))
+    assert nb.variant_info(26)["precision"] == 1 and nb.variant_info(26)["packed"] == 1
+    with nb.NBody(m, x, v, eps=eps, precision="ds", block_steps=False, lev_shared=10) as s:
+        st = s.get_state()
+        t, na = s.next_block()
+        assert na == n
+        s.predict(t)
+        d_acc = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+        d_jerk = torch.zeros_like(d_acc)
+        s.force_jerk_dev(None, na, d_acc, d_jerk)
+        s.sync()
+        sel = torch.from_numpy(sample).cuda()
+        acc = d_acc[sel].cpu().numpy()
+        jerk = d_jerk[sel].cpu().numpy()
+        # the default shape for this length is the tile-relative one
+        s.set_force_variant(26, 0)
+        d_acc26 = torch.zeros_like(d_acc)
+        d_jerk26 = torch.zeros_like(d_acc)
+        s.force_jerk_dev(torch.arange(n, dtype=torch.int32, device="cuda"), n, d_acc26, d_jerk26)
+        s.sync()
+        assert torch.equal(d_acc, d_acc26) and torch.equal(d_jerk, d_jerk26)
+    dt = t - 0.0
+    xp, vp = oracle_mod.predict(st["x"], st["v"], st["a"], st["jerk"], dt)
+    ra, rj, cond = oracle_with_cond(oracle_mod, m, xp, vp, eps, idx=sample)
+    errs = check(acc, jerk, ra, rj, "ds", cond)
+    print("king 1M bench layout (max e_i acc, jerk, norm acc, jerk)", errs)
+    assert errs[0] <= 1e-6, f"per-particle DS force error {errs[0]:.3e} at N = 1M"

@@ -229,6 +229,63 @@ def test_host_fault_injection(nb):
         assert np.isfinite(tot)
 
 
+def test_device_wait_runs_out_and_context_recovers(nb):
+    """The bounded waits of the fused block steps' look-back: injection 3
+    makes each wait a few polls for a word no CTA ever publishes, so every
+    wait runs out, the kernel records it in the device error word and
+    returns, and nb_run_blocks reports NB_ERR_DEVICE (no hang, no fault).
+    After the injection is cleared and the saved state restored, the same
+    context runs the same steps bit for bit like a fresh one."""
+    n = 4096  # 16 tiles: 15 CTAs look back
+    m, x, v = ics.plummer(n, 41, masses=ics.salpeter_masses(n, 41))
+    kw = dict(eps=1e-4, eta=0.02, lev_min=6, lev_max=20)
+    t_end = 2.0**-7
+    with nb.NBody(m, x, v, **kw) as s:
+        st = s.get_state()
+        s.inject(3)
+        with pytest.raises(nb.NBodyError) as e:
+            s.run_blocks(t_end)
+        assert e.value.status == nb.NB_ERR_DEVICE
+        assert "look-back" in str(e.value)
+        s.inject(0)
+        s.set_state(st)
+        done, _ = s.run_blocks(t_end)
+        assert s.last_block_path() == "fused" and done > 0
+        got = s.get_state()
+    with nb.NBody(m, x, v, **kw) as r:
+        r.run_blocks(t_end)
+        want = r.get_state()
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+
+
+def test_fp32_range_reports_numeric_error(nb):
+    """Two particles 1e-18 apart with eps = 0: in FP64 the pair force is
+    ~1e33, but the FP32 pair arithmetic overflows (m / r^3 ~ 1e51), and the
+    library reports NB_ERR_NUMERIC instead of returning infinities: at
+    nb_init (the initial force) and from nb_force_jerk after nb_set_state
+    brings such a pair into a running context."""
+    n = 64
+    m, x, v = ics.plummer(n, 42)
+    x = x.copy()
+    x[0] = 0.0
+    x[1] = [1e-18, 0.0, 0.0]
+    for prec in ("ds", "fp32"):
+        with pytest.raises(nb.NBodyError) as e:
+            nb.NBody(m, x, v, eps=0.0, precision=prec)
+        assert e.value.status == nb.NB_ERR_NUMERIC
+    m, x, v = ics.plummer(n, 42)
+    with nb.NBody(m, x, v, eps=0.0, block_steps=False, lev_shared=8) as s:
+        st = s.get_state()
+        st["x"][0] = 0.0
+        st["x"][1] = [1e-18, 0.0, 0.0]
+        s.set_state(st)
+        s.predict(0.0)
+        with pytest.raises(nb.NBodyError) as e:
+            s.force_jerk(np.array([0, 1, 2], dtype=np.int32))
+        assert e.value.status == nb.NB_ERR_NUMERIC
+
+
 def test_allocation_cap_reports_oom(nb, monkeypatch):
     monkeypatch.setenv("NB_TEST_MAX_BYTES", "1000")
     m, x, v = ics.plummer(1000, 2)
