@@ -64,13 +64,15 @@ def parse():
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--workload", default="king1m",
                    choices=["king1m", "shared1024", "block65536", "batched", "adjoint",
-                            "nsweep", "symplectic"],
+                            "nsweep", "symplectic", "isplit"],
                    help="king1m is the headline; the others time the remaining workloads "
                         "and print their own JSON line")
     p.add_argument("--block-steps", type=int, default=0,
                    help="block65536: stop after this many block steps (0 = run to t = 1/8)")
     p.add_argument("--precisions", default="ds,fp32",
                    help="workloads other than king1m: comma-separated precisions to run")
+    p.add_argument("--shards", type=int, default=2,
+                   help="isplit: shards of the i-split run on this GPU")
     p.add_argument("--sweep", action="store_true",
                    help="also time single evaluations at active fractions 2^-10..1")
     return p.parse_args()
@@ -1032,12 +1034,60 @@ def run_nsweep(args):
     return 0
 
 
+def run_isplit(args):
+    """The i-split of the paper's two-GPU version (Sec. 4) on one GPU: the
+    headline cluster (N = 1,048,576 King W0 = 7 in the spatial layout,
+    eps = 1e-4, Hermite shared dt 2^-10, all active) advanced by P shard
+    contexts that each evaluate the force and corrector of their slice of
+    the active list and exchange the corrected records (one buffer every
+    shard exports into and imports from).  Against the unsharded context on
+    the same steps: the rate, and the largest position difference."""
+    import torch
+
+    from paper_0909_0879_gb300 import _lib, shard
+
+    n, P = args.n, args.shards
+    m, x, v = ics.king(n, W0, 1003)
+    perm = _lib.spatial_order(x, 256)
+    m, x, v = m[perm], x[perm], v[perm]
+    kw = dict(eps=EPS, precision=args.precision, block_steps=False, lev_shared=LEV_SHARED)
+    out = {"metric": f"G pair-interactions/s (acc+jerk, N={n}, i-split over {P} shards on one "
+                     f"GPU)", "unit": UNIT, "workload": workload_name(n), "shards": P,
+           "results": {}}
+    states = {}
+    for name, mk in (("unsharded", lambda: _lib.NBody(m, x, v, **kw)),
+                     (f"shards{P}", lambda: shard.ShardGroup(m, x, v, P, **kw))):
+        with mk() as g:
+            for _ in range(args.warmup):
+                g.step()
+            torch.cuda.synchronize()
+            e0, e1 = _events(torch)
+            t0 = time.perf_counter()
+            e0.record()
+            for _ in range(args.steps):
+                g.step()
+            e1.record()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            ms = e0.elapsed_time(e1)
+            states[name] = g.get_state(want=("x",))["x"]
+        out["results"][name] = {"value": args.steps * n * n / ms / 1e6, "ms_per_step":
+                                ms / args.steps, "wall_s": wall}
+    out["max_abs_dx_vs_unsharded"] = float(np.abs(states[f"shards{P}"] -
+                                                  states["unsharded"]).max())
+    out["note"] = ("shards run one after another on one GPU (the exchange is a shared buffer); "
+                   "on P GPUs each shard's force work is 1/P of the step")
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload != "king1m" and args.impl == "ours":
         return {"shared1024": run_shared1024, "block65536": run_block65536,
                 "batched": run_batched, "adjoint": run_adjoint,
-                "nsweep": run_nsweep, "symplectic": run_symplectic}[args.workload](args)
+                "nsweep": run_nsweep, "symplectic": run_symplectic,
+                "isplit": run_isplit}[args.workload](args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -447,6 +447,41 @@ nb_status nb_lf_backward(int64_t n, const float *d_m, const float *d_ckpt,
                          float *d_lm, float *d_work, void *stream);
 
 /* ------------------------------------------------------------------------
+ * i-split shards (the paper's two-GPU version of its code, Sec. 4, splits
+ * the particles whose forces are computed among the GPUs; every GPU keeps
+ * all particles as sources).  A context becomes shard `rank` of `nranks`
+ * (<= 64): it owns particles [bounds[rank], bounds[rank+1]) of a contiguous
+ * partition (bounds[0] = 0 <= ... <= bounds[nranks] = n, nranks + 1 host
+ * entries), keeps the whole state, and in the host-driven block step
+ *   nb_next_block  finds the whole active list and every rank's slice of
+ *                  it (ascending indices, so the slices are consecutive);
+ *   nb_predict     predicts every particle;
+ *   nb_force_jerk[_dev] (index list NULL) evaluates the own slice only
+ *                  (outputs, when given, hold the slice's rows);
+ *   nb_correct     corrects the own slice only;
+ *   nb_shard_export writes the slice's corrected records (count through
+ *                  *count) to d_rec, device memory of NB_SHARD_RECORD_DOUBLES
+ *                  doubles each: x, v, a, jerk (3 each), then the bit
+ *                  patterns of t_tick (int64) and lev (as an int64);
+ *   (the caller concatenates all ranks' records in rank order, e.g. by an
+ *    all-gather, or by letting every shard export at its slice's offset of
+ *    one buffer when all shards live on one device)
+ *   nb_shard_import takes that concatenation (n_rec = the block's active
+ *                  count, list order) and stores the other ranks' records.
+ * After the import every shard holds the same state.  nranks == 1 undoes
+ * the sharding.  Call between block steps (NB_ERR_STATE otherwise); shards
+ * run host-driven steps only (nb_run_blocks and nb_symplectic return
+ * NB_ERR_STATE), and nb_next_block returns NB_ERR_STATE until the last
+ * block's import is done.  nb_shard_offsets gives the nranks + 1 slice
+ * offsets of the block last found by nb_next_block (host array; for an
+ * unsharded context 0 and the active count). */
+#define NB_SHARD_RECORD_DOUBLES 14
+nb_status nb_shard_set(nb_ctx *ctx, int32_t nranks, int32_t rank, const int64_t *bounds);
+nb_status nb_shard_offsets(nb_ctx *ctx, int64_t *offsets);
+nb_status nb_shard_export(nb_ctx *ctx, double *d_rec, int64_t *count);
+nb_status nb_shard_import(nb_ctx *ctx, const double *d_rec, int64_t n_rec);
+
+/* ------------------------------------------------------------------------
  * Allocation-free force + jerk.  The paper has no counterpart: this entry
  * point exists for callers that cannot let the library allocate device
  * memory -- programs whose device memory all belongs to another allocator

@@ -18,6 +18,7 @@ NB_OK, NB_ERR_INVALID_ARG, NB_ERR_STATE, NB_ERR_CUDA = 0, 1, 2, 3
 NB_ERR_OOM, NB_ERR_NUMERIC, NB_ERR_TIMEOUT, NB_ERR_DEVICE = 4, 5, 6, 7
 NB_FP32, NB_DS = 0, 1
 TICKS_LOG2 = 20
+SHARD_RECORD_DOUBLES = 14  # NB_SHARD_RECORD_DOUBLES
 
 
 def eps_masks(eps: float) -> int:
@@ -115,6 +116,10 @@ SIGNATURES = [
                                 C.c_float, _i32, _vp, _vp]),
     ("nb_lf_backward", C.c_int, [_i64, _vp, _vp, _i64, C.c_float, C.c_float, C.c_float, _i32,
                                  _vp, _vp, _vp, _vp, _vp]),
+    ("nb_shard_set", C.c_int, [_vp, _i32, _i32, _vp]),
+    ("nb_shard_offsets", C.c_int, [_vp, _vp]),
+    ("nb_shard_export", C.c_int, [_vp, _vp, _P(_i64)]),
+    ("nb_shard_import", C.c_int, [_vp, _vp, _i64]),
     ("nb_force_jerk_noalloc", C.c_int, [_i64, _vp, _vp, _vp, _vp, _i64, _d, _d, _i32, _vp,
                                          _vp, _vp]),
     ("nb_status_string", C.c_char_p, [C.c_int]),
@@ -450,6 +455,35 @@ class NBody:
         _check(self._L.nb_set_force_table(self._h, k, mins.ctypes.data if k else None,
                                           vars_.ctypes.data if k else None,
                                           grids.ctypes.data if k else None))
+
+    # -- i-split shards (see nb_shard_set in include/nbody.h)
+    def shard_set(self, nranks: int, rank: int, bounds=None):
+        """Make this context shard `rank` of `nranks` owning particles
+        [bounds[rank], bounds[rank + 1]) (nranks == 1: unsharded)."""
+        self._shards = int(nranks)
+        if nranks == 1:
+            _check(self._L.nb_shard_set(self._h, 1, 0, None))
+            return
+        b = np.ascontiguousarray(bounds, dtype=np.int64)
+        _check(self._L.nb_shard_set(self._h, int(nranks), int(rank), b.ctypes.data))
+
+    def shard_offsets(self) -> np.ndarray:
+        """Offsets of every rank's slice in the current block's active list
+        (nranks + 1 entries)."""
+        out = np.zeros(getattr(self, "_shards", 1) + 1, dtype=np.int64)
+        _check(self._L.nb_shard_offsets(self._h, out.ctypes.data))
+        return out
+
+    def shard_export(self, d_rec) -> int:
+        """Corrected records of the own slice into device memory d_rec
+        (rows of SHARD_RECORD_DOUBLES doubles); returns the row count."""
+        cnt = C.c_int64()
+        _check(self._L.nb_shard_export(self._h, _ptr(d_rec), C.byref(cnt)))
+        return cnt.value
+
+    def shard_import(self, d_rec, n_rec: int):
+        """The whole active list's records (list order) from device memory."""
+        _check(self._L.nb_shard_import(self._h, _ptr(d_rec), int(n_rec)))
 
     def inject(self, kind: int):
         _check(self._L.nb_debug_inject(self._h, int(kind)))

@@ -228,6 +228,17 @@ struct nb_ctx {
   // no longer belong to them until nb_set_state
   bool sym_moved = false;
   ExtField ext;  // external Galactic field (symplectic integrators, energy)
+  // i-split shard (nb_shard_set): this context owns particles
+  // [sh.b[sh_rank], sh.b[sh_rank + 1]) of sh.p shards; own_lo..own_hi is its
+  // slice of the current block's active list (the whole list unsharded)
+  ShardBounds sh{1, {0}};
+  int sh_rank = 0;
+  int64_t *d_sh_off = nullptr;  // device: sh.p + 1 slice offsets
+  int64_t *h_sh_off = nullptr;  // pinned mirror
+  int64_t own_lo = 0, own_hi = 0;
+  bool sh_corrected = false;    // own slice corrected, other shards' records not yet imported
+  bool sh_off_valid = false;    // h_sh_off holds the last block's offsets
+  int64_t sh_nact = 0;          // active count of that block
   std::vector<void *> allocs;
 };
 
@@ -453,6 +464,7 @@ void nb_destroy(nb_ctx *c) {
     if (p) cudaFree(p);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_energy) cudaFreeHost(c->h_energy);
+  if (c->h_sh_off) cudaFreeHost(c->h_sh_off);
   if (c->ev) cudaEventDestroy(c->ev);
   if (c->blk_graph) cudaGraphExecDestroy(c->blk_graph);
   if (c->fus_graph) cudaGraphExecDestroy(c->fus_graph);
@@ -597,13 +609,24 @@ nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
   Range r("nb_next_block");
   nb_status s = check_hermite(c);
   if (s != NB_OK) return s;
+  if (c->sh_corrected)
+    return fail(NB_ERR_STATE, "shard: nb_shard_import of the last block's records comes first");
   int nl = 0;
   NB_CUDA(launch_next_block(c->n, c->t_tick, c->lev, c->act, c->blk, c->scal, c->stream, &nl));
   c->launches += nl;
+  if (c->sh.p > 1) {
+    NB_CUDA(launch_shard_offsets(c->act, c->scal, c->sh, c->d_sh_off, c->stream));
+    NB_CUDA(cudaMemcpyAsync(c->h_sh_off, c->d_sh_off, (c->sh.p + 1) * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, c->stream));
+    c->launches += 1;
+  }
   s = sync_ctx(c);
   if (s != NB_OK) return s;
   c->t_block = c->h_scal[kCtlTnext];
   c->n_act = c->h_scal[kCtlNact];
+  c->sh_off_valid = true;
+  c->own_lo = c->sh.p > 1 ? c->h_sh_off[c->sh_rank] : 0;
+  c->own_hi = c->sh.p > 1 ? c->h_sh_off[c->sh_rank + 1] : c->n_act;
   c->have_block = true;
   c->fresh = false;
   c->force_done = false;
@@ -639,13 +662,15 @@ nb_status nb_force_jerk_dev(nb_ctx *c, const int32_t *d_idx, int64_t n_idx, doub
                   (long long)c->n_act);
     if (c->t_pred != c->t_block)
       return fail(NB_ERR_STATE, "prediction time differs from the block time");
-    s = queue_force(c, c->act, c->n_act, c->a1, c->j1);
+    // a shard evaluates its own slice of the active list
+    const int64_t lo = c->own_lo, cnt = c->own_hi - c->own_lo;
+    s = queue_force(c, c->act + lo, cnt, c->a1 + 3 * lo, c->j1 + 3 * lo);
     if (s != NB_OK) return s;
-    if (d_acc)
-      NB_CUDA(cudaMemcpyAsync(d_acc, c->a1, 3 * c->n_act * sizeof(double),
+    if (d_acc && cnt)
+      NB_CUDA(cudaMemcpyAsync(d_acc, c->a1 + 3 * lo, 3 * cnt * sizeof(double),
                               cudaMemcpyDeviceToDevice, c->stream));
-    if (d_jerk)
-      NB_CUDA(cudaMemcpyAsync(d_jerk, c->j1, 3 * c->n_act * sizeof(double),
+    if (d_jerk && cnt)
+      NB_CUDA(cudaMemcpyAsync(d_jerk, c->j1 + 3 * lo, 3 * cnt * sizeof(double),
                               cudaMemcpyDeviceToDevice, c->stream));
     c->force_done = true;
     return NB_OK;
@@ -665,9 +690,9 @@ nb_status nb_force_jerk(nb_ctx *c, const int32_t *idx, int64_t n_idx, double *ac
   if (idx == nullptr) {
     s = nb_force_jerk_dev(c, nullptr, n_idx, nullptr, nullptr);
     if (s != NB_OK) return s;
-    src_a = c->a1;
-    src_j = c->j1;
-    cnt = c->n_act;
+    src_a = c->a1 + 3 * c->own_lo;
+    src_j = c->j1 + 3 * c->own_lo;
+    cnt = c->own_hi - c->own_lo;
   } else {
     if (n_idx < 0) return fail(NB_ERR_INVALID_ARG, "negative n_idx");
     for (int64_t k = 0; k < n_idx; ++k)
@@ -730,12 +755,18 @@ nb_status nb_correct(nb_ctx *c, double t) {
   if (!c->have_block || !c->force_done || tick != c->t_block)
     return fail(NB_ERR_STATE, "nb_correct needs nb_next_block, nb_predict and nb_force_jerk "
                               "of the active list at the same time first");
-  NB_CUDA(launch_correct(c->n_act, c->act, c->t_block, c->x, c->v, c->a, c->jk, c->t_tick,
-                         c->lev, c->a1, c->j1, c->cfg.eta, c->cfg.lev_min, c->cfg.lev_max,
-                         c->cfg.block_steps, c->clamped, c->ext, c->stream));
+  const int64_t lo = c->own_lo;
+  NB_CUDA(launch_correct(c->own_hi - lo, c->act + lo, c->t_block, c->x, c->v, c->a, c->jk,
+                         c->t_tick, c->lev, c->a1 + 3 * lo, c->j1 + 3 * lo, c->cfg.eta,
+                         c->cfg.lev_min, c->cfg.lev_max, c->cfg.block_steps, c->clamped,
+                         c->ext, c->stream));
   c->launches += 1;
   c->force_done = false;
   c->have_block = false;
+  if (c->sh.p > 1) {
+    c->sh_corrected = true;
+    c->sh_nact = c->n_act;
+  }
   return NB_OK;
 }
 
@@ -1181,6 +1212,7 @@ extern "C" nb_status nb_symplectic(nb_ctx *c, int32_t order, double dt, int64_t 
   Range r("nb_symplectic");
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
+  if (c->sh.p > 1) return fail(NB_ERR_STATE, "the symplectic integrators run unsharded contexts only");
   double w[7];
   const int S = symplectic_stages(order, w);
   if (S == 0) return fail(NB_ERR_INVALID_ARG, "symplectic order %d is not 2 or 6", order);
@@ -1257,6 +1289,8 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
   Range r("nb_run_blocks");
   nb_status s = check_hermite(c);
   if (s != NB_OK) return s;
+  if (c->sh.p > 1)
+    return fail(NB_ERR_STATE, "device-resident block steps run unsharded contexts only");
   bool ok;
   const int64_t tend = tick_of(t_end, &ok);
   if (!ok) return fail(NB_ERR_INVALID_ARG, "t_end %.17g is not a non-negative multiple of 2^-20",
@@ -1420,6 +1454,8 @@ nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double
   c->t_pred = -1;
   c->sym_moved = false;
   c->fresh = false;
+  c->sh_corrected = false;
+  c->sh_off_valid = false;
   return sync_ctx(c);
 }
 
@@ -1543,6 +1579,85 @@ nb_status nb_debug_inject(nb_ctx *c, int32_t kind) {
     return NB_OK;
   }
   return fail(NB_ERR_INVALID_ARG, "unknown injection kind %d", kind);
+}
+
+nb_status nb_shard_set(nb_ctx *c, int32_t nranks, int32_t rank, const int64_t *bounds) {
+  nb_status s = check_hermite(c);
+  if (s != NB_OK) return s;
+  if (nranks < 1 || nranks > kMaxShards || rank < 0 || rank >= nranks)
+    return fail(NB_ERR_INVALID_ARG, "need 1 <= nranks <= %d and 0 <= rank < nranks", kMaxShards);
+  if (nranks > 1 && !bounds) return fail(NB_ERR_INVALID_ARG, "null shard bounds");
+  if (nranks > 1) {
+    if (bounds[0] != 0 || bounds[nranks] != c->n)
+      return fail(NB_ERR_INVALID_ARG, "shard bounds must run from 0 to n");
+    for (int r = 0; r < nranks; ++r)
+      if (bounds[r + 1] < bounds[r])
+        return fail(NB_ERR_INVALID_ARG, "shard bounds must not decrease");
+  }
+  if (c->have_block || c->sh_corrected)
+    return fail(NB_ERR_STATE, "change the sharding between block steps only");
+  if (nranks > 1 && !c->d_sh_off) {
+    s = dev_alloc_t(c, &c->d_sh_off, kMaxShards + 1);
+    if (s != NB_OK) return s;
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_sh_off),
+                       (kMaxShards + 1) * sizeof(int64_t)) != cudaSuccess) {
+      c->h_sh_off = nullptr;
+      return fail(NB_ERR_CUDA, "pinned host buffer for the shard offsets");
+    }
+  }
+  c->sh.p = nranks;
+  c->sh_rank = nranks > 1 ? rank : 0;
+  for (int r = 0; r <= kMaxShards; ++r) c->sh.b[r] = 0;
+  if (nranks > 1)
+    for (int r = 0; r <= nranks; ++r) c->sh.b[r] = bounds[r];
+  c->sh_corrected = false;
+  c->sh_off_valid = false;
+  return NB_OK;
+}
+
+nb_status nb_shard_offsets(nb_ctx *c, int64_t *offsets) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (!offsets) return fail(NB_ERR_INVALID_ARG, "null output");
+  if (!c->sh_off_valid)
+    return fail(NB_ERR_STATE, "no block yet: call nb_next_block first");
+  if (c->sh.p == 1) {
+    offsets[0] = 0;
+    offsets[1] = c->n_act;
+    return NB_OK;
+  }
+  for (int r = 0; r <= c->sh.p; ++r) offsets[r] = c->h_sh_off[r];
+  return NB_OK;
+}
+
+nb_status nb_shard_export(nb_ctx *c, double *d_rec, int64_t *count) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (c->sh.p == 1 || !c->sh_corrected)
+    return fail(NB_ERR_STATE, "nb_shard_export follows nb_correct on a shard");
+  const int64_t cnt = c->own_hi - c->own_lo;
+  if (cnt > 0 && !d_rec) return fail(NB_ERR_INVALID_ARG, "null record buffer");
+  NB_CUDA(launch_shard_export(c->own_lo, c->own_hi, c->act, c->x, c->v, c->a, c->jk, c->t_tick,
+                              c->lev, d_rec, c->stream));
+  if (cnt > 0) c->launches += 1;
+  if (count) *count = cnt;
+  return NB_OK;
+}
+
+nb_status nb_shard_import(nb_ctx *c, const double *d_rec, int64_t n_rec) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (c->sh.p == 1 || !c->sh_corrected)
+    return fail(NB_ERR_STATE, "nb_shard_import follows nb_correct on a shard");
+  if (n_rec != c->sh_nact)
+    return fail(NB_ERR_INVALID_ARG, "%lld records for an active list of %lld",
+                (long long)n_rec, (long long)c->sh_nact);
+  if (n_rec > 0 && !d_rec) return fail(NB_ERR_INVALID_ARG, "null record buffer");
+  NB_CUDA(launch_shard_import(n_rec, c->own_lo, c->own_hi, c->act, d_rec, c->x, c->v, c->a,
+                              c->jk, c->t_tick, c->lev, c->stream));
+  if (n_rec > 0) c->launches += 1;
+  c->sh_corrected = false;
+  return NB_OK;
 }
 
 }  // extern "C"

@@ -259,6 +259,28 @@ struct EndArgs {
 cudaError_t launch_block_end(const EndArgs &E, int grid, cudaStream_t s);
 constexpr int kEndThreads = 256;
 
+// --- i-split shards (nb_shard.cu) ---
+constexpr int kMaxShards = 64;
+constexpr int kShardRecDoubles = 14;  // x, v, a, jerk (3 each), t_tick, lev (bit copies)
+// Contiguous index ranges [b[r], b[r+1]) of the p shards.
+struct ShardBounds {
+  int p;
+  int64_t b[kMaxShards + 1];
+};
+// off[r] (r = 0..p): first entry of the active list (ctl[kCtlNact] entries,
+// ascending) at or above b[r].
+cudaError_t launch_shard_offsets(const int32_t *act, const int64_t *ctl, const ShardBounds &B,
+                                 int64_t *off, cudaStream_t s);
+// rec[k - lo] = record of particle act[k] for k in [lo, hi).
+cudaError_t launch_shard_export(int64_t lo, int64_t hi, const int32_t *act, const double *x,
+                                const double *v, const double *a, const double *jk,
+                                const int64_t *t_tick, const int32_t *lev, double *rec,
+                                cudaStream_t s);
+// State of particle act[k] = rec[k] for k in [0, n_act) outside [lo, hi).
+cudaError_t launch_shard_import(int64_t n_act, int64_t lo, int64_t hi, const int32_t *act,
+                                const double *rec, double *x, double *v, double *a, double *jk,
+                                int64_t *t_tick, int32_t *lev, cudaStream_t s);
+
 // --- Fixed-step symplectic integration (nb_symplectic.cu) ---
 // Stage weights of the scheme of the given order into w (at most 7);
 // returns the stage count (1 for order 2, 7 for order 6, 0 otherwise).
