@@ -67,6 +67,55 @@ __device__ __forceinline__ void bpredict(const double *x, const double *v, const
   }
 }
 
+// The batched kernel keeps its predictor and corrector on the FP64 pipe:
+// there the FP32 pipe carries the pair sums of every cluster on the same
+// SM, and FP64 work runs beside it, while conversions and split-precision
+// arithmetic would compete with it (measured 5-13 % slower).
+//
+// Coefficients of the Hermite corrector for one shared step dt (a power of
+// two: every coefficient is exact).
+struct BHermCoef {
+  double dt, h2, h3;          // dt, dt/2, dt/3 (predictor)
+  double s_da, s_j0, s_jn;    // snap = s_da da + s_j0 j0 + s_jn jn
+  double c_da, c_j;           // crackle = c_da da + c_j (j0 + jn)
+  double x_s, x_c, v_s, v_c;  // dt^4/24, dt^5/120, dt^3/6, dt^4/24
+};
+
+__device__ __forceinline__ BHermCoef bherm_coef(double dt, double idt2, double idt3) {
+  BHermCoef K;
+  const double dt2 = dt * dt, dt3 = dt2 * dt;
+  const double idt = dt * idt2;  // 1/dt
+  K.dt = dt;
+  K.h2 = 0.5 * dt;
+  K.h3 = dt * (1.0 / 3.0);
+  K.s_da = -6.0 * idt2;
+  K.s_j0 = -4.0 * idt;
+  K.s_jn = -2.0 * idt;
+  K.c_da = 12.0 * idt3;
+  K.c_j = 6.0 * idt2;
+  K.x_s = dt2 * dt2 * (1.0 / 24.0);
+  K.x_c = dt3 * dt2 * (1.0 / 120.0);
+  K.v_s = dt3 * (1.0 / 6.0);
+  K.v_c = dt2 * dt2 * (1.0 / 24.0);
+  return K;
+}
+
+// One component of the Hermite-4 step in FP64: the predictor, snap =
+// (-6 da - dt (4 j0 + 2 jn)) / dt^2 and crackle = (12 da + 6 dt (j0 + jn)) /
+// dt^3 with da = a0 - an, x1 = x_p + dt^4 snap / 24 + dt^5 crackle / 120,
+// v1 = v_p + dt^3 snap / 6 + dt^4 crackle / 24.
+__device__ __forceinline__ void bherm_component(const BHermCoef &K, double x0, double v0,
+                                                double a0, double j0, double an, double jn,
+                                                double &x1, double &v1) {
+  const double xp = x0 + K.dt * (v0 + K.h2 * (a0 + K.h3 * j0));
+  const double vp = v0 + K.dt * (a0 + K.h2 * j0);
+  const double da = a0 - an;
+  const double snap = K.s_da * da + (K.s_j0 * j0 + K.s_jn * jn);
+  const double crackle = K.c_da * da + K.c_j * (j0 + jn);
+  x1 = xp + (K.x_s * snap + K.x_c * crackle);
+  v1 = vp + (K.v_s * snap + K.v_c * crackle);
+}
+
 template <int PREC, int IPT, int NT, int MASK, int PACK>
 __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs B) {
   using V = typename std::conditional<PACK != 0, float2, float>::type;
@@ -101,8 +150,7 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
     const int nsteps = B.init_only ? 1 : B.nsteps;
     // corrector coefficients of the shared step (dt a power of two: exact;
     // the host gives 1/dt^2, 1/dt^3)
-    const dev::HermCoef K =
-        dev::herm_coef(dt, 0.5 * dt, dt * (1.0 / 3.0), dt * dt, dt * dt * dt, B.idt2, B.idt3);
+    const BHermCoef K = bherm_coef(dt, B.idt2, B.idt3);
 
     for (int step = 0; step < nsteps; ++step) {
       for (int p = tid; p < n; p += NT) {
@@ -251,9 +299,9 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
           } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-              double x1, v1, a2, a3;
-              dev::herm_component(K, B.x[3 * gi + k], B.v[3 * gi + k], B.a[3 * gi + k],
-                                  B.jk[3 * gi + k], B.G * o[k], B.G * o[3 + k], x1, v1, a2, a3);
+              double x1, v1;
+              bherm_component(K, B.x[3 * gi + k], B.v[3 * gi + k], B.a[3 * gi + k],
+                              B.jk[3 * gi + k], B.G * o[k], B.G * o[3 + k], x1, v1);
               B.x[3 * gi + k] = x1;
               B.v[3 * gi + k] = v1;
               B.a[3 * gi + k] = B.G * o[k];

@@ -4,10 +4,11 @@
 // launch instead of a dozen:
 //
 //   block_begin  scheduling (next block time, ordered active list) and the
-//                FP64 predictor of every particle, with the j-tile frames;
+//                predictor of every particle's j-records (split precision on
+//                the FP32 pipe), with the j-tile frames;
 //   force        the force + jerk kernels of nb_force.cu, one launch per
 //                active-count bucket (the others return at once);
-//   block_end    the fix-up of split i-blocks and the FP64 corrector.
+//   block_end    the fix-up of split i-blocks and the corrector.
 //
 // Scheduling without a pass over the particles.  The integrator keeps every
 // particle's time t_i a multiple of its step dt_i = 2^-lev_i and its next
@@ -23,9 +24,10 @@
 // the general scheduler instead).
 //
 // The ordered compaction is a single pass: CTAs take tickets in the order
-// they start, publish their tile's active count, and read the counts before
-// them with a decoupled look-back (bounded waits; a CTA only waits on CTAs
-// that started earlier, so every wait ends).
+// they start, publish their tile's active count at once, predict their
+// tile, then read the counts before them with a decoupled look-back over
+// windows of 256 tiles (bounded waits; a CTA only waits on CTAs that
+// started earlier and published before predicting, so every wait ends).
 #include "nb_device.cuh"
 
 namespace nbi {
@@ -55,33 +57,52 @@ __device__ __forceinline__ uint64_t lb_word(uint64_t epoch, uint64_t flag, uint6
   return (epoch << 40) | (flag << kValBits) | (val & kValMask);
 }
 
-// Exclusive prefix of the active counts of the tiles before `vid`: one warp
-// reads 32 predecessors' words at a time (waiting, bounded, until all 32
-// are published in this epoch), adds them up to the nearest inclusive
-// prefix and stops there, or moves 32 tiles further back.  Returns false if
-// a wait ran out.  Warp-uniform.
-__device__ __forceinline__ bool look_back(const unsigned long long *status, int64_t vid,
-                                          uint64_t epoch, uint32_t limit, int lane,
-                                          int64_t *excl_out) {
+// Exclusive prefix of the active counts of the tiles before `vid`, by the
+// whole CTA: each thread reads one predecessor's word of the current window
+// of kJT tiles (waiting, bounded, until it is published in this epoch); the
+// window's counts are added up to the nearest inclusive prefix, where the
+// scan stops, or the next window further back is read.  A window covers
+// 256 tiles, so up to N = 65,536 one round of reads suffices.  Returns false
+// (on every thread) if a wait ran out.  Called by all threads of the CTA.
+__device__ __forceinline__ bool look_back_cta(const unsigned long long *status, int64_t vid,
+                                              uint64_t epoch, uint32_t limit,
+                                              int64_t *excl_out) {
+  __shared__ int64_t s_sum[kJT / 32];
+  __shared__ int s_near[kJT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int64_t excl = 0;
-  for (int64_t top = vid - 1; top >= 0; top -= 32) {
-    const int64_t j = top - lane;
+  for (int64_t top = vid - 1; top >= 0; top -= kJT) {
+    const int64_t j = top - tid;  // thread 0 reads the nearest predecessor
     uint64_t w = 0;
-    uint32_t it = 0;
-    for (;; ++it) {
-      if (j >= 0) w = ld_relaxed(status + j);
-      const bool ready = j < 0 || (w >> 40) == epoch;
-      if (__all_sync(0xffffffffu, ready)) break;
-      if (it >= limit) return false;
+    bool ready = true;
+    if (j >= 0) {
+      ready = false;
+      for (uint32_t it = 0; it < limit; ++it) {
+        w = ld_relaxed(status + j);
+        if ((w >> 40) == epoch) {
+          ready = true;
+          break;
+        }
+      }
     }
+    if (__syncthreads_or(!ready)) return false;
+    // nearest inclusive prefix of the window: the smallest such thread
     const bool pre = j >= 0 && ((w >> kValBits) & 3) == kFlagPre;
     const unsigned pm = __ballot_sync(0xffffffffu, pre);
-    const int last = pm ? __ffs(pm) - 1 : 31;  // nearest inclusive prefix
-    int64_t val = (j >= 0 && lane <= last) ? static_cast<int64_t>(w & kValMask) : 0;
+    if (lane == 0) s_near[wid] = pm ? wid * 32 + __ffs(pm) - 1 : kJT;
+    __syncthreads();
+    int near = kJT;
+#pragma unroll
+    for (int q = 0; q < kJT / 32; ++q) near = s_near[q] < near ? s_near[q] : near;
+    int64_t val = (j >= 0 && tid <= near) ? static_cast<int64_t>(w & kValMask) : 0;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
-    excl += val;
-    if (pm) break;
+    if (lane == 0) s_sum[wid] = val;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kJT / 32; ++q) excl += s_sum[q];
+    __syncthreads();  // s_sum and s_near are read before the next window
+    if (near < kJT) break;
   }
   *excl_out = excl;
   return true;
@@ -140,41 +161,39 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
   if (lane == 0) s_wcnt[wid] = __popc(bal);
   __syncthreads();
   const uint64_t epoch = static_cast<uint64_t>(blocks % kEpochMod) + 1;
-  if (wid == 0) {
-    // publish this tile's count, then look back while the other warps
-    // start on the predictor
-    int agg = 0;
-    for (int w = 0; w < kJT / 32; ++w) agg += s_wcnt[w];
-    if (lane == 0)
-      st_relaxed(B.status + vid,
-                 lb_word(epoch, vid == 0 ? kFlagPre : kFlagAgg, static_cast<uint64_t>(agg)));
-    int64_t excl = 0;
-    const bool ok = look_back(B.status, vid, epoch + B.lb_epoch_skew, B.lb_wait_limit, lane,
-                              &excl);
-    if (lane == 0) {
-      if (!ok)
-        atomicOr(reinterpret_cast<int *>(ctl + kCtlErr), kErrScanTimeout);
-      else if (vid > 0)
-        st_relaxed(B.status + vid,
-                   lb_word(epoch, kFlagPre, static_cast<uint64_t>(excl + agg)));
-      s_excl = excl;
-      s_agg = agg;
-      s_fail = ok ? 0 : 1;
-    }
-  }
+  int agg = 0;
+  for (int w = 0; w < kJT / 32; ++w) agg += s_wcnt[w];
+  // publish this tile's count at once, so that no later CTA waits for it
+  if (tid == 0)
+    st_relaxed(B.status + vid,
+               lb_word(epoch, vid == 0 ? kFlagPre : kFlagAgg, static_cast<uint64_t>(agg)));
 
-  // FP64 predictor of this tile's particles
+  // predictor of this tile's particles (split precision, FP32 pipe)
   float4 h = make_float4(0.f, 0.f, 0.f, 0.f), lo = h;
   if (real) {
-    const double dt = static_cast<double>(t_next - B.t_tick[i]) * kTick;
-    double xp[3], vp[3];
-    dev::predict_pos_vel(B.x, B.v, B.a, B.jk, i, dt, xp, vp);
-    h = dev::store_records(i, xp, vp, B.m[i], B.prec, B.jhi, B.jlo, B.jvel, &lo);
+    const float dt = static_cast<float>(t_next - B.t_tick[i]) * static_cast<float>(kTick);
+    float xh[3], xl[3], vp[3];
+    dev::predict_ds(B.x, B.v, B.a, B.jk, i, dt, xh, xl, vp);
+    h = dev::store_records_ds(i, xh, xl, vp, B.m[i], B.prec, B.jhi, B.jlo, B.jvel, &lo);
   }
   if (B.jrel)
     dev::tile_frame(vid, i, real, h, lo, B.jrel, B.tinfo);  // synchronises the CTA
   else
     __syncthreads();
+
+  // the predecessors' counts were published while this CTA predicted
+  int64_t excl = 0;
+  const bool ok = look_back_cta(B.status, vid, epoch + B.lb_epoch_skew, B.lb_wait_limit, &excl);
+  if (tid == 0) {
+    if (!ok)
+      atomicOr(reinterpret_cast<int *>(ctl + kCtlErr), kErrScanTimeout);
+    else if (vid > 0)
+      st_relaxed(B.status + vid, lb_word(epoch, kFlagPre, static_cast<uint64_t>(excl + agg)));
+    s_excl = excl;
+    s_agg = agg;
+    s_fail = ok ? 0 : 1;
+  }
+  __syncthreads();
   if (!s_fail && due) {
     int base = 0;
     for (int w = 0; w < wid; ++w) base += s_wcnt[w];

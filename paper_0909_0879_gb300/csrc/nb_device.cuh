@@ -225,6 +225,63 @@ __device__ __forceinline__ void ds_add_pair(float ah, float al, float bh, float 
   l = __fsub_rn(e, __fsub_rn(h, s));
 }
 
+// Particle i predicted by dt (ticks times 2^-20, exact in FP32), on the
+// FP32 pipe in split precision, for its j-records:
+//   x_p = x + dt v + dt^2 (a/2 + dt j/6),   v_p = v + dt a + dt^2 j/2.
+// x and v are split into FP32 pairs hi + lo (the FP64 subtraction of the
+// rounded high word is exact); dt v_hi is formed exactly as the FP32
+// product plus its FMA rounding error; the low words and the a and j terms,
+// smaller than dt v by about dt over the particle's dynamical time, are
+// summed in FP32; a two-sum adds the increment to the position pair.  The
+// position error is a few ulps of the a and j terms (~2^-24 |dt^2 a|),
+// far below the FP32 rounding of a pair difference; the velocity is
+// rounded to FP32 as the records store it.
+__device__ __forceinline__ void predict_ds(const double *__restrict__ x,
+                                           const double *__restrict__ v,
+                                           const double *__restrict__ a,
+                                           const double *__restrict__ jk, int64_t i, float dt,
+                                           float xh[3], float xl[3], float vp[3]) {
+  const float h2 = 0.5f * dt, h3 = dt * (1.0f / 3.0f);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double xc = x[3 * i + c], vc = v[3 * i + c];
+    const float x0 = d2f_rn(xc), x1 = d2f_rn(xc - f2d(x0));
+    const float v0 = d2f_rn(vc), v1 = d2f_rn(vc - f2d(v0));
+    const float ac = d2f_rn(a[3 * i + c]), jc = d2f_rn(jk[3 * i + c]);
+    const float p = dt * v0;
+    const float pe = fmaf(dt, v0, -p);  // dt v0 = p + pe exactly
+    const float q = fmaf(dt, v1, pe) + dt * (h2 * fmaf(h3, jc, ac));
+    float s, e;
+    two_sum(x0, p, s, e);
+    e = __fadd_rn(e, __fadd_rn(x1, q));
+    const float hh = __fadd_rn(s, e);
+    xh[c] = hh;
+    xl[c] = __fsub_rn(e, __fsub_rn(hh, s));
+    vp[c] = v0 + (v1 + dt * fmaf(h2, jc, ac));
+  }
+}
+
+// j-records of particle i from a split-precision prediction: high words and
+// mass, low words (DS only), FP32 velocity.  Returns the first and the low
+// words through *lo (zero in FP32).
+__device__ __forceinline__ float4 store_records_ds(int64_t i, const float xh[3],
+                                                   const float xl[3], const float vp[3],
+                                                   double m, int prec,
+                                                   float4 *__restrict__ jhi,
+                                                   float4 *__restrict__ jlo,
+                                                   float4 *__restrict__ jvel, float4 *lo) {
+  const float4 h = make_float4(xh[0], xh[1], xh[2], d2f_rn(m));
+  jhi[i] = h;
+  float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (prec) {
+    l = make_float4(xl[0], xl[1], xl[2], 0.f);
+    jlo[i] = l;
+  }
+  jvel[i] = make_float4(vp[0], vp[1], vp[2], 0.f);
+  *lo = l;
+  return h;
+}
+
 // The pair (h, l) times G in FP64.
 __device__ __forceinline__ double ds_to_double(float h, float l, double G) {
   return G * (f2d(h) + f2d(l));
@@ -287,30 +344,24 @@ __device__ __forceinline__ int level_from_dt(double dt, int lev_min, int lev_max
 
 // Level of the Aarseth step dt = sqrt(q), q = N / D >= 0, without forming
 // q or dt: floor(log2 q) = e_N - e_D - [f_N < f_D] exactly (N = f_N 2^e_N,
-// D = f_D 2^e_D, f in [0.5, 1)), and the largest 2^-lev <= dt has
-// lev = -floor(floor(log2 q) / 2).  This is the level level_from_dt gives
-// for the exact sqrt(N / D); special values follow it too (q = 0 or NaN:
-// lev_max and a clamp, q = inf: lev_min).
-__device__ __forceinline__ int level_from_ratio(double N, double D, int lev_min, int lev_max,
-                                                int *clamped) {
-  if (isnan(N) || isnan(D) || !(N > 0.0) || isinf(D)) {  // q = 0 or undefined
+// D = f_D 2^e_D, f in [1, 2)), and the largest 2^-lev <= dt has
+// lev = -floor(floor(log2 q) / 2).  N and D are FP32 (subnormals are flushed
+// to zero); special values: q = 0 or undefined, and an overflowed N, give
+// lev_max and a clamp; D = 0 (q = inf) gives lev_min.
+__device__ __forceinline__ int level_from_ratio_f(float N, float D, int lev_min, int lev_max,
+                                                  int *clamped) {
+  if (isnan(N) || isnan(D) || !(N > 0.f) || isinf(D)) {  // q = 0 or undefined
     *clamped = 1;
     return lev_max;
   }
-  if (isinf(N) || D == 0.0) return lev_min;  // q = inf
-  // exponents and mantissas from the bit patterns (frexp costs ~400 cycles
-  // of FP64 latency here); subnormal operands take frexp
-  const long long bN = __double_as_longlong(N), bD = __double_as_longlong(D);
-  const int xN = static_cast<int>((bN >> 52) & 0x7ff), xD = static_cast<int>((bD >> 52) & 0x7ff);
-  int F;
-  if (xN != 0 && xD != 0) {
-    const long long kMant = (1ll << 52) - 1;
-    F = xN - xD - ((bN & kMant) < (bD & kMant) ? 1 : 0);
-  } else {
-    int eN, eD;
-    const double fN = frexp(N, &eN), fD = frexp(D, &eD);
-    F = eN - eD - (fN < fD ? 1 : 0);
+  if (isinf(N)) {  // an FP32 overflow of the numerator: take the smallest step
+    *clamped = 1;
+    return lev_max;
   }
+  if (!(D > 0.f)) return lev_min;  // q = inf
+  const int bN = __float_as_int(N), bD = __float_as_int(D);
+  const int F = ((bN >> 23) & 0xff) - ((bD >> 23) & 0xff) -
+                ((bN & 0x7fffff) < (bD & 0x7fffff) ? 1 : 0);
   int lev = -(F >> 1);
   if (lev > lev_max) {
     *clamped = 1;
@@ -320,61 +371,75 @@ __device__ __forceinline__ int level_from_ratio(double N, double D, int lev_min,
   return lev;
 }
 
-// 2^k as a double, for |k| <= 1000, from its exponent bits (exact).
-__device__ __forceinline__ double pow2(int k) {
-  return __longlong_as_double(static_cast<long long>(1023 + k) << 52);
+// 2^k as a float, |k| <= 126 (exact).
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// |u| in FP32 without overflow or underflow of the squares: the components
+// are scaled by a power of two near 1 / max|u_c| first (exact).
+__device__ __forceinline__ float norm3f(const float u[3]) {
+  const float m = fmaxf(fabsf(u[0]), fmaxf(fabsf(u[1]), fabsf(u[2])));
+  if (isnan(u[0] + u[1] + u[2])) return u[0] + u[1] + u[2];
+  if (!(m > 0.f) || isinf(m)) return m;
+  int e = ((__float_as_int(m) >> 23) & 0xff) - 127;
+  e = e < -125 ? -125 : (e > 125 ? 125 : e);
+  const float sc = pow2f(-e);
+  const float x = u[0] * sc, y = u[1] * sc, z = u[2] * sc;
+  return sqrtf(fmaf(x, x, fmaf(y, y, z * z))) * pow2f(e);
 }
 
-// Coefficients of the Hermite corrector for one step dt, shared by the three
-// components (each FP64 instruction counts on this part: a scheduler
-// retires one FP64 warp instruction per ~68 cycles, whatever the number of
-// active lanes).  For a power-of-two dt every coefficient is exact.
-struct HermCoef {
-  double dt, h2, h3;            // dt, dt/2, dt/3 (predictor)
-  double s_da, s_j0, s_jn;      // snap = s_da da + s_j0 j0 + s_jn jn
-  double c_da, c_j;             // crackle = c_da da + c_j (j0 + jn)
-  double x_s, x_c, v_s, v_c;    // dt^4/24, dt^5/120, dt^3/6, dt^4/24
+// Coefficients of the Hermite corrector for one step dt on the FP32 pipe
+// (the FP64 pipe of this part retires one warp instruction per ~68 cycles
+// per scheduler).  dt is a power of two of ticks (2^-20 .. 2^0), so 1/dt is
+// exact and so is every coefficient.
+struct HermCoefF {
+  float dt;
+  float s_da, s_j0, s_jn;  // snap = s_da da + s_j0 j0 + s_jn jn
+  float c_da, c_j;         // crackle = c_da da + c_j (j0 + jn)
 };
 
-__device__ __forceinline__ HermCoef herm_coef(double dt, double h2, double h3, double dt2,
-                                              double dt3, double idt2, double idt3) {
-  HermCoef K;
-  const double idt = dt * idt2;  // 1/dt
+__device__ __forceinline__ HermCoefF herm_coef_f(float dt, float idt) {
+  HermCoefF K;
+  const float idt2 = idt * idt;
   K.dt = dt;
-  K.h2 = h2;
-  K.h3 = h3;
-  K.s_da = -6.0 * idt2;
-  K.s_j0 = -4.0 * idt;
-  K.s_jn = -2.0 * idt;
-  K.c_da = 12.0 * idt3;
-  K.c_j = 6.0 * idt2;
-  K.x_s = dt2 * dt2 * (1.0 / 24.0);
-  K.x_c = dt3 * dt2 * (1.0 / 120.0);
-  K.v_s = dt3 * (1.0 / 6.0);
-  K.v_c = dt2 * dt2 * (1.0 / 24.0);
+  K.s_da = -6.f * idt2;
+  K.s_j0 = -4.f * idt;
+  K.s_jn = -2.f * idt;
+  K.c_da = 12.f * idt2 * idt;
+  K.c_j = 6.f * idt2;
   return K;
 }
 
 // One component of the Hermite-4 step from (x0, v0, a0, j0) with the new
-// force (an, jn): the predictor (the expression of predict_pos_vel), the
-// second and third derivatives of a at the start of the step,
+// force (an, jn): the second and third derivatives of a at the start of the
+// step,
 //   snap = (-6 da - dt (4 j0 + 2 jn)) / dt^2,
 //   crackle = (12 da + 6 dt (j0 + jn)) / dt^3,   da = a0 - an,
-// the corrected x1 = x_p + dt^4 snap / 24 + dt^5 crackle / 120 and
-// v1 = v_p + dt^3 snap / 6 + dt^4 crackle / 24, and the derivatives at the
-// end of the step for the step criterion, a2 = snap + dt crackle, a3 = crackle.
-__device__ __forceinline__ void herm_component(const HermCoef &K, double x0, double v0,
-                                               double a0, double j0, double an, double jn,
-                                               double &x1, double &v1, double &a2,
-                                               double &a3) {
-  const double xp = x0 + K.dt * (v0 + K.h2 * (a0 + K.h3 * j0));
-  const double vp = v0 + K.dt * (a0 + K.h2 * j0);
-  const double da = a0 - an;
-  const double snap = K.s_da * da + (K.s_j0 * j0 + K.s_jn * jn);
-  const double crackle = K.c_da * da + K.c_j * (j0 + jn);
-  x1 = xp + (K.x_s * snap + K.x_c * crackle);
-  v1 = vp + (K.v_s * snap + K.v_c * crackle);
-  a2 = snap + crackle * K.dt;
+// the corrected
+//   x1 = x0 + dt (v0 + dt (a0/2 + dt (j0/6 + dt (snap/24 + dt crackle/120)))),
+//   v1 = v0 + dt (a0 + dt (j0/2 + dt (snap/6 + dt crackle/24))),
+// and the derivatives at the end of the step for the step criterion,
+// a2 = snap + dt crackle, a3 = crackle.  (This is the predictor's Taylor
+// polynomial plus the dt^4 and dt^5 terms.)  The terms of x0, v0, a0 and
+// the difference da are FP64, so that a smooth external field, which can
+// dominate a, keeps full precision; the terms of j0, snap and crackle,
+// smaller than the a0 term by about dt over the dynamical time, are
+// evaluated on the FP32 pipe (6 FP64 instructions per component instead
+// of 17: the FP64 pipe of this part retires one warp instruction per ~68
+// cycles per scheduler).
+__device__ __forceinline__ void herm_component_f(const HermCoefF &K, double dtd, double x0,
+                                                 double v0, double a0, float j0, double an,
+                                                 float jn, double &x1, double &v1, float &a2,
+                                                 float &a3) {
+  const float dt = K.dt;
+  const float da = d2f_rn(a0 - an);
+  const float snap = fmaf(K.s_da, da, fmaf(K.s_j0, j0, K.s_jn * jn));
+  const float crackle = fmaf(K.c_da, da, K.c_j * (j0 + jn));
+  const float qx =
+      dt * fmaf(dt, fmaf(dt, crackle * (1.f / 120.f), snap * (1.f / 24.f)), j0 * (1.f / 6.f));
+  const float qv = dt * fmaf(dt, fmaf(dt, crackle * (1.f / 24.f), snap * (1.f / 6.f)), 0.5f * j0);
+  x1 = fma(dtd, fma(dtd, fma(0.5, a0, f2d(qx)), v0), x0);
+  v1 = fma(dtd, a0 + f2d(qv), v0);
+  a2 = fmaf(crackle, dt, snap);
   a3 = crackle;
 }
 
@@ -530,26 +595,21 @@ __device__ __forceinline__ void correct_vals(
   double an3[3] = {an_pair[0], an_pair[1], an_pair[2]};
   double jn3[3] = {jn_pair[0], jn_pair[1], jn_pair[2]};
   if (ext && ext->on) ext_at_prediction(*ext, st, dt, h2, h3, an3, jn3);
-  const double dt2 = dt * dt, dt3 = dt2 * dt;
-  // A due particle's step is a power of two of ticks, so 1/dt^2 and 1/dt^3
-  // are powers of two, built exactly from the exponent (no division), and
-  // the products below equal the quotients bit for bit.
-  double idt2, idt3;
-  if (dtk > 0 && (dtk & (dtk - 1)) == 0) {
-    const int e = (63 - __clzll(dtk)) - kTicksLog2;  // dt = 2^e
-    idt2 = pow2(-2 * e);
-    idt3 = pow2(-3 * e);
-  } else {
-    idt2 = 1.0 / dt2;
-    idt3 = 1.0 / dt3;
-  }
-  const HermCoef K = herm_coef(dt, h2, h3, dt2, dt3, idt2, idt3);
-  double a2e[3], a3e[3];
+  // A due particle's step is a power of two of ticks, so 1/dt is a power
+  // of two, built exactly from the exponent (no division).
+  const float dtf = static_cast<float>(dtk) * static_cast<float>(kTick);
+  const float idt = (dtk > 0 && (dtk & (dtk - 1)) == 0)
+                        ? pow2f(kTicksLog2 - (63 - __clzll(dtk)))
+                        : 1.f / dtf;
+  const HermCoefF K = herm_coef_f(dtf, idt);
+  float anf[3], jnf[3], a2e[3], a3e[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     double x1, v1;
-    herm_component(K, st.x[c], st.v[c], st.a[c], st.j[c], an3[c], jn3[c], x1, v1, a2e[c],
-                   a3e[c]);
+    anf[c] = d2f_rn(an3[c]);
+    jnf[c] = d2f_rn(jn3[c]);
+    herm_component_f(K, dt, st.x[c], st.v[c], st.a[c], d2f_rn(st.j[c]), an3[c], jnf[c], x1,
+                     v1, a2e[c], a3e[c]);
     x[3 * i + c] = x1;
     v[3 * i + c] = v1;
     a[3 * i + c] = an3[c];
@@ -558,14 +618,13 @@ __device__ __forceinline__ void correct_vals(
   t_tick[i] = t_next;
   if (block_steps) {
     // Aarseth's criterion dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)
-    // as numerator and denominator; the level comes from their exponents
-    // (no FP64 divide or square root of the quotient: on this part each
-    // costs ~600 cycles of latency in a single warp)
-    const double na2 = dot3(an3), nj2 = dot3(jn3), n22 = dot3(a2e), n32 = dot3(a3e);
-    const double N = eta * (sqrt(na2 * n22) + nj2);
-    const double D = sqrt(nj2 * n32) + n22;
+    // in FP32, as numerator and denominator; the level comes from their
+    // exponents (it only has to place dt between powers of two)
+    const float na = norm3f(anf), nj = norm3f(jnf), n2 = norm3f(a2e), n3 = norm3f(a3e);
+    const float N = static_cast<float>(eta) * fmaf(na, n2, nj * nj);
+    const float D = fmaf(nj, n3, n2 * n2);
     int cl = 0;
-    const int want = level_from_ratio(N, D, lev_min, lev_max, &cl);
+    const int want = level_from_ratio_f(N, D, lev_min, lev_max, &cl);
     if (cl) atomicAdd(n_clamped, 1ull);
     const int old = st.lev;
     int nl = old;

@@ -1,5 +1,5 @@
-// O(N) kernels of the Hermite-4 block-step integrator, in FP64 on the GPU:
-// predictor (and the j-records it writes for the force kernels), corrector
+// O(N) kernels of the Hermite-4 block-step integrator on the GPU: predictor
+// of the j-records (split precision on the FP32 pipe), FP64 corrector
 // with the Aarseth step criterion and power-of-two block quantisation,
 // block scheduling (minimum next time and ordered compaction of the active
 // list), and the FP64 energy diagnostic.
@@ -30,11 +30,11 @@ __global__ void predict_kernel(int64_t n, int64_t t_next, const double *__restri
   }
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const double dt = static_cast<double>(t_next - t_tick[i]) * kTick;
-    double xp[3], vp[3];
-    dev::predict_pos_vel(x, v, a, jk, i, dt, xp, vp);
+    const float dt = static_cast<float>(t_next - t_tick[i]) * static_cast<float>(kTick);
+    float xh[3], xl[3], vp[3];
+    dev::predict_ds(x, v, a, jk, i, dt, xh, xl, vp);
     float4 lo;
-    dev::store_records(i, xp, vp, m[i], prec, jhi, jlo, jvel, &lo);
+    dev::store_records_ds(i, xh, xl, vp, m[i], prec, jhi, jlo, jvel, &lo);
   }
 }
 
