@@ -529,9 +529,25 @@ def run_shared1024(args):
             E1 = s.energy()[2]
         P = (m[:, None] * st["v"]).sum(0)
         L = (m[:, None] * np.cross(st["x"], st["v"])).sum(0)
+        # the same 256 steps device-resident (CUDA-graph replays of 32 steps,
+        # no host synchronisation per step); bit for bit the same states
+        with _lib.NBody(m, x, v, eps=eps, precision=prec, block_steps=False, lev_shared=lev) as s:
+            e2, e3 = _events(torch)
+            e2.record()
+            nblk, _ = s.run_blocks(1.0)
+            e3.record()
+            torch.cuda.synchronize()
+            ms_dev = e2.elapsed_time(e3)
+            same = bool(np.array_equal(s.get_state(want=("x",))["x"], st["x"]))
         out["results"][prec] = {"value": steps * n * n / ms / 1e6, "ms": ms,
                                 "dE_over_E": abs(E1 - E0) / abs(E0),
-                                "dP": float(np.abs(P).max()), "dL": float(np.abs(L - L0).max())}
+                                "dP": float(np.abs(P).max()), "dL": float(np.abs(L - L0).max()),
+                                "device_resident": {"value": nblk * n * n / ms_dev / 1e6,
+                                                    "ms": ms_dev, "steps": nblk,
+                                                    "same_state_as_host_loop": same},
+                                "note": "value/ms: host-driven nb_step loop (one host "
+                                        "synchronisation per step); device_resident: "
+                                        "nb_run_blocks"}
     if not args.no_cpu:
         from oracle import oracle as O
 
