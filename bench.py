@@ -60,8 +60,11 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--e2e-steps", type=int, default=0,
                    help="steps of the end-to-end leg (0 = as many as --steps)")
-    p.add_argument("--variant", type=int, default=-1)
+    p.add_argument("--variant", type=int, default=-1,
+                   help="king1m: force shape; batched: batched shape (skips the tuner)")
     p.add_argument("--grid", type=int, default=0)
+    p.add_argument("--batched-steps", type=int, default=1000,
+                   help="batched: shared steps per timed run")
     p.add_argument("--workload", default="king1m",
                    choices=["king1m", "shared1024", "block65536", "batched", "adjoint",
                             "nsweep", "symplectic", "isplit"],
@@ -617,9 +620,10 @@ def run_block65536(args):
         with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3, lev_max=20) as s:
             E0 = s.energy()[2]
             dev_res = None
-        if args.block_steps == 0:
+        if True:
             # device-resident block steps (CUDA-graph replays): the fused
             # form and the general scheduler, each from the initial state
+            # (at most --block-steps of them when given)
             dev_res = {}
             for mode in ("auto", "general"):
                 with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3,
@@ -630,7 +634,7 @@ def run_block65536(args):
                     l0 = s.launch_count()
                     t0 = time.perf_counter()
                     e0.record()
-                    nblk, _ = s.run_blocks(t_end * 2.0**-20)
+                    nblk, _ = s.run_blocks(t_end * 2.0**-20, max(0, args.block_steps))
                     e1.record()
                     torch.cuda.synchronize()
                     wall_dev = time.perf_counter() - t0
@@ -641,7 +645,8 @@ def run_block65536(args):
                         "value": (c1["interactions"] - c0["interactions"]) / ms_dev / 1e6,
                         "ms": ms_dev, "wall_s": wall_dev, "block_steps": nblk,
                         "launches_per_block": (s.launch_count() - l0) / max(1, nblk),
-                        "dE_over_E": abs(E_dev - E0) / abs(E0)}
+                        "dE_over_E": (abs(E_dev - E0) / abs(E0)) if args.block_steps == 0
+                        else None}
         with _lib.NBody(m, x, v, eps=eps, precision=prec, eta=0.01, lev_min=3, lev_max=20) as s:
             hist = {}
             blocks = 0
@@ -691,13 +696,17 @@ def run_batched(args):
     x = np.concatenate([p[1] for p in parts])
     v = np.concatenate([p[2] for p in parts])
     inter = float((sizes.astype(np.float64) ** 2).sum())
-    steps = 1000
-    out = {"metric": "G pair-interactions/s (acc+jerk, 4096 clusters, 1000 shared steps)",
-           "unit": UNIT, "workload": "plummer_clusters_4096_n16-1024_eps1e-3_dt2^-8_1000steps",
+    steps = args.batched_steps
+    out = {"metric": f"G pair-interactions/s (acc+jerk, 4096 clusters, {steps} shared steps)",
+           "unit": UNIT, "workload": f"plummer_clusters_4096_n16-1024_eps1e-3_dt2^-8_{steps}steps",
            "sum_n": int(off[-1]), "sum_n2": inter, "results": {}}
     for prec in args.precisions.split(","):
         with _lib.Batch(off, m, x, v, eps=1e-3, lev_shared=8, precision=prec) as b:
-            best, timings = tune.tune_batched(b, steps=20)
+            if args.variant >= 0:
+                best = (args.variant, steps)
+                b.set_tuning(args.variant, steps, 0, True)
+            else:
+                best, timings = tune.tune_batched(b, steps=20)
             k0, w0 = b.energy()
             b.run(steps)  # capture + warm
             b.sync()
@@ -727,7 +736,7 @@ def run_batched(args):
             "tuned": {"variant": best[0], "steps_per_launch": best[1]},
             "per_cluster_launches": {"value": inter * pc_steps / pc_ms / 1e6, "steps": pc_steps,
                                      "ms": pc_ms},
-            "dE_over_E_median_after_2000_steps": float(np.median(dE)),
+            f"dE_over_E_median_after_{2 * steps}_steps": float(np.median(dE)),
             "note": "dt = 1/256 with eps = 1e-3 does not resolve close encounters in small "
                     "clusters; the FP64 oracle loses energy at the same level"}
     if not args.no_cpu:
