@@ -80,6 +80,41 @@ bool finite_all(const double *p, int64_t cnt) {
   return true;
 }
 
+// finite_all over large arrays on the host's cores: contiguous chunks on
+// up to 16 threads (the caller's thread takes the last); a thread that
+// cannot be created leaves its chunk to the caller.
+bool finite_all_par(const double *p, int64_t cnt) {
+  constexpr int64_t kMinPar = int64_t(1) << 20;
+  if (cnt < kMinPar) return finite_all(p, cnt);
+  const unsigned hw = std::thread::hardware_concurrency();
+  int T = hw ? static_cast<int>(hw) : 1;
+  if (T > 16) T = 16;
+  if (T < 2) return finite_all(p, cnt);
+  const int64_t chunk = (cnt + T - 1) / T;
+  std::vector<std::thread> th;
+  std::vector<char> ok(T, 1);
+  int spawned = 0;
+  try {
+    th.reserve(T - 1);
+    for (int k = 0; k < T - 1; ++k) {
+      const int64_t b = k * chunk, e = b + chunk < cnt ? b + chunk : cnt;
+      th.emplace_back([p, b, e, k, &ok] { ok[k] = finite_all(p + b, e - b) ? 1 : 0; });
+      ++spawned;
+    }
+  } catch (...) {
+  }
+  bool good = true;
+  for (int k = spawned; k < T; ++k) {
+    const int64_t b = k * chunk;
+    if (b >= cnt) break;
+    const int64_t e = b + chunk < cnt ? b + chunk : cnt;
+    good = finite_all(p + b, e - b) && good;
+  }
+  for (auto &t : th) t.join();
+  for (int k = 0; k < spawned; ++k) good = good && ok[k];
+  return good;
+}
+
 int64_t tick_of(double t, bool *ok) {
   const double s = std::ldexp(t, kTicksLog2);
   *ok = std::isfinite(t) && s >= 0.0 && s < 9.0e18 && std::floor(s) == s;
@@ -481,7 +516,7 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   if (!m || !x || !v) return fail(NB_ERR_INVALID_ARG, "null input array");
   nb_status s = validate_config(cfg);
   if (s != NB_OK) return s;
-  if (!finite_all(m, n) || !finite_all(x, 3 * n) || !finite_all(v, 3 * n))
+  if (!finite_all_par(m, n) || !finite_all_par(x, 3 * n) || !finite_all_par(v, 3 * n))
     return fail(NB_ERR_INVALID_ARG, "non-finite mass, position or velocity");
   for (int64_t i = 0; i < n; ++i)
     if (m[i] < 0) return fail(NB_ERR_INVALID_ARG, "negative mass at %lld", (long long)i);
@@ -740,7 +775,7 @@ nb_status nb_force_jerk(nb_ctx *c, const int32_t *idx, int64_t n_idx, double *ac
                             c->stream));
   s = sync_ctx(c);
   if (s != NB_OK) return s;
-  if ((acc && !finite_all(acc, 3 * cnt)) || (jerk && !finite_all(jerk, 3 * cnt)))
+  if ((acc && !finite_all_par(acc, 3 * cnt)) || (jerk && !finite_all_par(jerk, 3 * cnt)))
     return fail(NB_ERR_NUMERIC, "non-finite acceleration or jerk");
   return NB_OK;
 }
@@ -1433,8 +1468,8 @@ nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double
   if (!x || !v || !a || !jerk || !t_tick || !lev)
     return fail(NB_ERR_INVALID_ARG, "nb_set_state needs all six arrays");
   const int64_t n = c->n;
-  if (!finite_all(x, 3 * n) || !finite_all(v, 3 * n) || !finite_all(a, 3 * n) ||
-      !finite_all(jerk, 3 * n))
+  if (!finite_all_par(x, 3 * n) || !finite_all_par(v, 3 * n) || !finite_all_par(a, 3 * n) ||
+      !finite_all_par(jerk, 3 * n))
     return fail(NB_ERR_INVALID_ARG, "non-finite state");
   for (int64_t i = 0; i < n; ++i) {
     if (lev[i] < 0 || lev[i] > kTicksLog2 || t_tick[i] < 0 ||

@@ -286,6 +286,27 @@ def test_fp32_range_reports_numeric_error(nb):
         assert e.value.status == nb.NB_ERR_NUMERIC
 
 
+def test_set_state_rejects_non_finite_values_in_large_states(nb):
+    """The state check of nb_set_state runs on the host's cores for large
+    arrays: a NaN or an infinity anywhere (first, last or in a middle chunk)
+    is rejected with NB_ERR_INVALID_ARG and the state is left unchanged."""
+    n = 800_000  # 2.4M values per array: the threaded check
+    m, x, v = ics.plummer(n, 43)
+    with nb.NBody(m, x, v, eps=1e-2, block_steps=False, lev_shared=8) as s:
+        st = s.get_state()
+        for key, pos, bad in (("x", 0, np.nan), ("v", 3 * n - 1, np.inf),
+                              ("a", 3 * n // 2 + 7, -np.inf), ("jerk", 1_234_567, np.nan)):
+            mod = {k: a.copy() for k, a in st.items()}
+            mod[key].reshape(-1)[pos] = bad
+            with pytest.raises(nb.NBodyError) as e:
+                s.set_state(mod)
+            assert e.value.status == nb.NB_ERR_INVALID_ARG
+        s.set_state(st)
+        back = s.get_state()
+    for k in st:
+        assert np.array_equal(back[k], st[k]), k
+
+
 def test_allocation_cap_reports_oom(nb, monkeypatch):
     monkeypatch.setenv("NB_TEST_MAX_BYTES", "1000")
     m, x, v = ics.plummer(1000, 2)
