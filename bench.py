@@ -440,6 +440,22 @@ def run_ours(args, rank, world, local_rank):
         ferr["sample"] = (f"the CPU baseline's {len(samp)} random particles (condition sums on "
                           f"the first {kc}), initial state; GPU: all N evaluated as in a timed "
                           f"step")
+        if sweep is not None:
+            # each active fraction of the sweep at the initial state: the same
+            # random subsets, 256 of their particles against the oracle
+            for row, k in zip(sweep, range(10, -1, -1)):
+                na = row["n_act"]
+                sub = ics.random_active_subset(n, na, 3000 + k)
+                d_sub = torch.from_numpy(sub).to(dev)
+                sa = torch.empty((na, 3), dtype=torch.float64, device=dev)
+                sj = torch.empty_like(sa)
+                s.force_jerk_dev(d_sub, na, sa, sj)
+                torch.cuda.synchronize(dev)
+                pick = np.sort(np.random.default_rng(4000 + k).choice(na, min(na, 256),
+                                                                       replace=False))
+                ra_k, rj_k = O.force_jerk(m, x, v, EPS, idx=sub[pick])
+                e = force_error(sa.cpu().numpy()[pick], sj.cpu().numpy()[pick], ra_k, rj_k)
+                row["force_err"] = {q: e[q] for q in ("acc_max_ei", "acc_norm", "jerk_max_ei")}
     del d_acc, d_jrk, d_idx
     out = {
         "metric": METRIC,
@@ -680,6 +696,47 @@ def run_block65536(args):
     return 0
 
 
+def batched_oracle_checks(_lib, O, off, m, x, v, tuned, steps, n_force=64, n_energy=32):
+    """The batched form against the FP64 oracle: the per-particle force and
+    jerk errors of the batch's first evaluation on n_force sampled
+    clusters, and the energy error over `steps` shared steps of 1/256 from
+    the initial state on n_energy of them, GPU (tuned shape) beside the
+    oracle's Hermite loop on the same clusters."""
+    nc = len(off) - 1
+    rng = np.random.default_rng(2004)
+    fc = np.sort(rng.choice(nc, n_force, replace=False))
+    ec = fc[:n_energy]
+    out = {}
+    for prec, (var, spl) in tuned.items():
+        with _lib.Batch(off, m, x, v, eps=1e-3, lev_shared=8, precision=prec) as b:
+            st0 = b.get_state()
+            k0, w0 = b.energy()
+            b.set_tuning(var, min(spl, steps), 0, True)
+            b.run(steps)
+            k1, w1 = b.energy()
+        ea, ej, na, nj = [], [], [], []
+        for c in fc:
+            sl = slice(off[c], off[c + 1])
+            ra, rj = O.force_jerk(m[sl], x[sl], v[sl], 1e-3)
+            e = force_error(st0["a"][sl], st0["jerk"][sl], ra, rj)
+            ea.append(e["acc_max_ei"]); ej.append(e["jerk_max_ei"])
+            na.append(e["acc_norm"]); nj.append(e["jerk_norm"])
+        dE_gpu = np.abs((k1 + w1) - (k0 + w0)) / np.abs(k0 + w0)
+        dE_orc = []
+        for c in ec:
+            sl = slice(off[c], off[c + 1])
+            E0 = O.energy(m[sl], x[sl], v[sl], 1e-3)[2]
+            xo, vo, _, _ = O.hermite_shared(m[sl], x[sl], v[sl], 1e-3, 8, steps)
+            dE_orc.append(abs(O.energy(m[sl], xo, vo, 1e-3)[2] - E0) / abs(E0))
+        out[prec] = {"acc_max_ei": float(max(ea)), "jerk_max_ei": float(max(ej)),
+                     "acc_norm_max": float(max(na)), "jerk_norm_max": float(max(nj)),
+                     "dE_over_E_median_gpu": float(np.median(dE_gpu[ec])),
+                     "dE_over_E_median_oracle": float(np.median(dE_orc))}
+    out["sample"] = (f"first evaluation of {n_force} random clusters (seed 2004); energy over "
+                     f"{steps} steps of 1/256 from the initial state on {n_energy} of them")
+    return out
+
+
 def run_batched(args):
     """4096 Plummer clusters of log-uniform size in [16, 1024] (seeds
     (1004, c)), eps = 1e-3, shared dt = 1/256, 1000 steps: the persistent
@@ -700,6 +757,7 @@ def run_batched(args):
     out = {"metric": f"G pair-interactions/s (acc+jerk, 4096 clusters, {steps} shared steps)",
            "unit": UNIT, "workload": f"plummer_clusters_4096_n16-1024_eps1e-3_dt2^-8_{steps}steps",
            "sum_n": int(off[-1]), "sum_n2": inter, "results": {}}
+    tuned = {}
     for prec in args.precisions.split(","):
         with _lib.Batch(off, m, x, v, eps=1e-3, lev_shared=8, precision=prec) as b:
             if args.variant >= 0:
@@ -731,6 +789,7 @@ def run_batched(args):
             e3.record()
             torch.cuda.synchronize()
             pc_ms = e2.elapsed_time(e3)
+        tuned[prec] = (best[0], best[1])
         out["results"][prec] = {
             "value": inter * steps / ms / 1e6, "ms": ms, "launches": launches,
             "tuned": {"variant": best[0], "steps_per_launch": best[1]},
@@ -742,6 +801,8 @@ def run_batched(args):
     if not args.no_cpu:
         from oracle import oracle as O
 
+        out["oracle_checks"] = batched_oracle_checks(_lib, O, off, m, x, v, tuned,
+                                                     min(steps, 200))
         # the oracle's shared-step loop over clusters until ~4e8 interactions
         take, work = [], 0.0
         for c in range(len(sizes)):
@@ -954,6 +1015,24 @@ def run_symplectic(args):
     if not args.no_cpu:
         from oracle import oracle as O
 
+        # the acceleration the integrator used, against the FP64 oracle: one
+        # sixth-order step (automatic layout), then the stored a = A(x) on
+        # 1024 sampled particles
+        samp = np.sort(np.random.default_rng(2006).choice(n, 1024, replace=False))
+        ferr = {}
+        for prec in args.precisions.split(","):
+            with _lib.NBody(m, x, v, eps=eps, precision=prec) as s:
+                s.symplectic(6, 2.0**-8, 1)
+                st = s.get_state(want=("x", "v", "a"))
+            ra, rj = O.force_jerk(m, st["x"], st["v"], eps, idx=samp)
+            ca, _ = O.force_jerk_abs(m, st["x"], st["v"], eps, idx=samp)
+            e = force_error(st["a"][samp], rj, ra, rj, (ca, ca))
+            ferr[prec] = {k: e[k] for k in ("acc_max_ei", "acc_p99_ei", "acc_norm",
+                                            "acc_cond_max")}
+        ferr["sample"] = ("1024 random particles (seed 2006) after one sixth-order step of "
+                          "2^-8: the stored acceleration against the oracle's at the same "
+                          "positions")
+        out["force_err"] = ferr
         out["cpu_baseline"] = _oracle_beside(
             lambda: O.acc(m, x, eps), n * n / 1e9, UNIT,
             "one FP64 acceleration evaluation of all N particles by the oracle (the "
