@@ -19,10 +19,11 @@
 //  * Split precision ("double-single", after Gaburov, Harfst & Portegies
 //    Zwart 2009, cited in the paper's Sec. 4): positions are hi + lo FP32
 //    pairs and d = (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo); FP32 partial sums
-//    over short runs of j (32 per thread for the acceleration, a 256-record
-//    tile for the jerk) are folded into hi + lo accumulators with an
-//    error-free two-sum, so the split-precision overhead is per run, not per
-//    pair, except for the three extra subtractions per coordinate.
+//    over runs of j (32 per thread for the acceleration in near tiles, a
+//    256-record tile for the acceleration in far tiles and for the jerk) are
+//    folded into hi + lo accumulators with an error-free two-sum, so the
+//    split-precision overhead is per run, not per pair, except for the
+//    three extra subtractions per coordinate in near tiles.
 //  * Work decomposition: the (i-block, j-tile) space is cut into equal
 //    contiguous ranges, one per persistent CTA (a "stream-K" split), so every
 //    active-list length fills the GPU evenly.  An i-block whose j-range spans
@@ -116,7 +117,7 @@ using dev::VOps;
 // Split-precision accumulators of IPT i-particles: acceleration and jerk,
 // high and low words.  In registers, or (SMEM) in shared memory at a
 // per-thread slot so that wide IPT shapes keep registers for the pair
-// arithmetic; the slots are touched only at folds, every 32 j.
+// arithmetic; the slots are touched only at folds.
 template <int IPT, int NT, bool SMEM>
 struct DsAcc;
 template <int IPT, int NT>
@@ -325,26 +326,32 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int c = 0; c < 3; ++c) p1[q][c] = p2[q][c] = O::bc(0.f);
 
-      // The tile is walked in chunks of CH j-records per thread; the
+      // The tile is walked in chunks of CHW j-records per thread; the
       // acceleration's FP32 chunk sums are folded into the accumulators after
-      // every chunk (a large close-pair term then only inflates the rounding
-      // of the few additions that follow it in its chunk), the jerk's once
-      // per tile (its tolerance is ten times looser).
+      // every chunk, the jerk's once per tile (its tolerance is ten times
+      // looser).  Near tiles fold every kFoldChunk j: a large close-pair term
+      // then only inflates the rounding of the few additions that follow it
+      // in its chunk.  A far tile (every pair at least kRelKappa tile radii
+      // away) has no such terms and folds once per tile (measured at N = 1M:
+      // 881 -> 866 ms per evaluation with the 16-deep unroll, the same
+      // sampled errors).
       constexpr int CH = (PREC && kFoldChunk < kJT / TPI) ? kFoldChunk : kJT / TPI;
-      // j-loop unroll: 8 for the tile-relative kernel (measured 1 % faster
-      // at N = 1M), 4 elsewhere (8 is 3 % slower for the FP32 IPT = 4 shape)
-      constexpr int UNR = REL ? 8 : 4;
+      // j-loop unroll: 16 for the tile-relative kernel (measured at N = 1M:
+      // 878 ms against 881 with 8, which was 1 % faster than 4), 4 elsewhere
+      // (8 is 3 % slower for the FP32 IPT = 4 shape)
+      constexpr int UNR = REL ? 16 : 4;
       auto walk_tile = [&](auto far_tag) {
         constexpr bool FAR = decltype(far_tag)::value;
+        constexpr int CHW = FAR ? kJT / TPI : CH;
 #pragma unroll 1
-      for (int c0 = r; c0 < kJT; c0 += CH * TPI) {
+      for (int c0 = r; c0 < kJT; c0 += CHW * TPI) {
         V pa[NQ][3];
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
           for (int c = 0; c < 3; ++c) pa[q][c] = O::bc(0.f);
 #pragma unroll(UNR)
-        for (int jj = c0; jj < c0 + CH * TPI; jj += TPI) {
+        for (int jj = c0; jj < c0 + CHW * TPI; jj += TPI) {
           float4 hj, lj;
           V vxj, vyj, vzj;
           if (JRK) {
