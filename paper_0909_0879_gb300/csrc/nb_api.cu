@@ -205,6 +205,8 @@ struct nb_ctx {
   int32_t *lev = nullptr;
   float4 *jhi = nullptr, *jlo = nullptr, *jvel = nullptr;  // j-records
   float4 *jrel = nullptr, *tinfo = nullptr;  // tile-relative records, tile boxes (DS)
+  float4 *sp4 = nullptr;  // the predictor's FP32 split of the state (fused block steps)
+  float2 *sp2 = nullptr;
   int32_t *act = nullptr;       // active list
   int32_t *blk = nullptr;       // scheduling scratch
   int64_t *scal = nullptr;      // [0] t_next ticks, [1] n_act
@@ -564,6 +566,8 @@ nb_status nb_init(nb_ctx **out, int64_t n, const double *m, const double *x,
   TRY(dev_alloc_t(c, &c->blk, next_block_scratch_ints(n) + 1));
   TRY(dev_alloc_t(c, &c->scal, kCtlSlots));
   TRY(dev_alloc_t(c, &c->lb_status, c->n_jt));
+  TRY(dev_alloc_t(c, &c->sp4, 4 * static_cast<size_t>(n)));
+  TRY(dev_alloc_t(c, &c->sp2, n));
   // the device error word and the clamp counter live in scal[2] and scal[3]
   c->err = reinterpret_cast<int *>(c->scal + kCtlErr);
   c->clamped = reinterpret_cast<unsigned long long *>(c->scal + kCtlClamped);
@@ -914,6 +918,8 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   B.m = c->m;
   B.t_tick = c->t_tick;
   B.lev = c->lev;
+  B.sp4 = c->sp4;
+  B.sp2 = c->sp2;
   B.prec = c->cfg.precision;
   B.jhi = c->jhi;
   B.jlo = c->jlo;
@@ -937,6 +943,7 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
     E.hi[k] = b[k].hi;
     E.bi[k] = block_i(variant_at(b[k].v));
     E.pmax[k] = c->num_sms * ctas_per_sm(b[k].v);
+    E.mu[k] = static_cast<int>(min_units(variant_at(b[k].v).tpi));
   }
   E.part = reinterpret_cast<const float2 *>(c->part);
   E.G = c->cfg.G;
@@ -956,6 +963,8 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   E.n_clamped = c->clamped;
   E.ctl = c->scal;
   E.ext = c->ext;
+  E.sp4 = c->sp4;
+  E.sp2 = c->sp2;
   const int end_grid = c->num_sms * 2;
   // The bucket launches are independent graph branches (fork after
   // block_begin, join before block_end), so the ones outside their range
@@ -1350,7 +1359,10 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
                             c->stream));
     int nl = 0;
     NB_CUDA(launch_schedule_check(c->n, c->t_tick, c->lev, c->scal, c->stream, &nl));
-    c->launches += nl;
+    // the predictor's FP32 split of the state, kept current by the fused
+    // corrector from here on
+    NB_CUDA(launch_split_refresh(c->n, c->x, c->v, c->a, c->jk, c->sp4, c->sp2, c->stream));
+    c->launches += nl + 1;
   }
   s = sync_ctx(c);
   if (s != NB_OK) return s;

@@ -168,12 +168,15 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
     st_relaxed(B.status + vid,
                lb_word(epoch, vid == 0 ? kFlagPre : kFlagAgg, static_cast<uint64_t>(agg)));
 
-  // predictor of this tile's particles (split precision, FP32 pipe)
+  // predictor of this tile's particles (split precision, FP32 pipe, from
+  // the state's FP32 split)
   float4 h = make_float4(0.f, 0.f, 0.f, 0.f), lo = h;
   if (real) {
     const float dt = static_cast<float>(t_next - B.t_tick[i]) * static_cast<float>(kTick);
+    dev::PSplit S;
+    dev::load_split(i, B.sp4, B.sp2, S);
     float xh[3], xl[3], vp[3];
-    dev::predict_ds(B.x, B.v, B.a, B.jk, i, dt, xh, xl, vp);
+    dev::predict_split(S, dt, xh, xl, vp);
     h = dev::store_records_ds(i, xh, xl, vp, B.m[i], B.prec, B.jhi, B.jlo, B.jvel, &lo);
   }
   if (B.jrel)
@@ -223,20 +226,34 @@ __device__ __forceinline__ void fixup_warp_n(const float2 *__restrict__ part,
     for (int c = 0; c < 6; ++c) h[e][c] = l[e][c] = 0.f;
     if (use[e] && phi[e] - plo[e] + 1 > span) span = phi[e] - plo[e] + 1;
   }
-  for (int o = lane; o < span; o += 32) {
+  // a single entry loads NB of its lane's partials before adding them (in
+  // the same ascending order), so their round trips overlap
+  constexpr int NB = NQ == 1 ? 4 : 1;
+  for (int o0 = lane; o0 < span; o0 += 32 * NB) {
 #pragma unroll
     for (int e = 0; e < NQ; ++e) {
-      const int p = plo[e] + o;
-      if (use[e] && p <= phi[e]) {
-        const uint64_t u0p = dev::udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
-        const int slot = (dev::udiv(u0p, n_jt) == ib[e]) ? 0 : 1;
-        const float2 *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+      float2 w[NB][6];
+      bool have[NB];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const float2 w = src[static_cast<size_t>(c) * BI + kk[e]];
-          dev::ds_add_pair(h[e][c], l[e][c], w.x, w.y, h[e][c], l[e][c]);
+      for (int b = 0; b < NB; ++b) {
+        const int p = plo[e] + o0 + 32 * b;
+        have[b] = use[e] && p <= phi[e];
+        if (have[b]) {
+          const uint64_t u0p =
+              dev::udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
+          const int slot = (dev::udiv(u0p, n_jt) == ib[e]) ? 0 : 1;
+          const float2 *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) w[b][c] = src[static_cast<size_t>(c) * BI + kk[e]];
         }
       }
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (have[b]) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+            dev::ds_add_pair(h[e][c], l[e][c], w[b][c].x, w[b][c].y, h[e][c], l[e][c]);
+        }
     }
   }
 #pragma unroll
@@ -254,10 +271,10 @@ __device__ __forceinline__ void fixup_warp_n(const float2 *__restrict__ part,
 constexpr int kEndWarps = kEndThreads / 32;
 
 // New force of one round's entry as block_end stages it: the fix-up sum of a
-// split i-block (split precision, converted to FP64 by the corrector lane)
-// or nothing (its only CTA wrote the FP64 value to a1, j1).
+// split i-block (converted to FP64 by the fix-up warp's lanes 0..5) or
+// nothing (its only CTA wrote the FP64 value to a1, j1).
 struct EndStage {
-  float2 f[4 * kEndWarps][6];
+  double f[4 * kEndWarps][6];
   int split[4 * kEndWarps];
 };
 
@@ -284,37 +301,50 @@ __device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t 
     phi[e] = dev::owner_of((ib[e] + 1) * n_jt - 1, U, P);
     split[e] = valid[e] && plo[e] != phi[e];
   }
-  // warp 0 loads the corrector's inputs of the round's entries while the
-  // warps add the partial sums
+  // The corrector runs on three lanes per entry (one per component, ten
+  // entries per warp): these lanes load its inputs while the warps add
+  // the partial sums.
+  constexpr int kRound = NQ * kEndWarps;
+  const int eq = lane < 30 ? wid * 10 + lane / 3 : kRound;  // this lane's entry
+  const int cq = lane % 3;
   dev::PState st;
   int64_t ci = -1;
-  if (wid == 0 && lane < NQ * kEndWarps && k0 + lane < n_act) {
-    ci = E.act[k0 + lane];
+  if (eq < kRound && k0 + eq < n_act) {
+    ci = E.act[k0 + eq];
     dev::load_state(ci, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, st);
   }
   float h[NQ][6], l[NQ][6];
   fixup_warp_n<NQ>(E.part, ib, kk, plo, phi, split, U, P, n_jt, BI, lane, h, l);
-  if (lane == 0) {
+  // every lane holds the sums: lane c converts component c, so the FP64
+  // work (whose warp instructions cost the same however few lanes are
+  // active) is one round per warp instead of six on the corrector lane
 #pragma unroll
-    for (int e = 0; e < NQ; ++e) {
-      const int q = wid + kEndWarps * e;
-      sg.split[q] = split[e] ? 1 : 0;
+  for (int e = 0; e < NQ; ++e) {
+    const int q = wid + kEndWarps * e;
+    if (lane == 0) sg.split[q] = split[e] ? 1 : 0;
+    if (split[e] && lane < 6) {
+      float hh = h[e][0], ll = l[e][0];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) sg.f[q][c] = make_float2(h[e][c], l[e][c]);
+      for (int c = 1; c < 6; ++c)
+        if (lane == c) {
+          hh = h[e][c];
+          ll = l[e][c];
+        }
+      sg.f[q][lane] = dev::ds_to_double(hh, ll, E.G);
     }
   }
   __syncthreads();
   if (ci >= 0) {
-    const int64_t k = k0 + lane;
+    const int64_t k = k0 + eq;
     double an[3], jn[3];
-    if (sg.split[lane]) {
+    if (sg.split[eq]) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        an[c] = dev::ds_to_double(sg.f[lane][c].x, sg.f[lane][c].y, E.G);
-        jn[c] = dev::ds_to_double(sg.f[lane][3 + c].x, sg.f[lane][3 + c].y, E.G);
-        E.a1[3 * k + c] = an[c];
-        E.j1[3 * k + c] = jn[c];
+        an[c] = sg.f[eq][c];
+        jn[c] = sg.f[eq][3 + c];
       }
+      E.a1[3 * k + cq] = dev::sel3(an, cq);
+      E.j1[3 * k + cq] = dev::sel3(jn, cq);
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -322,9 +352,15 @@ __device__ __forceinline__ void end_round(const EndArgs &E, int64_t k0, int64_t 
         jn[c] = E.j1[3 * k + c];
       }
     }
-    dev::correct_vals(ci, st, an, jn, t_next, E.x, E.v, E.a, E.jk, E.t_tick, E.lev, E.eta,
-                      E.lev_min, E.lev_max, E.block_steps, E.n_clamped, E.ctl + kCtlLevCnt,
-                      &E.ext);
+    // the warp's corrector lanes: whole triples of its valid entries
+    int64_t nv = n_act - k0 - static_cast<int64_t>(wid) * 10;
+    const int64_t cap = kRound - wid * 10;
+    nv = nv < cap ? nv : cap;
+    nv = nv < 10 ? nv : 10;
+    const unsigned mask = nv >= 10 ? 0x3fffffffu : ((1u << (3 * nv)) - 1u);
+    dev::correct_vals3(cq, mask, lane - cq, ci, st, an, jn, t_next, E.x, E.v, E.a, E.jk,
+                       E.t_tick, E.lev, E.eta, E.lev_min, E.lev_max, E.block_steps,
+                       E.n_clamped, E.ctl + kCtlLevCnt, &E.ext, E.sp4, E.sp2);
   }
   __syncthreads();
 }
@@ -347,7 +383,8 @@ __global__ void __launch_bounds__(kEndThreads) block_end_kernel(const EndArgs E)
   const int BI = E.bi[b];
   const uint64_t U = dev::udiv(static_cast<uint64_t>(n_act + BI - 1), BI) *
                      static_cast<uint64_t>(E.n_jt);
-  const uint64_t pm = (U + kMinUnits - 1) / kMinUnits;
+  const uint64_t mu = static_cast<uint64_t>(E.mu[b]);
+  const uint64_t pm = (U + mu - 1) / mu;
   const int P = static_cast<int>(pm < static_cast<uint64_t>(E.pmax[b]) ? pm : E.pmax[b]);
   // short lists: one entry per warp per round (the fix-ups in parallel);
   // long lists: four, so that the corrector warp runs 32 lanes
@@ -422,7 +459,36 @@ __global__ void __launch_bounds__(kChkThreads)
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlLastT] = t_cur;
 }
 
+// The predictor's FP32 split of every particle's state.
+__global__ void __launch_bounds__(kChkThreads)
+    split_refresh_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ v,
+                         const double *__restrict__ a, const double *__restrict__ jk,
+                         float4 *__restrict__ sp4, float2 *__restrict__ sp2) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double xs[3], vs[3], as[3], js[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    xs[c] = x[3 * i + c];
+    vs[c] = v[3 * i + c];
+    as[c] = a[3 * i + c];
+    js[c] = jk[3 * i + c];
+  }
+  dev::PSplit S;
+  dev::split_state(xs, vs, as, js, S);
+  dev::store_split(i, S, sp4, sp2);
+}
+
 }  // namespace
+
+cudaError_t launch_split_refresh(int64_t n, const double *x, const double *v, const double *a,
+                                 const double *jk, float4 *sp4, float2 *sp2, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + kChkThreads - 1) / kChkThreads;
+  split_refresh_kernel<<<static_cast<unsigned>(nb), kChkThreads, 0, s>>>(n, x, v, a, jk, sp4,
+                                                                          sp2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_schedule_check(int64_t n, const int64_t *t_tick, const int32_t *lev,
                                   int64_t *ctl, cudaStream_t s, int *launches) {

@@ -236,18 +236,61 @@ __device__ __forceinline__ void ds_add_pair(float ah, float al, float bh, float 
 // position error is a few ulps of the a and j terms (~2^-24 |dt^2 a|),
 // far below the FP32 rounding of a pair difference; the velocity is
 // rounded to FP32 as the records store it.
-__device__ __forceinline__ void predict_ds(const double *__restrict__ x,
-                                           const double *__restrict__ v,
-                                           const double *__restrict__ a,
-                                           const double *__restrict__ jk, int64_t i, float dt,
-                                           float xh[3], float xl[3], float vp[3]) {
+// The predictor takes the state as its FP32 split (PSplit): per component
+// the high and low words of x and v and a, j rounded to FP32.  The fused
+// block steps keep this split beside the FP64 state (the corrector writes
+// it), so that predicting all N particles each step is FP32 work only.
+struct PSplit {
+  float x0[3], x1[3], v0[3], v1[3], a[3], j[3];
+};
+
+__device__ __forceinline__ void split_state(const double xs[3], const double vs[3],
+                                            const double as[3], const double js[3],
+                                            PSplit &S) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    S.x0[c] = d2f_rn(xs[c]);
+    S.x1[c] = d2f_rn(xs[c] - f2d(S.x0[c]));
+    S.v0[c] = d2f_rn(vs[c]);
+    S.v1[c] = d2f_rn(vs[c] - f2d(S.v0[c]));
+    S.a[c] = d2f_rn(as[c]);
+    S.j[c] = d2f_rn(js[c]);
+  }
+}
+
+// Storage of the split: four float4 (sp4[4 i .. 4 i + 3]) and one float2
+// (sp2[i]) per particle, in the order x0, x1, v0, v1, a, j.
+__device__ __forceinline__ void store_split(int64_t i, const PSplit &S, float4 *sp4,
+                                            float2 *sp2) {
+  sp4[4 * i + 0] = make_float4(S.x0[0], S.x0[1], S.x0[2], S.x1[0]);
+  sp4[4 * i + 1] = make_float4(S.x1[1], S.x1[2], S.v0[0], S.v0[1]);
+  sp4[4 * i + 2] = make_float4(S.v0[2], S.v1[0], S.v1[1], S.v1[2]);
+  sp4[4 * i + 3] = make_float4(S.a[0], S.a[1], S.a[2], S.j[0]);
+  sp2[i] = make_float2(S.j[1], S.j[2]);
+}
+
+__device__ __forceinline__ void load_split(int64_t i, const float4 *__restrict__ sp4,
+                                           const float2 *__restrict__ sp2, PSplit &S) {
+  const float4 q0 = sp4[4 * i + 0];
+  const float4 q1 = sp4[4 * i + 1];
+  const float4 q2 = sp4[4 * i + 2];
+  const float4 q3 = sp4[4 * i + 3];
+  const float2 q4 = sp2[i];
+  S.x0[0] = q0.x; S.x0[1] = q0.y; S.x0[2] = q0.z; S.x1[0] = q0.w;
+  S.x1[1] = q1.x; S.x1[2] = q1.y; S.v0[0] = q1.z; S.v0[1] = q1.w;
+  S.v0[2] = q2.x; S.v1[0] = q2.y; S.v1[1] = q2.z; S.v1[2] = q2.w;
+  S.a[0] = q3.x; S.a[1] = q3.y; S.a[2] = q3.z; S.j[0] = q3.w;
+  S.j[1] = q4.x; S.j[2] = q4.y;
+}
+
+__device__ __forceinline__ void predict_split(const PSplit &S, float dt, float xh[3],
+                                              float xl[3], float vp[3]) {
   const float h2 = 0.5f * dt, h3 = dt * (1.0f / 3.0f);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double xc = x[3 * i + c], vc = v[3 * i + c];
-    const float x0 = d2f_rn(xc), x1 = d2f_rn(xc - f2d(x0));
-    const float v0 = d2f_rn(vc), v1 = d2f_rn(vc - f2d(v0));
-    const float ac = d2f_rn(a[3 * i + c]), jc = d2f_rn(jk[3 * i + c]);
+    const float x0 = S.x0[c], x1 = S.x1[c];
+    const float v0 = S.v0[c], v1 = S.v1[c];
+    const float ac = S.a[c], jc = S.j[c];
     const float p = dt * v0;
     const float pe = fmaf(dt, v0, -p);  // dt v0 = p + pe exactly
     const float q = fmaf(dt, v1, pe) + dt * (h2 * fmaf(h3, jc, ac));
@@ -259,6 +302,32 @@ __device__ __forceinline__ void predict_ds(const double *__restrict__ x,
     xl[c] = __fsub_rn(e, __fsub_rn(hh, s));
     vp[c] = v0 + (v1 + dt * fmaf(h2, jc, ac));
   }
+}
+
+// (predict_ds_vals takes the particle's loaded state, predict_ds loads it.)
+__device__ __forceinline__ void predict_ds_vals(const double xs[3], const double vs[3],
+                                                const double as[3], const double js[3],
+                                                float dt, float xh[3], float xl[3],
+                                                float vp[3]) {
+  PSplit S;
+  split_state(xs, vs, as, js, S);
+  predict_split(S, dt, xh, xl, vp);
+}
+
+__device__ __forceinline__ void predict_ds(const double *__restrict__ x,
+                                           const double *__restrict__ v,
+                                           const double *__restrict__ a,
+                                           const double *__restrict__ jk, int64_t i, float dt,
+                                           float xh[3], float xl[3], float vp[3]) {
+  double xs[3], vs[3], as[3], js[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    xs[c] = x[3 * i + c];
+    vs[c] = v[3 * i + c];
+    as[c] = a[3 * i + c];
+    js[c] = jk[3 * i + c];
+  }
+  predict_ds_vals(xs, vs, as, js, dt, xh, xl, vp);
 }
 
 // j-records of particle i from a split-precision prediction: high words and
@@ -588,7 +657,8 @@ __device__ __forceinline__ void correct_vals(
     int64_t t_next, double *__restrict__ x, double *__restrict__ v, double *__restrict__ a,
     double *__restrict__ jk, int64_t *__restrict__ t_tick, int32_t *__restrict__ lev,
     double eta, int lev_min, int lev_max, int block_steps, unsigned long long *n_clamped,
-    int64_t *lev_cnt, const ExtField *ext = nullptr) {
+    int64_t *lev_cnt, const ExtField *ext = nullptr, float4 *sp4 = nullptr,
+    float2 *sp2 = nullptr) {
   const int64_t dtk = t_next - st.t;
   const double dt = static_cast<double>(dtk) * kTick;
   const double h2 = 0.5 * dt, h3 = dt * (1.0 / 3.0);
@@ -603,23 +673,132 @@ __device__ __forceinline__ void correct_vals(
                         : 1.f / dtf;
   const HermCoefF K = herm_coef_f(dtf, idt);
   float anf[3], jnf[3], a2e[3], a3e[3];
+  double xn[3], vn[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double x1, v1;
     anf[c] = d2f_rn(an3[c]);
     jnf[c] = d2f_rn(jn3[c]);
-    herm_component_f(K, dt, st.x[c], st.v[c], st.a[c], d2f_rn(st.j[c]), an3[c], jnf[c], x1,
-                     v1, a2e[c], a3e[c]);
-    x[3 * i + c] = x1;
-    v[3 * i + c] = v1;
+    herm_component_f(K, dt, st.x[c], st.v[c], st.a[c], d2f_rn(st.j[c]), an3[c], jnf[c], xn[c],
+                     vn[c], a2e[c], a3e[c]);
+    x[3 * i + c] = xn[c];
+    v[3 * i + c] = vn[c];
     a[3 * i + c] = an3[c];
     jk[3 * i + c] = jn3[c];
   }
   t_tick[i] = t_next;
+  if (sp4) {
+    // the predictor's FP32 split of the new state (a, j: the values above)
+    PSplit S;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      S.x0[c] = d2f_rn(xn[c]);
+      S.x1[c] = d2f_rn(xn[c] - f2d(S.x0[c]));
+      S.v0[c] = d2f_rn(vn[c]);
+      S.v1[c] = d2f_rn(vn[c] - f2d(S.v0[c]));
+      S.a[c] = anf[c];
+      S.j[c] = jnf[c];
+    }
+    store_split(i, S, sp4, sp2);
+  }
   if (block_steps) {
     // Aarseth's criterion dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)
     // in FP32, as numerator and denominator; the level comes from their
     // exponents (it only has to place dt between powers of two)
+    const float na = norm3f(anf), nj = norm3f(jnf), n2 = norm3f(a2e), n3 = norm3f(a3e);
+    const float N = static_cast<float>(eta) * fmaf(na, n2, nj * nj);
+    const float D = fmaf(nj, n3, n2 * n2);
+    int cl = 0;
+    const int want = level_from_ratio_f(N, D, lev_min, lev_max, &cl);
+    if (cl) atomicAdd(n_clamped, 1ull);
+    const int old = st.lev;
+    int nl = old;
+    if (want >= old) {
+      nl = want;
+    } else if (old - 1 >= lev_min) {
+      const int64_t period = static_cast<int64_t>(1) << (kTicksLog2 - (old - 1));
+      if (t_next % period == 0) nl = old - 1;
+    }
+    lev[i] = nl;
+    if (lev_cnt && nl != old) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(lev_cnt + old),
+                static_cast<unsigned long long>(-1ll));
+      atomicAdd(reinterpret_cast<unsigned long long *>(lev_cnt + nl), 1ull);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T sel3(const T u[3], int c) {
+  return c == 0 ? u[0] : (c == 1 ? u[1] : u[2]);
+}
+
+// correct_vals on three lanes of a warp, lane base + c taking component c
+// of the Hermite update (the same arithmetic per component): every lane of
+// the triple holds the particle's whole state and new pair force, the
+// derivatives at the end of the step and the split words meet by shuffles,
+// and lane base writes the time, the step criterion's level and the split.
+// The FP64 and integer-pipe work per warp is a third of one lane's doing
+// all three components.  mask: the lanes of the warp that call it (whole
+// triples).
+__device__ __forceinline__ void correct_vals3(
+    int c, unsigned mask, int base, int64_t i, const PState &st, const double an_pair[3],
+    const double jn_pair[3], int64_t t_next, double *__restrict__ x, double *__restrict__ v,
+    double *__restrict__ a, double *__restrict__ jk, int64_t *__restrict__ t_tick,
+    int32_t *__restrict__ lev, double eta, int lev_min, int lev_max, int block_steps,
+    unsigned long long *n_clamped, int64_t *lev_cnt, const ExtField *ext, float4 *sp4,
+    float2 *sp2) {
+  const int64_t dtk = t_next - st.t;
+  const double dt = static_cast<double>(dtk) * kTick;
+  const double h2 = 0.5 * dt, h3 = dt * (1.0 / 3.0);
+  double an3[3] = {an_pair[0], an_pair[1], an_pair[2]};
+  double jn3[3] = {jn_pair[0], jn_pair[1], jn_pair[2]};
+  if (ext && ext->on) ext_at_prediction(*ext, st, dt, h2, h3, an3, jn3);
+  const float dtf = static_cast<float>(dtk) * static_cast<float>(kTick);
+  const float idt = (dtk > 0 && (dtk & (dtk - 1)) == 0)
+                        ? pow2f(kTicksLog2 - (63 - __clzll(dtk)))
+                        : 1.f / dtf;
+  const HermCoefF K = herm_coef_f(dtf, idt);
+  const double anc = sel3(an3, c), jnc = sel3(jn3, c);
+  const float jncf = d2f_rn(jnc);
+  double xn, vn;
+  float a2c, a3c;
+  herm_component_f(K, dt, sel3(st.x, c), sel3(st.v, c), sel3(st.a, c), d2f_rn(sel3(st.j, c)),
+                   anc, jncf, xn, vn, a2c, a3c);
+  x[3 * i + c] = xn;
+  v[3 * i + c] = vn;
+  a[3 * i + c] = anc;
+  jk[3 * i + c] = jnc;
+  const float x0 = d2f_rn(xn), x1 = d2f_rn(xn - f2d(x0));
+  const float v0 = d2f_rn(vn), v1 = d2f_rn(vn - f2d(v0));
+  const float ancf = d2f_rn(anc);
+  float anf[3], jnf[3], a2e[3], a3e[3], sx0[3], sx1[3], sv0[3], sv1[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    anf[q] = __shfl_sync(mask, ancf, base + q);
+    jnf[q] = __shfl_sync(mask, jncf, base + q);
+    a2e[q] = __shfl_sync(mask, a2c, base + q);
+    a3e[q] = __shfl_sync(mask, a3c, base + q);
+    sx0[q] = __shfl_sync(mask, x0, base + q);
+    sx1[q] = __shfl_sync(mask, x1, base + q);
+    sv0[q] = __shfl_sync(mask, v0, base + q);
+    sv1[q] = __shfl_sync(mask, v1, base + q);
+  }
+  if (c != 0) return;
+  t_tick[i] = t_next;
+  if (sp4) {
+    PSplit S;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      S.x0[q] = sx0[q];
+      S.x1[q] = sx1[q];
+      S.v0[q] = sv0[q];
+      S.v1[q] = sv1[q];
+      S.a[q] = anf[q];
+      S.j[q] = jnf[q];
+    }
+    store_split(i, S, sp4, sp2);
+  }
+  if (block_steps) {
     const float na = norm3f(anf), nj = norm3f(jnf), n2 = norm3f(a2e), n3 = norm3f(a3e);
     const float N = static_cast<float>(eta) * fmaf(na, n2, nj * nj);
     const float D = fmaf(nj, n3, n2 * n2);

@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(NT, 1)
     n_i = A.ctl[kCtlNact];
     if (n_i < A.lo || n_i >= A.hi || n_i <= 0) return;
     U = dev::udiv(static_cast<uint64_t>(n_i + BI - 1), BI) * n_jt;
-    const uint64_t pmax = (U + kMinUnits - 1) / kMinUnits;
+    constexpr uint64_t MU = min_units(TPI);
+    const uint64_t pmax = (U + MU - 1) / MU;
     P = static_cast<int>(pmax < gridDim.x ? pmax : gridDim.x);
     if (p >= P) return;
   }
@@ -531,7 +532,7 @@ __global__ void force_fixup_kernel(const float2 *__restrict__ part, int64_t n_i,
                                    uint64_t n_jt, uint64_t U, int P, int BI,
                                    double G, double *__restrict__ acc,
                                    double *__restrict__ jerk, const int64_t *ctl,
-                                   int64_t lo, int64_t hi) {
+                                   int64_t lo, int64_t hi, int mu) {
   const int lane = threadIdx.x & 31;
   const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (ctl) {
@@ -539,7 +540,7 @@ __global__ void force_fixup_kernel(const float2 *__restrict__ part, int64_t n_i,
     n_i = ctl[kCtlNact];
     if (n_i < lo || n_i >= hi || n_i <= 0) return;
     U = dev::udiv(static_cast<uint64_t>(n_i + BI - 1), BI) * n_jt;
-    const uint64_t pmax = (U + kMinUnits - 1) / kMinUnits;
+    const uint64_t pmax = (U + mu - 1) / mu;
     if (pmax < static_cast<uint64_t>(P)) P = static_cast<int>(pmax);
   }
   if (k >= n_i) return;  // uniform per warp
@@ -666,13 +667,13 @@ ShapeBuckets shape_buckets(int prec, int mask, int64_t n_jt, int num_sms) {
   }
   const int vs[3] = {prec ? 4 : 9, prec ? 16 : 8, prec ? 26 : 14};
   const int64_t base[3] = {1, kBucketMid, kBucketLong};
-  // i-blocks a shape needs so that every SM gets kMinUnits units (a small
+  // i-blocks a shape needs so that every SM gets min_units units (a small
   // N has few j-tiles: N = 1024 is 4, and one 1024-particle i-block would
   // then run on a single CTA)
-  const int64_t need = kMinUnits * static_cast<int64_t>(num_sms);
-  const int64_t blocks = (need + n_jt - 1) / n_jt;
   b.nbk = 3;
   for (int k = 0; k < 3; ++k) {
+    const int64_t need = min_units(kTable[vs[k]].V.tpi) * static_cast<int64_t>(num_sms);
+    const int64_t blocks = (need + n_jt - 1) / n_jt;
     const int64_t fill = (blocks - 1) * block_i(kTable[vs[k]].V) + 1;
     b.lo[k] = k == 0 ? 1 : std::max(base[k], fill);
     if (k > 0 && b.lo[k] < b.lo[k - 1]) b.lo[k] = b.lo[k - 1];
@@ -716,8 +717,9 @@ int force_grid(int v, int64_t n_i, int64_t n_jt, int num_sms, int grid_cap) {
   const int64_t U = n_ib * n_jt;
   int64_t P = static_cast<int64_t>(num_sms) * ctas_per_sm(v);
   if (grid_cap > 0 && grid_cap < P) P = grid_cap;
-  // at least kMinUnits j-tiles per CTA
-  if ((U + kMinUnits - 1) / kMinUnits < P) P = (U + kMinUnits - 1) / kMinUnits;
+  // at least min_units j-tiles per CTA
+  const int64_t mu = min_units(V.tpi);
+  if ((U + mu - 1) / mu < P) P = (U + mu - 1) / mu;
   return static_cast<int>(P < 1 ? 1 : P);
 }
 
@@ -736,7 +738,7 @@ cudaError_t launch_force_dev(int v, const ForceArgs &A, int grid, int64_t n_max,
   const int64_t nb = (cap + 7) / 8;
   force_fixup_kernel<<<static_cast<unsigned>(nb > 0 ? nb : 1), 256, 0, s>>>(
       A.part, 0, static_cast<uint64_t>(A.n_jt), 0, grid, BI, A.G, A.acc, A.jerk, A.ctl, A.lo,
-      A.hi);
+      A.hi, static_cast<int>(min_units(E.V.tpi)));
   if (launches) *launches += 2;
   return cudaGetLastError();
 }
@@ -780,7 +782,7 @@ cudaError_t launch_force(int v, const ForceArgs &A, int grid, cudaStream_t s,
     const int64_t nb = (A.n_i + 7) / 8;
     force_fixup_kernel<<<static_cast<unsigned>(nb), tb, 0, s>>>(
         A.part, A.n_i, static_cast<uint64_t>(A.n_jt), U, grid, BI, A.G, A.acc,
-        A.jerk, nullptr, 0, 0);
+        A.jerk, nullptr, 0, 0, 4);
     e = cudaGetLastError();
     ++nl;
   }

@@ -86,9 +86,12 @@ constexpr int kCtlSlots = 40;
 // Device error-word bit of a timed-out look-back in the fused compaction.
 constexpr int kErrScanTimeout = 2;
 
-// Minimum j-tiles per CTA of the stream-K split (short lists are
-// latency-bound; fewer split segments keep the fix-up short).
-constexpr int64_t kMinUnits = 4;
+
+// Minimum j-tiles per CTA of the stream-K split, by the shape's threads
+// per i-particle: 2 for the short-list shapes (16 or more; their lists are
+// latency-bound and the CTA with the most tiles sets the time), 4
+// otherwise (fewer split segments keep the fix-up short).
+__host__ __device__ constexpr int64_t min_units(int tpi) { return tpi >= 16 ? 2 : 4; }
 
 // Active-list lengths where the built-in force shape changes.
 constexpr int64_t kBucketMid = 64;
@@ -127,7 +130,7 @@ int block_i(const Variant &V);  // i-particles per i-block
 // Built-in force shapes by active-list length: bucket k (lo[k] <= n_i <
 // lo[k+1]) runs variant v[k].  A bucket's lower edge is raised above its
 // nominal length (kBucketMid, kBucketLong) until its shape has enough
-// (i-block, j-tile) units to give every SM kMinUnits of them.
+// (i-block, j-tile) units to give every SM min_units of them.
 struct ShapeBuckets {
   int nbk;
   int64_t lo[3];
@@ -223,6 +226,8 @@ struct BeginArgs {
   const double *x, *v, *a, *jk, *m;
   const int64_t *t_tick;
   const int32_t *lev;
+  const float4 *sp4;                 // the predictor's FP32 split of the state
+  const float2 *sp2;
   int prec;
   float4 *jhi, *jlo, *jvel;
   float4 *jrel, *tinfo;              // DS only (tile frames), else null
@@ -243,6 +248,7 @@ struct EndArgs {
   int nbk;                           // force-shape buckets of the step
   int64_t lo[3], hi[3];              // active-count range of each bucket
   int bi[3], pmax[3];                // i-block size and persistent grid
+  int mu[3];                         // minimum j-tiles per CTA (min_units)
   const float2 *part;                // partial sums of split i-blocks (hi, lo pairs)
   double G;
   double *a1, *j1;
@@ -255,9 +261,15 @@ struct EndArgs {
   unsigned long long *n_clamped;
   int64_t *ctl;
   ExtField ext;                      // external field (on = 0: none)
+  float4 *sp4;                       // the predictor's FP32 split, kept current
+  float2 *sp2;
 };
+// The predictor's FP32 split of every particle's state into sp4, sp2.
+cudaError_t launch_split_refresh(int64_t n, const double *x, const double *v, const double *a,
+                                 const double *jk, float4 *sp4, float2 *sp2, cudaStream_t s);
 cudaError_t launch_block_end(const EndArgs &E, int grid, cudaStream_t s);
 constexpr int kEndThreads = 256;
+
 
 // --- i-split shards (nb_shard.cu) ---
 constexpr int kMaxShards = 64;
