@@ -631,6 +631,8 @@ const Entry kTable[] = {
     NB_VR(1, 2, 1, 256, 0, 1),  // 27
     NB_VR(1, 2, 4, 256, 0, 1),  // 28
     NB_VA(0, 8, 1, 256, 0, 1),  // 29 FP32, packed, 8 i-particles per thread
+    NB_VA(1, 1, 32, 512, 0, 0), // 30 DS, short lists, a warp per i-particle
+    NB_VA(0, 1, 32, 512, 0, 0), // 31 FP32, short lists, a warp per i-particle
 };
 constexpr int kNumVariants = sizeof(kTable) / sizeof(kTable[0]);
 
@@ -655,7 +657,11 @@ ShapeBuckets shape_buckets(int prec, int mask, int64_t n_jt, int num_sms) {
   // tile-relative far field, which costs ~1% when particles are not stored
   // in a spatial order and gains ~4-8% when they are; FP32 with IPT = 4,
   // 3-4% faster than IPT = 2 at every active fraction from 2^-10 to 1),
-  // more threads per i-particle as the list shortens.  The host-driven and
+  // more threads per i-particle as the list shortens (the shortest lists a
+  // warp per i-particle in 512-thread CTAs: twice the warps of the
+  // 256-thread, 16-per-particle shape on the same 16-particle i-blocks,
+  // N = 65,536 block steps 136.4 -> 141.0 G interactions/s in FP32 and
+  // N = 1024 shared steps 50.3 -> 53.8 in DS).  The host-driven and
   // the device-resident steps use the same buckets.  nb_set_force_table
   // overrides the choice per workload.
   ShapeBuckets b{};
@@ -665,7 +671,7 @@ ShapeBuckets shape_buckets(int prec, int mask, int64_t n_jt, int num_sms) {
     b.v[0] = prec ? 10 : 11;
     return b;
   }
-  const int vs[3] = {prec ? 4 : 9, prec ? 16 : 8, prec ? 26 : 14};
+  const int vs[3] = {prec ? 30 : 31, prec ? 16 : 8, prec ? 26 : 14};
   const int64_t base[3] = {1, kBucketMid, kBucketLong};
   // i-blocks a shape needs so that every SM gets min_units units (a small
   // N has few j-tiles: N = 1024 is 4, and one 1024-particle i-block would
