@@ -226,6 +226,17 @@ __device__ __forceinline__ void fixup_warp_n(const float2 *__restrict__ part,
     for (int c = 0; c < 6; ++c) h[e][c] = l[e][c] = 0.f;
     if (use[e] && phi[e] - plo[e] + 1 > span) span = phi[e] - plo[e] + 1;
   }
+  // A CTA's partial of i-block ib sits in its slot 0 (its first segment)
+  // unless ib is the CTA's second segment, which only the first CTA of the
+  // i-block can have (every later one starts inside ib): one division per
+  // entry instead of two per partial.
+  int slot0[NQ];
+#pragma unroll
+  for (int e = 0; e < NQ; ++e) {
+    const uint64_t u0p =
+        dev::udiv(U * static_cast<uint64_t>(plo[e]), static_cast<uint64_t>(P));
+    slot0[e] = (u0p == ib[e] * n_jt) ? 0 : 1;
+  }
   // a single entry loads NB of its lane's partials before adding them (in
   // the same ascending order), so their round trips overlap
   constexpr int NB = NQ == 1 ? 4 : 1;
@@ -239,9 +250,7 @@ __device__ __forceinline__ void fixup_warp_n(const float2 *__restrict__ part,
         const int p = plo[e] + o0 + 32 * b;
         have[b] = use[e] && p <= phi[e];
         if (have[b]) {
-          const uint64_t u0p =
-              dev::udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
-          const int slot = (dev::udiv(u0p, n_jt) == ib[e]) ? 0 : 1;
+          const int slot = p == plo[e] ? slot0[e] : 0;
           const float2 *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
 #pragma unroll
           for (int c = 0; c < 6; ++c) w[b][c] = src[static_cast<size_t>(c) * BI + kk[e]];

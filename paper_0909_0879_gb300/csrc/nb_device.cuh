@@ -366,9 +366,12 @@ __device__ __forceinline__ void fixup_warp(const float2 *__restrict__ part, uint
                                            float l[6]) {
 #pragma unroll
   for (int c = 0; c < 6; ++c) h[c] = l[c] = 0.f;
+  // slot 1 (a CTA's second segment) only for the first CTA, and only when
+  // its range starts before the i-block
+  const int slot0 =
+      udiv(U * static_cast<uint64_t>(plo), static_cast<uint64_t>(P)) == ib * n_jt ? 0 : 1;
   for (int p = plo + lane; p <= phi; p += 32) {
-    const uint64_t u0p = udiv(U * static_cast<uint64_t>(p), static_cast<uint64_t>(P));
-    const int slot = (udiv(u0p, n_jt) == ib) ? 0 : 1;
+    const int slot = p == plo ? slot0 : 0;
     const float2 *src = part + static_cast<size_t>(p * 2 + slot) * 6 * BI;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
