@@ -380,9 +380,12 @@ __global__ void __launch_bounds__(kEndThreads) block_end_kernel(const EndArgs E)
   if (t_next < 0) return;
   const int64_t n_act = E.ctl[kCtlNact];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    E.ctl[kCtlBlocks] += 1;
+    // reductions without a return value: the thread does not wait for a
+    // round trip before its CTA's corrector work
+    atomicAdd(reinterpret_cast<unsigned long long *>(E.ctl + kCtlBlocks), 1ull);
+    atomicAdd(reinterpret_cast<unsigned long long *>(E.ctl + kCtlInter),
+              static_cast<unsigned long long>(n_act * E.n));
     E.ctl[kCtlLastT] = t_next;
-    E.ctl[kCtlInter] += n_act * E.n;
   }
   int b = -1;
   for (int q = 0; q < E.nbk; ++q)
