@@ -5,9 +5,10 @@ force + jerk hot path at N = 1,048,576.
 Workload: a King W0 = 7 cluster (seeded, equal masses, Henon units),
 eps = 1e-4, advanced by 4th-order Hermite steps with a shared step
 dt = 2^-10 so that every particle is active in every step.  One timed step
-is one pass of the whole path: block scheduling, FP64 predictor (writing
-the split-precision j-records), force + jerk of all N active particles
-against all N, FP64 corrector.  An interaction is one (i, j) pair
+is one pass of the whole path: block scheduling, predictor (split
+precision on the FP32 pipe from the FP64 state, writing the j-records),
+force + jerk of all N active particles against all N, corrector (FP64
+position and velocity update).  An interaction is one (i, j) pair
 evaluation; a step evaluates N^2 of them.
 
 Output: one JSON line (rank 0).  `value` is whole-job interactions/s from
