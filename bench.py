@@ -79,6 +79,9 @@ def parse():
                    help="isplit: shards of the i-split run on this GPU")
     p.add_argument("--sweep", action="store_true",
                    help="also time single evaluations at active fractions 2^-10..1")
+    p.add_argument("--oracle-replay", action="store_true",
+                   help="block65536: the FP64 oracle replays the GPU's schedule to t = 1/8 "
+                        "and compares |dE/E| (minutes of CPU work)")
     return p.parse_args()
 
 
@@ -578,6 +581,51 @@ def run_shared1024(args):
     return 0
 
 
+def block_energy_replay(_lib, m, x, v, eps, t_end_tick):
+    """Energy error of the block-step workload against the FP64 oracle in
+    replay mode: the GPU (split precision, host-driven steps) records its
+    schedule (block time and ordered active list of every block step) to
+    t_end, when all particles are synchronised; the oracle starts from the
+    same state and levels and takes the same steps.  The energy pass is
+    |dE/E|_gpu <= 2 max(|dE/E|_oracle, 1e-10)."""
+    from oracle import oracle as O
+
+    kw = dict(eps=eps, precision="ds", eta=0.01, eta_start=0.01, lev_min=3, lev_max=20)
+    sched = []
+    with _lib.NBody(m, x, v, **kw) as s:
+        lev0 = s.get_state(want=("lev",))["lev"].copy()
+        E0 = s.energy()[2]
+        while True:
+            st = s.get_state(want=("t_tick", "lev"))
+            due = st["t_tick"] + (1 << (20 - st["lev"].astype(np.int64)))
+            if due.min() > t_end_tick:
+                break
+            t, na = s.next_block()
+            act = s.active()
+            s.predict(t)
+            s.force_jerk_dev(None, na, None, None)
+            s.correct(t)
+            sched.append((int(round(t * 2**20)), act.astype(np.int64)))
+        xg = s.get_state(want=("x",))["x"]
+        E1 = s.energy()[2]
+    t0 = time.perf_counter()
+    orc = O.HermiteState(m, x, v, eps, eta=0.01, eta_start=0.01, lev_min=3, lev_max=20)
+    lev_agree = float(np.mean(orc.lev == lev0))
+    orc.lev[:] = lev0  # the GPU's initial levels (equal except at thresholds)
+    E0o = orc.energy()[2]
+    for tn, act in sched:
+        orc.step(replay=(tn, act))
+    E1o = orc.energy()[2]
+    dg, do = abs(E1 - E0) / abs(E0), abs(E1o - E0o) / abs(E0o)
+    return {"block_steps": len(sched), "dE_over_E_gpu": dg, "dE_over_E_oracle": do,
+            "pass": bool(dg <= 2 * max(do, 1e-10)),
+            "max_abs_dx": float(np.abs(xg - orc.x).max()),
+            "initial_levels_equal": lev_agree, "oracle_s": time.perf_counter() - t0,
+            "oracle_threads": O.max_threads(),
+            "note": "GPU split precision, host-driven steps; the oracle (FP64, every "
+                    "interaction) replays the GPU's schedule from the same initial levels"}
+
+
 def block_force_errors(_lib, m, x, v, eps, precs, checkpoints=(0, 5, 15), ns=4096):
     """Force + jerk errors of the block-step workload against the FP64
     oracle: at the given block steps (from the start), the GPU's force on
@@ -692,6 +740,8 @@ def run_block65536(args):
             "note": "value/ms: host-driven nb_step loop; device_resident: nb_run_blocks"}
     if not args.no_cpu:
         out["force_err"] = block_force_errors(_lib, m, x, v, eps, args.precisions.split(","))
+        if args.oracle_replay:
+            out["energy_vs_oracle_replay"] = block_energy_replay(_lib, m, x, v, eps, t_end)
         out["cpu_baseline"] = cpu_baseline(m, x, v, n, 3.0)
     print(json.dumps(out), flush=True)
     return 0
