@@ -747,7 +747,7 @@ def run_block65536(args):
     return 0
 
 
-def batched_oracle_checks(_lib, O, off, m, x, v, tuned, steps, n_force=64, n_energy=32):
+def batched_oracle_checks(_lib, O, off, m, x, v, tuned, steps, n_force=64, n_energy=64):
     """The batched form against the FP64 oracle: the per-particle force and
     jerk errors of the batch's first evaluation on n_force sampled
     clusters, and the energy error over `steps` shared steps of 1/256 from
@@ -766,12 +766,15 @@ def batched_oracle_checks(_lib, O, off, m, x, v, tuned, steps, n_force=64, n_ene
             b.run(steps)
             k1, w1 = b.energy()
         ea, ej, na, nj = [], [], [], []
+        ca = []
         for c in fc:
             sl = slice(off[c], off[c + 1])
             ra, rj = O.force_jerk(m[sl], x[sl], v[sl], 1e-3)
-            e = force_error(st0["a"][sl], st0["jerk"][sl], ra, rj)
+            cond = O.force_jerk_abs(m[sl], x[sl], v[sl], 1e-3)
+            e = force_error(st0["a"][sl], st0["jerk"][sl], ra, rj, cond)
             ea.append(e["acc_max_ei"]); ej.append(e["jerk_max_ei"])
             na.append(e["acc_norm"]); nj.append(e["jerk_norm"])
+            ca.append(e["acc_cond_max"])
         dE_gpu = np.abs((k1 + w1) - (k0 + w0)) / np.abs(k0 + w0)
         dE_orc = []
         for c in ec:
@@ -779,10 +782,16 @@ def batched_oracle_checks(_lib, O, off, m, x, v, tuned, steps, n_force=64, n_ene
             E0 = O.energy(m[sl], x[sl], v[sl], 1e-3)[2]
             xo, vo, _, _ = O.hermite_shared(m[sl], x[sl], v[sl], 1e-3, 8, steps)
             dE_orc.append(abs(O.energy(m[sl], xo, vo, 1e-3)[2] - E0) / abs(E0))
+        dE_orc = np.array(dE_orc)
+        ok = dE_gpu[ec] <= 2 * np.maximum(dE_orc, 1e-10)
         out[prec] = {"acc_max_ei": float(max(ea)), "jerk_max_ei": float(max(ej)),
                      "acc_norm_max": float(max(na)), "jerk_norm_max": float(max(nj)),
+                     "acc_cond_max": float(max(ca)),
                      "dE_over_E_median_gpu": float(np.median(dE_gpu[ec])),
-                     "dE_over_E_median_oracle": float(np.median(dE_orc))}
+                     "dE_over_E_median_oracle": float(np.median(dE_orc)),
+                     "energy_pass_fraction": float(np.mean(ok)),
+                     "dE_ratio_gpu_over_oracle_median": float(np.median(
+                         dE_gpu[ec] / np.maximum(dE_orc, 1e-300)))}
     out["sample"] = (f"first evaluation of {n_force} random clusters (seed 2004); energy over "
                      f"{steps} steps of 1/256 from the initial state on {n_energy} of them")
     return out
@@ -852,8 +861,7 @@ def run_batched(args):
     if not args.no_cpu:
         from oracle import oracle as O
 
-        out["oracle_checks"] = batched_oracle_checks(_lib, O, off, m, x, v, tuned,
-                                                     min(steps, 200))
+        out["oracle_checks"] = batched_oracle_checks(_lib, O, off, m, x, v, tuned, steps)
         # the oracle's shared-step loop over clusters until ~4e8 interactions
         take, work = [], 0.0
         for c in range(len(sizes)):
