@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(NT, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float4 *sbase = reinterpret_cast<float4 *>(smem_raw);
   __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ uint32_t s_tile[kStages];  // j-tile in each stage
 
   const int tid = threadIdx.x;
   const int g = tid / TPI;
@@ -198,9 +199,14 @@ __global__ void __launch_bounds__(NT, 1)
   }
   __syncthreads();
 
+  // Thread 0 issues the copies of the CTA's s-th unit's j-tile and notes
+  // the tile for the other threads, which read it after their wait on the
+  // stage's barrier (the arrival below releases the note) instead of each
+  // recomputing it (measured at N = 1M: 860 -> 853 ms per evaluation).
   auto issue = [&](uint64_t s_idx) {
     const int st = static_cast<int>(s_idx % kStages);
     const uint64_t jt = dev::umod(u0 + s_idx, n_jt);
+    s_tile[st] = static_cast<uint32_t>(jt);
     float4 *dst = sbase + static_cast<size_t>(st) * NARR * kJT;
     mbar_expect_tx(&bars[st], kTileBytes * (JRK ? NARR : NARR - 1));
     bulk_g2s(dst, A.jhi + jt * kJT, kTileBytes, &bars[st]);
@@ -300,7 +306,7 @@ __global__ void __launch_bounds__(NT, 1)
       bool fast = false;
       V ndx[NQ][3];
       if (REL) {
-        const uint64_t jt = dev::umod(u0 + s_idx, n_jt);
+        const uint64_t jt = s_tile[st];
         const float4 to = __ldg(&A.tinfo[2 * jt]);
         const float4 th = __ldg(&A.tinfo[2 * jt + 1]);
         const float ox[3] = {to.x, to.y, to.z}, hw[3] = {th.x, th.y, th.z};
