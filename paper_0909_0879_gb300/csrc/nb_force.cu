@@ -343,10 +343,10 @@ __global__ void __launch_bounds__(NT, 1)
       // 881 -> 866 ms per evaluation with the 16-deep unroll, the same
       // sampled errors).
       constexpr int CH = (PREC && kFoldChunk < kJT / TPI) ? kFoldChunk : kJT / TPI;
-      // j-loop unroll: 16 for the tile-relative kernel (measured at N = 1M:
-      // 878 ms against 881 with 8, which was 1 % faster than 4), 4 elsewhere
-      // (8 is 3 % slower for the FP32 IPT = 4 shape)
-      constexpr int UNR = REL ? 16 : 4;
+      // j-loop unroll: 8 for the tile-relative kernel (measured at N = 1M:
+      // 848 ms against 851 with 16 and 850 with 32), 4 elsewhere (8 is 3 %
+      // slower for the FP32 IPT = 4 shape)
+      constexpr int UNR = REL ? 8 : 4;
       auto walk_tile = [&](auto far_tag) {
         constexpr bool FAR = decltype(far_tag)::value;
         constexpr int CHW = FAR ? kJT / TPI : CH;
