@@ -500,3 +500,31 @@ def test_fused_block_steps_large_ragged_n(nb, block_steps):
     assert a[3]["interactions"] == g[3]["interactions"]
     for k in a[2]:
         assert np.array_equal(a[2][k], g[2][k]), k
+
+
+def test_fused_steps_rebuild_the_predictor_split_after_set_state(nb):
+    """The fused predictor reads an FP32 split of the state that the fused
+    corrector keeps current; a state set between two nb_run_blocks calls
+    (here: every position moved) must be split anew by the second call.
+    The context that ran before the change ends in the same bits as a
+    fresh context started from the changed state."""
+    n = 2048 + 5
+    m, x, v = ics.plummer(n, 61, masses=ics.salpeter_masses(n, 61))
+    kw = dict(eps=1e-4, eta=0.02, lev_min=5, lev_max=20)
+    rng = np.random.default_rng(62)
+    with nb.NBody(m, x, v, **kw) as a:
+        a.run_blocks(2.0**-7)
+        assert a.last_block_path() == "fused"
+        st = a.get_state()
+        st["x"] = st["x"] + 1e-3 * rng.standard_normal(st["x"].shape)
+        a.set_state(st)
+        d_a, _ = a.run_blocks(2.0**-6)
+        assert a.last_block_path() == "fused" and d_a > 0
+        got = a.get_state()
+    with nb.NBody(m, x, v, **kw) as b:
+        b.set_state(st)
+        d_b, _ = b.run_blocks(2.0**-6)
+        want = b.get_state()
+    assert d_a == d_b
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
