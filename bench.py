@@ -373,6 +373,11 @@ def run_ours(args, rank, world, local_rank):
     h2d = sum(a.nbytes for a in st.values())
     d2h = h2d
     torch.cuda.synchronize(dev)
+    # the clocks of this leg too: after the timed steps a long run can
+    # meet the power limit here
+    e2e_sampler = ClockSampler(local_rank) if rank == 0 else None
+    if e2e_sampler:
+        e2e_sampler.start()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         s.set_state(st)
@@ -380,6 +385,7 @@ def run_ours(args, rank, world, local_rank):
         s.get_state(out=st)
     torch.cuda.synchronize(dev)
     e2e_t = time.perf_counter() - t0
+    e2e_clocks = e2e_sampler.stop() if e2e_sampler else None
     e2e_val = e2e_steps * n * n / e2e_t / 1e9
     if world > 1:
         e2e_val = metrics.aggregate_throughput(e2e_t, e2e_steps * n * n, dev)[0] / 1e9
@@ -503,7 +509,8 @@ def run_ours(args, rank, world, local_rank):
         },
         "force_ms": float(np.mean(force_ms)),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h),
+                "d2h_bytes_per_step": int(d2h), "steps": int(e2e_steps),
+                "clocks": e2e_clocks,
                 "note": "nb_set_state + nb_step + nb_get_state with host arrays in pinned "
                         "memory, wall clock"},
         "gpu_launches": int(launches),
