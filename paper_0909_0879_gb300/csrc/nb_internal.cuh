@@ -86,7 +86,6 @@ constexpr int kCtlSlots = 40;
 // Device error-word bit of a timed-out look-back in the fused compaction.
 constexpr int kErrScanTimeout = 2;
 
-
 // Minimum j-tiles per CTA of the stream-K split, by the shape's threads
 // per i-particle: 2 for the short-list shapes (16 or more; their lists are
 // latency-bound and the CTA with the most tiles sets the time), 4
@@ -269,7 +268,6 @@ cudaError_t launch_split_refresh(int64_t n, const double *x, const double *v, co
                                  const double *jk, float4 *sp4, float2 *sp2, cudaStream_t s);
 cudaError_t launch_block_end(const EndArgs &E, int grid, cudaStream_t s);
 constexpr int kEndThreads = 256;
-
 
 // --- i-split shards (nb_shard.cu) ---
 constexpr int kMaxShards = 64;
