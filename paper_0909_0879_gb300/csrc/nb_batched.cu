@@ -203,8 +203,7 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
           for (int q = 0; q < NQ; ++q)
 #pragma unroll
             for (int k = 0; k < 3; ++k) pa[q][k] = O::bc(0.f);
-#pragma unroll 4
-          for (int j = j0; j < jend; j += tpi) {
+          auto pair = [&](int j) {
             const float4 hj = s_hi[j];
             const float4 wj = s_v[j];
             float4 lj = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -242,6 +241,16 @@ __global__ void __launch_bounds__(NT, 2) batched_hermite_kernel(const BatchArgs 
               p2[q][1] = O::fma(cc, dy, p2[q][1]);
               p2[q][2] = O::fma(cc, dz, p2[q][2]);
             }
+          };
+          if (tpi == 1 && jend - j0 == kBatchFold) {
+            // a whole chunk of consecutive j (the large clusters, which
+            // carry most of the pairs): a fixed trip count, so the
+            // shared-memory reads take immediate offsets
+#pragma unroll 8
+            for (int jj = 0; jj < kBatchFold; ++jj) pair(j0 + jj);
+          } else {
+#pragma unroll 4
+            for (int j = j0; j < jend; j += tpi) pair(j);
           }
 #pragma unroll
           for (int q = 0; q < IPT; ++q)
