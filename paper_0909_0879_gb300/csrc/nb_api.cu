@@ -926,6 +926,10 @@ nb_status queue_fused_blocks(nb_ctx *c, cudaStream_t s, int64_t *launches) {
   B.jvel = c->jvel;
   B.jrel = c->jrel;
   B.tinfo = c->tinfo;
+  // the smallest active count whose force shape takes the far field
+  B.rel_lo = INT64_MAX;
+  for (int k = 0; k < nbk; ++k)
+    if (variant_at(b[k].v).rel && b[k].lo < B.rel_lo) B.rel_lo = b[k].lo;
   B.act = c->act;
   B.ctl = c->scal;
   B.status = c->lb_status;

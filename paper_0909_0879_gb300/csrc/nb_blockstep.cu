@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
   __shared__ unsigned s_vid;
   __shared__ int s_lmax;
   __shared__ int64_t s_ctl[4];  // t_cur, blocks, max blocks, t_end
+  __shared__ int64_t s_cnt[kTicksLog2 + 1];
   __shared__ int s_wcnt[kJT / 32];
   __shared__ int64_t s_excl;
   __shared__ int s_agg, s_fail;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
   if (wid == 0) {
     const int64_t c = lane <= kTicksLog2 ? ctl[kCtlLevCnt + lane] : 0;
     const unsigned occ = __ballot_sync(0xffffffffu, c > 0);
+    if (lane <= kTicksLog2) s_cnt[lane] = c;
     if (lane == 0) {
       s_lmax = occ ? 31 - __clz(occ) : -1;
       s_vid = static_cast<unsigned>(
@@ -156,6 +158,16 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
   const int l_thr = kTicksLog2 - (tz < kTicksLog2 ? tz : kTicksLog2);
   const int64_t i = static_cast<int64_t>(vid) * kJT + tid;
   const bool real = i < B.n;
+  // the predictor's inputs, loaded before the ballot and the barrier so
+  // that their round trip overlaps the level's
+  dev::PSplit S;
+  int64_t ti = 0;
+  double mi = 0.0;
+  if (real) {
+    dev::load_split(i, B.sp4, B.sp2, S);
+    ti = B.t_tick[i];
+    mi = B.m[i];
+  }
   const bool due = real && B.lev[i] >= l_thr;
   const unsigned bal = __ballot_sync(0xffffffffu, due);
   if (lane == 0) s_wcnt[wid] = __popc(bal);
@@ -172,14 +184,16 @@ __global__ void __launch_bounds__(kJT, 2) block_begin_kernel(const BeginArgs B) 
   // the state's FP32 split)
   float4 h = make_float4(0.f, 0.f, 0.f, 0.f), lo = h;
   if (real) {
-    const float dt = static_cast<float>(t_next - B.t_tick[i]) * static_cast<float>(kTick);
-    dev::PSplit S;
-    dev::load_split(i, B.sp4, B.sp2, S);
+    const float dt = static_cast<float>(t_next - ti) * static_cast<float>(kTick);
     float xh[3], xl[3], vp[3];
     dev::predict_split(S, dt, xh, xl, vp);
-    h = dev::store_records_ds(i, xh, xl, vp, B.m[i], B.prec, B.jhi, B.jlo, B.jvel, &lo);
+    h = dev::store_records_ds(i, xh, xl, vp, mi, B.prec, B.jhi, B.jlo, B.jvel, &lo);
   }
-  if (B.jrel)
+  // Tile frames only for steps whose force shape takes the far field (the
+  // active count is the sum of the due levels' counts).
+  int64_t n_due = 0;
+  for (int l = l_thr; l <= kTicksLog2; ++l) n_due += s_cnt[l];
+  if (B.jrel && n_due >= B.rel_lo)
     dev::tile_frame(vid, i, real, h, lo, B.jrel, B.tinfo);  // synchronises the CTA
   else
     __syncthreads();

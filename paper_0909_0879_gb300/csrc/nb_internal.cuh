@@ -230,6 +230,7 @@ struct BeginArgs {
   int prec;
   float4 *jhi, *jlo, *jvel;
   float4 *jrel, *tinfo;              // DS only (tile frames), else null
+  int64_t rel_lo;                    // tile frames only from this active count on
   int32_t *act;
   int64_t *ctl;
   unsigned long long *status;        // n_jt look-back words
