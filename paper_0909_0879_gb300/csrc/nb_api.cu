@@ -80,6 +80,79 @@ bool finite_all(const double *p, int64_t cnt) {
   return true;
 }
 
+// Particles [b, e) of a state nb_set_state takes: the first particle with
+// a non-finite value (*nonfinite set) or an invalid level or tick, else e.
+int64_t first_bad_particle(const double *x, const double *v, const double *a,
+                           const double *jerk, const int64_t *t_tick, const int32_t *lev,
+                           int64_t b, int64_t e, bool *nonfinite) {
+  constexpr int64_t kBlk = 1024;
+  for (int64_t i0 = b; i0 < e; i0 += kBlk) {
+    const int64_t i1 = i0 + kBlk < e ? i0 + kBlk : e;
+    const int64_t m = 3 * (i1 - i0);
+    if (!finite_all(x + 3 * i0, m) || !finite_all(v + 3 * i0, m) ||
+        !finite_all(a + 3 * i0, m) || !finite_all(jerk + 3 * i0, m)) {
+      // the exact particle, for the message
+      for (int64_t i = i0; i < i1; ++i)
+        if (!finite_all(x + 3 * i, 3) || !finite_all(v + 3 * i, 3) ||
+            !finite_all(a + 3 * i, 3) || !finite_all(jerk + 3 * i, 3)) {
+          *nonfinite = true;
+          return i;
+        }
+    }
+    for (int64_t i = i0; i < i1; ++i)
+      if (lev[i] < 0 || lev[i] > kTicksLog2 || t_tick[i] < 0 ||
+          (t_tick[i] & ((int64_t(1) << (kTicksLog2 - lev[i])) - 1)) != 0) {
+        *nonfinite = false;
+        return i;
+      }
+  }
+  return e;
+}
+
+// The same over all n particles on up to 16 of the host's cores (one pass:
+// contiguous ranges, the caller's thread takes the last): the first bad
+// particle in index order, or n.
+int64_t first_bad_particle_par(int64_t n, const double *x, const double *v, const double *a,
+                               const double *jerk, const int64_t *t_tick, const int32_t *lev,
+                               bool *nonfinite) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  int T = hw ? static_cast<int>(hw) : 1;
+  if (T > 16) T = 16;
+  if (n < (int64_t(1) << 16) || T < 2)
+    return first_bad_particle(x, v, a, jerk, t_tick, lev, 0, n, nonfinite);
+  const int64_t chunk = (n + T - 1) / T;
+  std::vector<int64_t> bad(T, n);
+  std::vector<char> nf(T, 0);
+  std::vector<std::thread> th;
+  int spawned = 0;
+  auto run = [&](int k) {
+    const int64_t b = k * chunk, e = b + chunk < n ? b + chunk : n;
+    if (b >= e) return;
+    bool f = false;
+    const int64_t r = first_bad_particle(x, v, a, jerk, t_tick, lev, b, e, &f);
+    if (r < e) {
+      bad[k] = r;
+      nf[k] = f ? 1 : 0;
+    }
+  };
+  try {
+    th.reserve(T - 1);
+    for (int k = 0; k < T - 1; ++k) {
+      th.emplace_back(run, k);
+      ++spawned;
+    }
+  } catch (...) {
+  }
+  for (int k = spawned; k < T; ++k) run(k);
+  for (auto &t : th) t.join();
+  for (int k = 0; k < T; ++k)
+    if (bad[k] < n) {
+      *nonfinite = nf[k] != 0;
+      return bad[k];
+    }
+  return n;
+}
+
 // finite_all over large arrays on the host's cores: contiguous chunks on
 // up to 16 threads (the caller's thread takes the last); a thread that
 // cannot be created leaves its chunk to the caller.
@@ -1484,13 +1557,14 @@ nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double
   if (!x || !v || !a || !jerk || !t_tick || !lev)
     return fail(NB_ERR_INVALID_ARG, "nb_set_state needs all six arrays");
   const int64_t n = c->n;
-  if (!finite_all_par(x, 3 * n) || !finite_all_par(v, 3 * n) || !finite_all_par(a, 3 * n) ||
-      !finite_all_par(jerk, 3 * n))
-    return fail(NB_ERR_INVALID_ARG, "non-finite state");
-  for (int64_t i = 0; i < n; ++i) {
-    if (lev[i] < 0 || lev[i] > kTicksLog2 || t_tick[i] < 0 ||
-        (t_tick[i] & ((int64_t(1) << (kTicksLog2 - lev[i])) - 1)) != 0)
-      return fail(NB_ERR_INVALID_ARG, "particle %lld: level or tick invalid", (long long)i);
+  // one pass over the six arrays on the host's cores before any copy, so a
+  // rejected state leaves the context's state as it was
+  bool nonfinite = false;
+  const int64_t bad = first_bad_particle_par(n, x, v, a, jerk, t_tick, lev, &nonfinite);
+  if (bad < n) {
+    if (nonfinite) return fail(NB_ERR_INVALID_ARG, "non-finite state (particle %lld)",
+                               (long long)bad);
+    return fail(NB_ERR_INVALID_ARG, "particle %lld: level or tick invalid", (long long)bad);
   }
   const size_t n3 = 3 * static_cast<size_t>(n) * sizeof(double);
   NB_CUDA(cudaMemcpyAsync(c->x, x, n3, cudaMemcpyHostToDevice, c->stream));

@@ -288,8 +288,9 @@ def test_fp32_range_reports_numeric_error(nb):
 
 def test_set_state_rejects_non_finite_values_in_large_states(nb):
     """The state check of nb_set_state runs on the host's cores for large
-    arrays: a NaN or an infinity anywhere (first, last or in a middle chunk)
-    is rejected with NB_ERR_INVALID_ARG and the state is left unchanged."""
+    arrays: a NaN or an infinity anywhere (first, last or in a middle chunk),
+    or an invalid tick or level, is rejected with NB_ERR_INVALID_ARG naming
+    the first bad particle, and the state is left unchanged."""
     n = 800_000  # 2.4M values per array: the threaded check
     m, x, v = ics.plummer(n, 43)
     with nb.NBody(m, x, v, eps=1e-2, block_steps=False, lev_shared=8) as s:
@@ -301,6 +302,16 @@ def test_set_state_rejects_non_finite_values_in_large_states(nb):
             with pytest.raises(nb.NBodyError) as e:
                 s.set_state(mod)
             assert e.value.status == nb.NB_ERR_INVALID_ARG
+            assert f"particle {pos // 3}" in str(e.value)
+        # a tick that is not a multiple of its step, in a middle chunk, and
+        # two bad particles: the first in index order is named
+        mod = {k: a.copy() for k, a in st.items()}
+        mod["t_tick"][654_321] = 3
+        mod["lev"][700_001] = -1
+        with pytest.raises(nb.NBodyError) as e:
+            s.set_state(mod)
+        assert e.value.status == nb.NB_ERR_INVALID_ARG
+        assert "particle 654321" in str(e.value)
         s.set_state(st)
         back = s.get_state()
     for k in st:
