@@ -80,6 +80,9 @@ def parse():
                    help="isplit: shards of the i-split run on this GPU")
     p.add_argument("--sweep", action="store_true",
                    help="also time single evaluations at active fractions 2^-10..1")
+    p.add_argument("--relayout-every", type=int, default=0,
+                   help="king1m: re-store the particles in a fresh spatial order every K "
+                        "block steps (nb_set_relayout_every; 0 = keep the initial order)")
     p.add_argument("--oracle-replay", action="store_true",
                    help="block65536: the FP64 oracle replays the GPU's schedule to t = 1/8 "
                         "and compares |dE/E| (minutes of CPU work)")
@@ -309,6 +312,8 @@ def run_ours(args, rank, world, local_rank):
                    lev_shared=LEV_SHARED, stream=stream)
     if args.variant >= 0 or args.grid > 0:
         s.set_force_variant(args.variant, args.grid)
+    if args.relayout_every > 0:
+        s.set_relayout_every(args.relayout_every)
     props = torch.cuda.get_device_properties(dev)
     num_sms = props.multi_processor_count
     st0 = s.get_state()  # the initial state, for the force-error check
@@ -342,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
     if sampler:
         sampler.start()
     l0 = s.launch_count()
+    r0 = s.storage_order()[1]
     evs = []
     inter = 0
     for _ in range(args.steps):
@@ -350,6 +356,7 @@ def run_ours(args, rank, world, local_rank):
         inter += na * n
     torch.cuda.synchronize(dev)
     launches = s.launch_count() - l0
+    relayouts = s.storage_order()[1] - r0
     clocks = sampler.stop() if sampler else None
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     force_ms = [e[1].elapsed_time(e[2]) for e in evs]
@@ -495,7 +502,11 @@ def run_ours(args, rank, world, local_rank):
             "parallelism": f"replicas x{world} (independent clusters per GPU)",
             "l2": "flushed between timed steps (256 MB write outside the events)",
             "seed": "1003 + rank",
-            "layout": "particles stored in nb_spatial_order (balanced bisection, 256 per leaf)",
+            "layout": "particles stored in nb_spatial_order (balanced bisection, 256 per leaf)"
+                      + (f"; re-stored in the order of the current positions every "
+                         f"{args.relayout_every} block steps (nb_set_relayout_every)"
+                         if args.relayout_every > 0 else ""),
+            "relayouts_timed": relayouts,
         },
         "dE_over_E": dE,
         "dE_note": f"FP64 GPU energy before warm-up and after {args.warmup + args.steps} steps "

@@ -280,10 +280,48 @@ nb_status nb_set_state(nb_ctx *ctx, const double *x, const double *v,
                        const double *a, const double *jerk,
                        const int64_t *t_tick, const int32_t *lev);
 
-/* Copy the current active list (ascending int32 indices) into idx, which
- * holds cap entries; *n_active receives its length.  Synchronises. */
+/* Copy the current active list (int32 indices) into idx, which holds cap
+ * entries; *n_active receives its length.  The list is in storage order:
+ * ascending indices until nb_relayout re-stores the particles, afterwards
+ * ascending storage slots given as the caller's indices (the order of the
+ * rows of nb_force_jerk's result for idx == NULL).  Synchronises. */
 nb_status nb_get_active(nb_ctx *ctx, int32_t *idx, int64_t cap,
                         int64_t *n_active);
+
+/* Storage order (no counterpart in the paper; it keeps the force kernel's
+ * tile-relative far field, a layout optimisation, effective over a long
+ * run).  The split-precision force kernel walks a 256-record tile with
+ * plain FP32 differences when the tile is far from the i-block (box
+ * distance at least the tile's radius), which needs tiles and i-blocks
+ * compact in space: particles given in nb_spatial_order are, but as they
+ * move the tiles spread and more of them take the slower split path (a
+ * King W0 = 7 cluster of 2^20 particles: 97 % of tile pairs far at t = 0,
+ * about 78 % at t = 0.1 and 15 % at t = 0.5).
+ * nb_relayout re-stores every per-particle array of the context in a
+ * balanced-bisection order of the current positions (256-particle leaves,
+ * computed on the host cores, as nb_spatial_order): the caller's view does
+ * not change.  nb_get_state, nb_set_state and the index lists of
+ * nb_force_jerk / nb_force_jerk_dev keep the caller's (nb_init) order,
+ * nb_get_active returns the caller's indices; what changes is the order of
+ * the force sums (results differ by rounding only) and the order of the
+ * active list.  The j-records and the active list of the old order are
+ * dropped: the next call must be nb_next_block, nb_run_blocks or
+ * nb_symplectic.  Synchronises; costs a copy of the positions to the host,
+ * the bisection (~0.1 s for 2^20 particles) and a gather of the state on
+ * the device.  NB_ERR_STATE on a shard (nb_shard_set with nranks > 1),
+ * NB_ERR_NUMERIC for a non-finite position. */
+nb_status nb_relayout(nb_ctx *ctx);
+
+/* Automatic relayout: nb_next_block and nb_run_blocks re-store the
+ * particles first when at least block_steps block steps have been taken
+ * since the last relayout (nb_run_blocks checks at the start of each call
+ * only).  0 (the default) turns it off; NB_ERR_INVALID_ARG if negative. */
+nb_status nb_set_relayout_every(nb_ctx *ctx, int64_t block_steps);
+
+/* perm (n entries, may be NULL): perm[s] is the caller's index of the
+ * particle stored in slot s (the identity before the first relayout);
+ * *relayouts (may be NULL): relayouts so far. */
+nb_status nb_get_storage_order(nb_ctx *ctx, int32_t *perm, int64_t *relayouts);
 
 /* Counters: block steps taken, interactions evaluated (n_act * n summed
  * over force evaluations), and particles whose step criterion fell below
@@ -472,7 +510,8 @@ nb_status nb_lf_backward(int64_t n, const float *d_m, const float *d_ckpt,
  * the sharding.  Call between block steps (NB_ERR_STATE otherwise); shards
  * run host-driven steps only (nb_run_blocks and nb_symplectic return
  * NB_ERR_STATE), and nb_next_block returns NB_ERR_STATE until the last
- * block's import is done.  nb_shard_offsets gives the nranks + 1 slice
+ * block's import is done; a context re-stored by nb_relayout cannot
+ * become a shard (NB_ERR_STATE).  nb_shard_offsets gives the nranks + 1 slice
  * offsets of the block last found by nb_next_block (host array; for an
  * unsharded context 0 and the active count). */
 #define NB_SHARD_RECORD_DOUBLES 14

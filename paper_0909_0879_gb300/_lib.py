@@ -90,6 +90,9 @@ SIGNATURES = [
     ("nb_get_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_set_state", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("nb_get_active", C.c_int, [_vp, _vp, _i64, _P(_i64)]),
+    ("nb_relayout", C.c_int, [_vp]),
+    ("nb_set_relayout_every", C.c_int, [_vp, _i64]),
+    ("nb_get_storage_order", C.c_int, [_vp, _vp, _P(_i64)]),
     ("nb_get_counters", C.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)]),
     ("nb_sync", C.c_int, [_vp]),
     ("nb_launch_count", _i64, [_vp]),
@@ -429,6 +432,23 @@ class NBody:
         na = C.c_int64()
         _check(self._L.nb_get_active(self._h, idx.ctypes.data, idx.shape[0], C.byref(na)))
         return idx[: na.value].copy()
+
+    def relayout(self):
+        """Re-store the particles in a bisection order of their current
+        positions (the caller's order of every input and output stays)."""
+        _check(self._L.nb_relayout(self._h))
+
+    def set_relayout_every(self, block_steps: int):
+        """Relayout automatically after this many block steps (0: off)."""
+        _check(self._L.nb_set_relayout_every(self._h, int(block_steps)))
+
+    def storage_order(self):
+        """(perm, relayouts): perm[s] is the caller's index of the particle
+        stored in slot s."""
+        perm = np.zeros(self.n, dtype=np.int32)
+        cnt = C.c_int64()
+        _check(self._L.nb_get_storage_order(self._h, perm.ctypes.data, C.byref(cnt)))
+        return perm, cnt.value
 
     def counters(self):
         b, i, c = C.c_int64(), C.c_int64(), C.c_int64()

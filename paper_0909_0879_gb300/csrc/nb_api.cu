@@ -349,6 +349,17 @@ struct nb_ctx {
   bool sh_corrected = false;    // own slice corrected, other shards' records not yet imported
   bool sh_off_valid = false;    // h_sh_off holds the last block's offsets
   int64_t sh_nact = 0;          // active count of that block
+  // storage order (nb_relayout): slot s holds the particle the caller
+  // knows as perm[s]; the identity until the first relayout
+  bool permuted = false;
+  int32_t *d_perm = nullptr;    // slot -> caller's index
+  int32_t *d_slot = nullptr;    // caller's index -> slot
+  int64_t *d_q = nullptr;       // a relayout's gather order (old slots)
+  double *lay_buf = nullptr;    // 3n doubles: staging of the reordering copies
+  std::vector<int32_t> h_perm;  // host copy of d_perm
+  int64_t relayout_every = 0;   // automatic relayout after this many block steps (0: off)
+  int64_t layout_blocks = 0;    // n_blocks at the last relayout
+  int64_t relayouts = 0;
   std::vector<void *> allocs;
 };
 
@@ -530,6 +541,11 @@ nb_status validate_config(const nb_config *cfg) {
   }
   return NB_OK;
 }
+
+// storage order (defined with the spatial layout below)
+nb_status relayout(nb_ctx *c);
+nb_status relayout_if_due(nb_ctx *c);
+nb_status ensure_qidx(nb_ctx *c, int64_t n_idx);
 
 }  // namespace
 
@@ -723,6 +739,8 @@ nb_status nb_next_block(nb_ctx *c, double *t_next, int64_t *n_active) {
   if (s != NB_OK) return s;
   if (c->sh_corrected)
     return fail(NB_ERR_STATE, "shard: nb_shard_import of the last block's records comes first");
+  s = relayout_if_due(c);
+  if (s != NB_OK) return s;
   int nl = 0;
   NB_CUDA(launch_next_block(c->n, c->t_tick, c->lev, c->act, c->blk, c->scal, c->stream, &nl));
   c->launches += nl;
@@ -790,6 +808,14 @@ nb_status nb_force_jerk_dev(nb_ctx *c, const int32_t *d_idx, int64_t n_idx, doub
   if (n_idx < 0) return fail(NB_ERR_INVALID_ARG, "negative n_idx");
   if (n_idx > 0 && (!d_acc || !d_jerk))
     return fail(NB_ERR_INVALID_ARG, "d_acc and d_jerk are required with an explicit index list");
+  if (c->permuted && n_idx > 0) {
+    // the caller's indices to storage slots
+    s = ensure_qidx(c, n_idx);
+    if (s != NB_OK) return s;
+    NB_CUDA(launch_map_index(n_idx, d_idx, c->d_slot, c->n, c->qidx, c->stream));
+    c->launches += 1;
+    d_idx = c->qidx;
+  }
   return queue_force(c, d_idx, n_idx, d_acc, d_jerk);
 }
 
@@ -811,18 +837,8 @@ nb_status nb_force_jerk(nb_ctx *c, const int32_t *idx, int64_t n_idx, double *ac
       if (idx[k] < 0 || idx[k] >= c->n)
         return fail(NB_ERR_INVALID_ARG, "index %lld at position %lld out of range [0, %lld)",
                     (long long)idx[k], (long long)k, (long long)c->n);
-    if (n_idx > c->qidx_cap) {
-      if (c->qidx) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(c->qidx);
-        for (auto &p : c->allocs)
-          if (p == c->qidx) p = nullptr;
-        c->qidx = nullptr;
-      }
-      s = dev_alloc_t(c, &c->qidx, n_idx);
-      if (s != NB_OK) return s;
-      c->qidx_cap = n_idx;
-    }
+    s = ensure_qidx(c, n_idx);
+    if (s != NB_OK) return s;
     if (6 * n_idx > c->qout_cap) {
       if (c->qout) {
         cudaStreamSynchronize(c->stream);
@@ -838,6 +854,10 @@ nb_status nb_force_jerk(nb_ctx *c, const int32_t *idx, int64_t n_idx, double *ac
     if (n_idx > 0)
       NB_CUDA(cudaMemcpyAsync(c->qidx, idx, n_idx * sizeof(int32_t), cudaMemcpyHostToDevice,
                               c->stream));
+    if (c->permuted && n_idx > 0) {
+      NB_CUDA(launch_map_index(n_idx, c->qidx, c->d_slot, c->n, c->qidx, c->stream));
+      c->launches += 1;
+    }
     s = queue_force(c, c->qidx, n_idx, c->qout, c->qout + 3 * n_idx);
     if (s != NB_OK) return s;
     src_a = c->qout;
@@ -1251,6 +1271,110 @@ nb_status spatial_gather(nb_ctx *c, SymArrays *A) {
   return NB_OK;
 }
 
+// Re-store every per-particle array in a balanced-bisection order of the
+// current positions (leaves of one 256-record tile).  The new slot s holds
+// the particle of old slot q[s]; the caller's index of slot s becomes
+// perm_old[q[s]].  Each array is gathered into the staging buffer and
+// copied back, so the arrays keep their addresses (captured CUDA graphs
+// stay valid).  The j-records, the active list and the fused steps' split
+// state belong to the old order: the protocol restarts at nb_next_block
+// and nb_run_blocks rebuilds the split at its start.
+nb_status relayout(nb_ctx *c) {
+  const int64_t n = c->n;
+  const size_t n3 = 3 * static_cast<size_t>(n);
+  if (!c->lay_buf) {
+    nb_status s = dev_alloc_t(c, &c->lay_buf, n3);
+    if (s == NB_OK) s = dev_alloc_t(c, &c->d_perm, n);
+    if (s == NB_OK) s = dev_alloc_t(c, &c->d_slot, n);
+    if (s == NB_OK) s = dev_alloc_t(c, &c->d_q, n);
+    if (s != NB_OK) return s;
+  }
+  std::vector<double> hx;
+  std::vector<int64_t> q;
+  std::vector<int32_t> perm_new;
+  try {
+    hx.resize(n3);
+    q.resize(n);
+    perm_new.resize(n);
+    if (!c->permuted) {
+      c->h_perm.resize(n);
+      std::iota(c->h_perm.begin(), c->h_perm.end(), int32_t(0));
+    }
+  } catch (...) {
+    return fail(NB_ERR_OOM, "host memory for the relayout");
+  }
+  NB_CUDA(cudaMemcpyAsync(hx.data(), c->x, n3 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  nb_status s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  if (!finite_all_par(hx.data(), static_cast<int64_t>(n3)))
+    return fail(NB_ERR_NUMERIC, "non-finite position: no relayout");
+  std::iota(q.begin(), q.end(), int64_t(0));
+  try {
+    kd_split(hx.data(), q.data(), 0, n, kJT, kd_threads());
+  } catch (...) {
+    return fail(NB_ERR_OOM, "host memory for the bisection");
+  }
+  for (int64_t k = 0; k < n; ++k) perm_new[k] = c->h_perm[q[k]];
+  NB_CUDA(cudaMemcpyAsync(c->d_q, q.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                          c->stream));
+  double *const vec3[] = {c->x, c->v, c->a, c->jk};
+  for (double *p : vec3) {
+    NB_CUDA((launch_gather_rows<double, int64_t>(n, c->d_q, p, c->lay_buf, 3, c->stream)));
+    NB_CUDA(cudaMemcpyAsync(p, c->lay_buf, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream));
+  }
+  NB_CUDA((launch_gather_rows<double, int64_t>(n, c->d_q, c->m, c->lay_buf, 1, c->stream)));
+  NB_CUDA(cudaMemcpyAsync(c->m, c->lay_buf, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                          c->stream));
+  int64_t *ti = reinterpret_cast<int64_t *>(c->lay_buf);
+  NB_CUDA((launch_gather_rows<int64_t, int64_t>(n, c->d_q, c->t_tick, ti, 1, c->stream)));
+  NB_CUDA(cudaMemcpyAsync(c->t_tick, ti, n * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                          c->stream));
+  int32_t *li = reinterpret_cast<int32_t *>(c->lay_buf);
+  NB_CUDA((launch_gather_rows<int32_t, int64_t>(n, c->d_q, c->lev, li, 1, c->stream)));
+  NB_CUDA(cudaMemcpyAsync(c->lev, li, n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                          c->stream));
+  NB_CUDA(cudaMemcpyAsync(c->d_perm, perm_new.data(), n * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, c->stream));
+  NB_CUDA(launch_invert(n, c->d_perm, c->d_slot, c->stream));
+  c->launches += 8;
+  // the host vectors go out of scope: the copies from them finish first
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  c->h_perm.swap(perm_new);
+  c->permuted = true;
+  c->have_block = false;
+  c->force_done = false;
+  c->t_pred = -1;
+  c->layout_blocks = c->n_blocks;
+  c->relayouts += 1;
+  return NB_OK;
+}
+
+// The automatic relayout of nb_set_relayout_every, when it is due.
+nb_status relayout_if_due(nb_ctx *c) {
+  if (c->relayout_every <= 0 || c->sh.p > 1) return NB_OK;
+  if (c->n_blocks - c->layout_blocks < c->relayout_every) return NB_OK;
+  return relayout(c);
+}
+
+// Room for n_idx staged indices.
+nb_status ensure_qidx(nb_ctx *c, int64_t n_idx) {
+  if (n_idx <= c->qidx_cap) return NB_OK;
+  if (c->qidx) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->qidx);
+    for (auto &p : c->allocs)
+      if (p == c->qidx) p = nullptr;
+    c->qidx = nullptr;
+  }
+  nb_status s = dev_alloc_t(c, &c->qidx, n_idx);
+  if (s != NB_OK) return s;
+  c->qidx_cap = n_idx;
+  return NB_OK;
+}
+
 }  // namespace
 
 extern "C" void nb_external_allen_santillan(nb_external *e) {
@@ -1417,6 +1541,8 @@ extern "C" nb_status nb_run_blocks(nb_ctx *c, double t_end, int64_t max_blocks,
   if (!ok) return fail(NB_ERR_INVALID_ARG, "t_end %.17g is not a non-negative multiple of 2^-20",
                        t_end);
   if (max_blocks < 0) return fail(NB_ERR_INVALID_ARG, "negative block budget");
+  s = relayout_if_due(c);
+  if (s != NB_OK) return s;
   // partial-sum scratch for every shape the device-resident steps may run
   size_t pb = 0;
   {
@@ -1537,6 +1663,34 @@ nb_status nb_get_state(nb_ctx *c, double *x, double *v, double *a, double *jerk,
   nb_status s = check_ctx(c);
   if (s != NB_OK) return s;
   const size_t n3 = 3 * static_cast<size_t>(c->n) * sizeof(double);
+  if (c->permuted) {
+    // gathered into the caller's order (slot of caller index u: d_slot[u]),
+    // one array at a time through the staging buffer
+    const int64_t n = c->n;
+    double *const src3[] = {c->x, c->v, c->a, c->jk};
+    double *const dst3[] = {x, v, a, jerk};
+    for (int k = 0; k < 4; ++k) {
+      if (!dst3[k]) continue;
+      NB_CUDA((launch_gather_rows<double, int32_t>(n, c->d_slot, src3[k], c->lay_buf, 3,
+                                                  c->stream)));
+      NB_CUDA(cudaMemcpyAsync(dst3[k], c->lay_buf, n3, cudaMemcpyDeviceToHost, c->stream));
+      c->launches += 1;
+    }
+    if (t_tick) {
+      int64_t *ti = reinterpret_cast<int64_t *>(c->lay_buf);
+      NB_CUDA((launch_gather_rows<int64_t, int32_t>(n, c->d_slot, c->t_tick, ti, 1, c->stream)));
+      NB_CUDA(cudaMemcpyAsync(t_tick, ti, n * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                              c->stream));
+      c->launches += 1;
+    }
+    if (lev) {
+      int32_t *li = reinterpret_cast<int32_t *>(c->lay_buf);
+      NB_CUDA((launch_gather_rows<int32_t, int32_t>(n, c->d_slot, c->lev, li, 1, c->stream)));
+      NB_CUDA(cudaMemcpyAsync(lev, li, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+      c->launches += 1;
+    }
+    return sync_ctx(c);
+  }
   if (x) NB_CUDA(cudaMemcpyAsync(x, c->x, n3, cudaMemcpyDeviceToHost, c->stream));
   if (v) NB_CUDA(cudaMemcpyAsync(v, c->v, n3, cudaMemcpyDeviceToHost, c->stream));
   if (a) NB_CUDA(cudaMemcpyAsync(a, c->a, n3, cudaMemcpyDeviceToHost, c->stream));
@@ -1567,13 +1721,33 @@ nb_status nb_set_state(nb_ctx *c, const double *x, const double *v, const double
     return fail(NB_ERR_INVALID_ARG, "particle %lld: level or tick invalid", (long long)bad);
   }
   const size_t n3 = 3 * static_cast<size_t>(n) * sizeof(double);
-  NB_CUDA(cudaMemcpyAsync(c->x, x, n3, cudaMemcpyHostToDevice, c->stream));
-  NB_CUDA(cudaMemcpyAsync(c->v, v, n3, cudaMemcpyHostToDevice, c->stream));
-  NB_CUDA(cudaMemcpyAsync(c->a, a, n3, cudaMemcpyHostToDevice, c->stream));
-  NB_CUDA(cudaMemcpyAsync(c->jk, jerk, n3, cudaMemcpyHostToDevice, c->stream));
-  NB_CUDA(cudaMemcpyAsync(c->t_tick, t_tick, n * sizeof(int64_t), cudaMemcpyHostToDevice,
-                          c->stream));
-  NB_CUDA(cudaMemcpyAsync(c->lev, lev, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  if (c->permuted) {
+    // uploaded in the caller's order, then gathered into the storage order
+    // (slot s holds the caller's particle d_perm[s])
+    double *const dst3[] = {c->x, c->v, c->a, c->jk};
+    const double *const src3[] = {x, v, a, jerk};
+    for (int k = 0; k < 4; ++k) {
+      NB_CUDA(cudaMemcpyAsync(c->lay_buf, src3[k], n3, cudaMemcpyHostToDevice, c->stream));
+      NB_CUDA((launch_gather_rows<double, int32_t>(n, c->d_perm, c->lay_buf, dst3[k], 3,
+                                                  c->stream)));
+    }
+    int64_t *ti = reinterpret_cast<int64_t *>(c->lay_buf);
+    NB_CUDA(cudaMemcpyAsync(ti, t_tick, n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA((launch_gather_rows<int64_t, int32_t>(n, c->d_perm, ti, c->t_tick, 1, c->stream)));
+    int32_t *li = reinterpret_cast<int32_t *>(c->lay_buf);
+    NB_CUDA(cudaMemcpyAsync(li, lev, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA((launch_gather_rows<int32_t, int32_t>(n, c->d_perm, li, c->lev, 1, c->stream)));
+    c->launches += 6;
+  } else {
+    NB_CUDA(cudaMemcpyAsync(c->x, x, n3, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(cudaMemcpyAsync(c->v, v, n3, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(cudaMemcpyAsync(c->a, a, n3, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(cudaMemcpyAsync(c->jk, jerk, n3, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(cudaMemcpyAsync(c->t_tick, t_tick, n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                            c->stream));
+    NB_CUDA(cudaMemcpyAsync(c->lev, lev, n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            c->stream));
+  }
   c->have_block = false;
   c->force_done = false;
   c->t_pred = -1;
@@ -1596,7 +1770,42 @@ nb_status nb_get_active(nb_ctx *c, int32_t *idx, int64_t cap, int64_t *n_active)
       NB_CUDA(cudaMemcpyAsync(idx, c->act, c->n_act * sizeof(int32_t), cudaMemcpyDeviceToHost,
                               c->stream));
   }
-  return sync_ctx(c);
+  s = sync_ctx(c);
+  if (s != NB_OK) return s;
+  if (idx && c->permuted)  // storage slots to the caller's indices
+    for (int64_t k = 0; k < c->n_act; ++k) idx[k] = c->h_perm[idx[k]];
+  return NB_OK;
+}
+
+nb_status nb_relayout(nb_ctx *c) {
+  Range r("nb_relayout");
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (c->sh.p > 1)
+    return fail(NB_ERR_STATE, "a shard exchanges records in its peers' order: no relayout");
+  return relayout(c);
+}
+
+nb_status nb_set_relayout_every(nb_ctx *c, int64_t block_steps) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (block_steps < 0) return fail(NB_ERR_INVALID_ARG, "negative relayout interval");
+  c->relayout_every = block_steps;
+  c->layout_blocks = c->n_blocks;
+  return NB_OK;
+}
+
+nb_status nb_get_storage_order(nb_ctx *c, int32_t *perm, int64_t *relayouts) {
+  nb_status s = check_ctx(c);
+  if (s != NB_OK) return s;
+  if (perm) {
+    if (c->permuted)
+      std::copy(c->h_perm.begin(), c->h_perm.end(), perm);
+    else
+      std::iota(perm, perm + c->n, int32_t(0));
+  }
+  if (relayouts) *relayouts = c->relayouts;
+  return NB_OK;
 }
 
 nb_status nb_get_counters(nb_ctx *c, int64_t *n_blocks, int64_t *n_interactions,
@@ -1721,6 +1930,9 @@ nb_status nb_shard_set(nb_ctx *c, int32_t nranks, int32_t rank, const int64_t *b
   }
   if (c->have_block || c->sh_corrected)
     return fail(NB_ERR_STATE, "change the sharding between block steps only");
+  if (nranks > 1 && c->permuted)
+    return fail(NB_ERR_STATE, "shards need the caller's particle order: this context was "
+                              "re-stored by nb_relayout");
   if (nranks > 1 && !c->d_sh_off) {
     s = dev_alloc_t(c, &c->d_sh_off, kMaxShards + 1);
     if (s != NB_OK) return s;

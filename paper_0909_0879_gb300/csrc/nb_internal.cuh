@@ -310,4 +310,16 @@ cudaError_t launch_permute(int64_t n, const int64_t *perm, const double *src, do
 // a += a_ext(x) for every particle.
 cudaError_t launch_ext_add(int64_t n, const ExtField &E, const double *x, double *a,
                            cudaStream_t s);
+
+// --- Storage order (nb_layout.cu) ---
+// Rows of w elements: dst[k] = src[idx[k]], k < n (T: double, int64_t,
+// int32_t; I: int32_t, int64_t).
+template <class T, class I>
+cudaError_t launch_gather_rows(int64_t n, const I *idx, const T *src, T *dst, int w,
+                               cudaStream_t s);
+// inv[perm[k]] = k for a permutation of [0, n).
+cudaError_t launch_invert(int64_t n, const int32_t *perm, int32_t *inv, cudaStream_t s);
+// out[k] = slot[in[k]] for indices in [0, n); others are left as they are.
+cudaError_t launch_map_index(int64_t n_idx, const int32_t *in, const int32_t *slot, int64_t n,
+                             int32_t *out, cudaStream_t s);
 }  // namespace nbi
