@@ -242,3 +242,33 @@ def test_relayout_protocol_and_errors(nb):
         with pytest.raises(nb.NBodyError) as e:
             s.relayout()
         assert e.value.status == nb.NB_ERR_STATE
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32"])
+def test_symplectic_after_relayout(nb, oracle_mod, prec):
+    """Sixth-order symplectic steps on a re-stored context (N = 3000,
+    eps = 0.05, 4 steps of 1/32) return x, v and a in the caller's order
+    within the symplectic tests' bound of the FP64 oracle: a force error of
+    at most tol * sum_j |f_ij| moves a particle by at most T^2/2 times it
+    and changes its velocity by at most T times it over T = 1/8 (twice
+    those bounds per particle; tol 1e-6 split precision, 2e-5 FP32)."""
+    n, eps, dt, ns = 3000, 0.05, 1.0 / 32, 4
+    T = dt * ns
+    tol = {"ds": 1e-6, "fp32": 2e-5}[prec]
+    m, x, v = ics.plummer(n, 47)
+    xo, vo = oracle_mod.symplectic(m, x, v, eps, dt, ns, 6)
+    aabs = np.maximum(oracle_mod.force_jerk_abs(m, x, np.zeros_like(x), eps)[0],
+                      oracle_mod.force_jerk_abs(m, xo, np.zeros_like(xo), eps)[0])
+    with nb.NBody(m, x, v, eps=eps, precision=prec) as s:
+        s.relayout()
+        perm, nrel = s.storage_order()
+        assert nrel == 1 and not np.array_equal(perm, np.arange(n))
+        s.symplectic(6, dt, ns)
+        st = s.get_state(want=("x", "v", "a"))
+    dx = np.linalg.norm(st["x"] - xo, axis=1)
+    dv = np.linalg.norm(st["v"] - vo, axis=1)
+    assert np.all(dx <= 2 * 0.5 * T * T * tol * aabs)
+    assert np.all(dv <= 2 * T * tol * aabs)
+    ao = oracle_mod.acc(m, st["x"], eps)
+    ca = oracle_mod.force_jerk_abs(m, st["x"], np.zeros_like(x), eps)[0]
+    assert np.all(np.linalg.norm(st["a"] - ao, axis=1) <= tol * ca)
