@@ -46,6 +46,13 @@ struct VOps<float> {
     if (MASK) return r2 > 0.f ? rsqrtf(r2) : 0.f;
     return rsqrtf(r2);
   }
+  // 1/r2 from the MUFU pipe (PTX rcp.approx.ftz.f32, the hardware's
+  // approximate reciprocal) instead of rinv * rinv on the FMA pipe
+  static __device__ __forceinline__ float rcp(float r2) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+    return y;
+  }
   static __device__ __forceinline__ float lane(float a, int) { return a; }
   static __device__ __forceinline__ void set(float &a, int, float s) { a = s; }
 };
@@ -61,6 +68,9 @@ struct VOps<float2> {
   template <int MASK>
   static __device__ __forceinline__ float2 rsq(float2 r2) {
     return make_float2(VOps<float>::rsq<MASK>(r2.x), VOps<float>::rsq<MASK>(r2.y));
+  }
+  static __device__ __forceinline__ float2 rcp(float2 r2) {
+    return make_float2(VOps<float>::rcp(r2.x), VOps<float>::rcp(r2.y));
   }
   static __device__ __forceinline__ float lane(float2 a, int w) { return w ? a.y : a.x; }
   static __device__ __forceinline__ void set(float2 &a, int w, float s) {
