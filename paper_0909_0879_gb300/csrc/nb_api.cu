@@ -1339,9 +1339,9 @@ nb_status relayout(nb_ctx *c) {
                           cudaMemcpyHostToDevice, c->stream));
   NB_CUDA(launch_invert(n, c->d_perm, c->d_slot, c->stream));
   c->launches += 8;
-  // the host vectors go out of scope: the copies from them finish first
-  s = sync_ctx(c);
-  if (s != NB_OK) return s;
+  // the new order is queued on the stream: the host side follows it before
+  // the wait, so the mapping matches the arrays even if the wait reports an
+  // error (the copies from the host vectors were staged when queued)
   c->h_perm.swap(perm_new);
   c->permuted = true;
   c->have_block = false;
@@ -1349,7 +1349,7 @@ nb_status relayout(nb_ctx *c) {
   c->t_pred = -1;
   c->layout_blocks = c->n_blocks;
   c->relayouts += 1;
-  return NB_OK;
+  return sync_ctx(c);
 }
 
 // The automatic relayout of nb_set_relayout_every, when it is due.
